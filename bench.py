@@ -1,0 +1,454 @@
+"""Benchmark of the fixpoint relaxation sweep on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload rmat22|grid4096|er16k]
+
+One step is one pass of the whole hot path over the workload, all resident in
+HBM when the timed region starts: build the graph (CSR, COO, symmetrised copy,
+degree buckets) from the device-resident edge list, then SSSP and BFS from 8
+seeded sources plus CC, each in all four modes (vertex/edge x sync/async),
+every result copied out in bulk, then free the graph.  The value is GTEPS
+(Graph500 convention: input edges whose source is reached, per query; all
+edges for CC) over the whole step.  ``e2e`` is the same step through the same
+C ABI with pinned host buffers (graph upload and result downloads inside the
+timed region).  Under torchrun, every rank runs an independent replica
+(the method shards by independent queries; no data-path collective).
+
+``--impl reference`` times the CPU oracle (single thread) on a bounded sample
+of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import graphgen as gg  # noqa: E402
+
+METRIC = "SSSP/BFS GTEPS & HBM-roofline %; served p50/p99 latency vs one-at-a-time"
+MODE_NAMES = ["vertex_sync", "vertex_async", "edge_sync", "edge_async"]
+ALGO_NAMES = ["sssp", "bfs", "cc"]
+
+# DRAM bytes per launch from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by kernel; valid only while the kernel source
+# is unchanged (sha256 of csrc/fg_fixpoint.cu at capture time).
+NCU_TRAFFIC: dict = {}
+
+
+def fixpoint_source_sha() -> str:
+    p = os.path.join(ROOT, "paper_1903_01665_gb300", "csrc", "fg_fixpoint.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+# ---------------------------------------------------------------- workloads
+def make_workload(name: str):
+    if name == "rmat22":
+        g = gg.rmat(22)
+        desc = ("rmat-22 (4,194,304 V, 67,108,864 E, a,b,c=.57,.19,.19, w U[1,1000]): SSSP+BFS from 8 "
+                "seeded sources + CC, each in 4 modes, graph build included")
+    elif name == "grid4096":
+        g = gg.grid(4096)
+        desc = ("grid-4096 (16,777,216 V, ~65.8M E, 2% deleted, 0.1% shortcuts, w U[1,10000]): SSSP+BFS "
+                "from 8 seeded sources + CC, each in 4 modes, graph build included")
+    elif name == "er16k":
+        g = gg.er()
+        desc = "er-16384-131072 (w U[1,100]): SSSP from vertex 0, vertex-sync"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    srcs = [0] if name == "er16k" else [int(s) for s in gg.sources(g, 8)]
+    return g, srcs, desc
+
+
+def queries_for(workload: str, srcs):
+    """(algo, mode, source) triples of one step."""
+    if workload == "er16k":
+        return [(0, 0, 0)]
+    q = []
+    for mode in range(4):
+        for s in srcs:
+            q.append((0, mode, s))
+            q.append((1, mode, s))
+        q.append((2, mode, 0))
+    return q
+
+
+# ---------------------------------------------------------------- algorithmic bytes
+def algorithmic_bytes(algo: int, mode: int, st: dict, info: dict) -> float:
+    """Bytes the variant must move for one query, from its device counters.
+
+    R rounds, Va expanded vertices, Ea relaxed edges, U successful MIN
+    updates, P worklist appends, n vertices, nz vertices with out-edges, m
+    edges (symmetrised graph for CC).  4-byte ids, values and offsets.
+    """
+    R, Va, Ea, U, P = st["rounds"], st["vertices_processed"], st["edges_relaxed"], st["updates"], st["pushes"]
+    n = info["n"]
+    if algo == 2:
+        m = info["m_sym"]
+        nz = n - info["n_isolated"]
+    else:
+        m = info["m"]
+        nz = n - info["n_zero_out"]
+    per_edge = {0: 12, 1: 8, 2: 8}[algo]          # col (+ w for SSSP) + target value
+    if mode == 0:   # vertex-sync: stamp test per listed vertex per round
+        if algo == 1:
+            b = R * 4 * nz + Va * 8 + Ea * per_edge + U * 4
+        else:
+            b = R * 4 * nz + Va * 16 + Ea * per_edge + U * 12
+    elif mode == 2:  # edge-sync: src stream + source test per round
+        if algo == 1:
+            b = R * (4 * m + 4 * nz) + Ea * per_edge + U * 4
+        else:
+            b = R * (4 * m + 4 * nz + 4 * n) + Va * 8 + Ea * per_edge + U * 12
+    else:            # async: per item (item, offsets, value), per edge, per update, per push
+        item = 12 if algo == 1 else 16
+        if mode == 3:
+            item += 16                              # degree prefix: item, offsets, prefix write
+        upd = 8 if algo == 1 else 16
+        b = Va * item + Ea * per_edge + U * upd + P * 12
+    if algo == 2:
+        b += st["jump_passes"] * n * 8
+    return float(b)
+
+
+# ---------------------------------------------------------------- clocks
+REASONS = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", "-i", str(self.idx),
+               "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+               "--format=csv,noheader,nounits", "-lms", "200"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+
+        def pump():
+            for line in self.proc.stdout:
+                self.lines.append(line.strip())
+        self.thread = threading.Thread(target=pump, daemon=True)
+        self.thread.start()
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"error": "nvidia-smi unavailable"}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, power, seen = [], [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(REASONS[1:], parts[4:8]):
+                if val.lower().startswith("active"):
+                    seen.add(name)
+        if not sm:
+            return {"error": "no clock samples"}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(seen)}
+
+
+# ---------------------------------------------------------------- our arm
+class Runner:
+    def __init__(self, workload: str, device):
+        import torch
+        import paper_1903_01665_gb300 as fg
+        self.fg, self.torch = fg, torch
+        self.workload = workload
+        self.g, self.srcs, self.desc = make_workload(workload)
+        g = self.g
+        self.d_src = torch.from_numpy(g.src).to(device)
+        self.d_dst = torch.from_numpy(g.dst).to(device)
+        self.d_w = torch.from_numpy(g.w).to(device)
+        self.h_src = torch.from_numpy(g.src).pin_memory()
+        self.h_dst = torch.from_numpy(g.dst).pin_memory()
+        self.h_w = torch.from_numpy(g.w).pin_memory()
+        self.queries = queries_for(workload, self.srcs)
+        self.outs = [torch.empty(g.n, dtype=torch.int32, device=device) for _ in range(2)]
+        self.h_out = torch.empty(g.n, dtype=torch.int32).pin_memory()
+        self.deg = np.bincount(g.src, minlength=g.n).astype(np.int64)
+        self.teps_edges = self._teps_edges()
+        self.info = None
+
+    def _teps_edges(self):
+        """Graph500 edge count per query: edges whose source is reached (all edges for CC)."""
+        fg, torch, g = self.fg, self.torch, self.g
+        st, h = fg.fg_graph_create_coo(g.n, self.d_src, self.d_dst, self.d_w)
+        fg.check(st)
+        st, info = fg.fg_graph_info(h)
+        self.info_base = info.as_dict()
+        reach = {}
+        for s in set(self.srcs):
+            fg.check(fg.fg_bfs(h, s, self.outs[0], fg.FG_EDGE_ASYNC))
+            lv = self.outs[0].cpu().numpy()
+            reach[s] = int(self.deg[lv != fg.FG_INF].sum())
+        fg.check(fg.fg_graph_destroy(h))
+        return {(a, s): (reach[s] if a != 2 else g.m) for (a, _m, s) in self.queries}
+
+    def step(self, e2e: bool = False, record=None):
+        """One pass of the hot path; returns (units, stats list)."""
+        fg, g = self.fg, self.g
+        if e2e:
+            st, h = fg.fg_graph_create_coo(g.n, self.h_src, self.h_dst, self.h_w)
+        else:
+            st, h = fg.fg_graph_create_coo(g.n, self.d_src, self.d_dst, self.d_w)
+        fg.check(st)
+        if self.info is None:
+            st2, info = fg.fg_graph_info(h)
+            self.info = info.as_dict()
+        units = 0
+        for i, (algo, mode, s) in enumerate(self.queries):
+            out = self.h_out if e2e else self.outs[i & 1]
+            st, stats = fg.fg_run(h, algo, s, out, mode)
+            fg.check(st)
+            units += self.teps_edges[(algo, s)]
+            if record is not None:
+                record.append((algo, mode, stats.as_dict()))
+        fg.check(fg.fg_graph_destroy(h))
+        return units
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_ours(args):
+    import torch
+    import paper_1903_01665_gb300 as fg
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+        pg = dist
+    fg.load(build_if_missing=False)
+    r = Runner(args.workload, device)
+    stream = torch.cuda.current_stream(device)
+
+    def barrier():
+        torch.cuda.synchronize(device)
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize(device)
+
+    for _ in range(args.warmup):
+        r.step()
+    # ---- timed region: device-resident inputs
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_idx = vis.split(",")[local] if vis and not vis.startswith("GPU-") else str(local)
+    clocks = ClockSampler(int(smi_idx) if smi_idx.isdigit() else local)
+    clocks.start()
+    record = []
+    barrier()
+    l0 = fg.fg_kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    units = 0
+    for _ in range(args.steps):
+        units += r.step(record=record)
+    ev1.record(stream)
+    barrier()
+    launches = fg.fg_kernel_launches() - l0
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if pg:
+        t = torch.tensor([ms], device=device)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * units / (ms * 1e-3) / 1e9
+
+    # ---- roofline of the dominant kernel (largest share of device time)
+    per_kernel = {}
+    for algo, mode, st in record:
+        k = (algo, mode)
+        d = per_kernel.setdefault(k, {"ms": 0.0, "bytes": 0.0, "launches": 0})
+        d["ms"] += st["kernel_ms"]
+        d["bytes"] += algorithmic_bytes(algo, mode, st, r.info)
+        d["launches"] += 1
+    total_kernel_ms = sum(d["ms"] for d in per_kernel.values())
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
+    dk = per_kernel[dom]
+    peaks = load_peaks()
+    achieved = (dk["bytes"] / dk["launches"]) / (dk["ms"] / dk["launches"] * 1e-3) / 1e9
+    kname = f"fixpoint_kernel<{ALGO_NAMES[dom[0]]},{MODE_NAMES[dom[1]]}>"
+    traffic = None
+    rec = NCU_TRAFFIC.get(kname)
+    if rec and rec.get("src_sha") == fixpoint_source_sha():
+        traffic = rec["bytes_per_launch"]
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peaks[0],
+                "unit": "GB/s", "frac": round(achieved / peaks[0], 4), "peak_source": peaks[1],
+                "traffic": traffic, "algorithmic_bytes_per_launch": dk["bytes"] / dk["launches"],
+                "avg_launch_ms": dk["ms"] / dk["launches"],
+                "share_of_kernel_time": round(dk["ms"] / total_kernel_ms, 4)}
+    per_mode = {}
+    for (algo, mode), d in sorted(per_kernel.items()):
+        per_mode[f"{ALGO_NAMES[algo]}/{MODE_NAMES[mode]}"] = {
+            "avg_ms": round(d["ms"] / d["launches"], 4),
+            "gbps": round(d["bytes"] / (d["ms"] * 1e-3) / 1e9, 1)}
+
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        k2 = max(1, min(args.steps, 3))
+        barrier()
+        t0 = time.perf_counter()
+        u2 = 0
+        for _ in range(k2):
+            u2 += r.step(e2e=True)
+        barrier()
+        dt = time.perf_counter() - t0
+        if pg:
+            t = torch.tensor([dt], device=device)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": round(ws * u2 / dt / 1e9, 4), "unit": "GTEPS",
+               "h2d_bytes_per_step": 3 * 4 * r.g.m,
+               "d2h_bytes_per_step": 4 * r.g.n * len(r.queries), "steps": k2}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(r.g, r.srcs, r.deg, args.workload)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+                "data": "synthetic (seeded generators in graphgen/)",
+                "config": {"workload": r.desc, "queries_per_step": len(r.queries),
+                           "teps_edges_per_step": units // max(args.steps, 1),
+                           "l2": "inputs larger than L2 (graph ~1.9-2.2 GB built per step)",
+                           "parallelism": f"replicas x{ws}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk, "per_kernel": per_mode}
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- oracle timing
+def cpu_baseline_sample(g, srcs, deg, workload):
+    """The oracle, untuned, single thread: SSSP + BFS from one source and CC."""
+    import oracle
+    s = srcs[0]
+    t0 = time.perf_counter()
+    rc1, d = oracle.sssp(g.n, g.src, g.dst, g.w, s)
+    rc2, lv = oracle.bfs(g.n, g.src, g.dst, s)
+    units = 2 * int(deg[lv != oracle.UNREACHED].sum())
+    if workload != "er16k":
+        oracle.cc(g.n, g.src, g.dst)
+        units += g.m
+    dt = time.perf_counter() - t0
+    return {"value": round(units / dt / 1e9, 5), "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"1 SSSP + 1 BFS from source {s}" + (" + 1 CC" if workload != "er16k" else "")
+                      + f" on {workload}, sequential C, {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    import oracle
+    g, srcs, desc = make_workload(args.workload)
+    deg = np.bincount(g.src, minlength=g.n).astype(np.int64)
+    oracle.build()
+
+    def one(i):
+        s = srcs[i % len(srcs)]
+        _, lv = oracle.bfs(g.n, g.src, g.dst, s)
+        oracle.sssp(g.n, g.src, g.dst, g.w, s)
+        units = 2 * int(deg[lv != oracle.UNREACHED].sum())
+        if args.workload != "er16k":
+            oracle.cc(g.n, g.src, g.dst)
+            units += g.m
+        return units
+
+    for i in range(args.warmup):
+        one(i)
+    t0 = time.perf_counter()
+    units = 0
+    for i in range(args.steps):
+        units += one(args.warmup + i)
+    dt = time.perf_counter() - t0
+    value = units / dt / 1e9
+    sample = (f"each step: 1 SSSP + 1 BFS from one of the 8 sources" +
+              (" + 1 CC" if args.workload != "er16k" else "") + f" on {args.workload}, sequential C oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "GTEPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic (seeded generators in graphgen/)", "config": {"workload": desc},
+            "cpu_baseline": {"value": round(value, 5), "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 5), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat22", choices=["rmat22", "grid4096", "er16k"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * fg -- fixpoint graph relaxation on NVIDIA GB300 (sm_103a).
+ *
+ * C ABI of the data-parallel hot path of the Falcon method (Gogoi,
+ * Cheramangalath and Nasre, "Custom Code Generation for a Graph DSL",
+ * arXiv 1903.01665): the edge-relaxation sweep repeated until a fixpoint for
+ * single-source shortest paths (Alg. 1 and 2), breadth-first search (Alg. 3)
+ * and connected components (benchmarked in Sec. 4), in the four variants the
+ * paper generates from one specification (Sec. 3.1-3.3):
+ *
+ *   FG_VERTEX_SYNC  vertex-based over CSR (points x outnbrs, Alg. 1),
+ *                   double-buffered values, one grid barrier per round;
+ *   FG_EDGE_SYNC    edge-based over the COO edge list (edges, Alg. 2),
+ *                   double-buffered values, one grid barrier per round;
+ *   FG_VERTEX_ASYNC data-driven (Sec. 3.3): a device worklist of vertices,
+ *                   in-place atomic MIN, run until the worklist is empty;
+ *   FG_EDGE_ASYNC   the same worklist expanded to its out-edges and relaxed
+ *                   edge-parallel, in place.
+ *
+ * All four reach the same unique fixpoint, so their outputs are identical.
+ *
+ * Conventions for every call:
+ *   - Ids, weights, distances, levels and labels are int32.  "Unreached" is
+ *     INT32_MAX (FG_INF) for SSSP and BFS.
+ *   - Input and output arrays may be host memory (pageable or pinned) or
+ *     device memory of the current device; the library tells them apart
+ *     with cudaPointerGetAttributes.  Inputs are read during the call only
+ *     and never retained.  Outputs are caller-owned int32[n], written once,
+ *     in bulk, only on success (the paper's aggregated transfer, Sec. 3.5).
+ *   - Every call returns an fg_status; nothing throws across the ABI.  On
+ *     error, fg_last_error() gives a message for the calling thread and the
+ *     outputs are untouched.
+ *   - A graph handle is immutable after creation and may be queried from
+ *     several host threads and streams at once; each query owns its state.
+ *   - Queries run on the calling thread's current CUDA device, which must
+ *     be the device the graph was created on.
+ */
+#ifndef FG_H
+#define FG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FG_INF 2147483647
+
+typedef struct fg_graph fg_graph;
+
+typedef enum {
+    FG_OK = 0,
+    FG_ERR_INVALID_ARG = 1,     /* null pointer, n <= 0, m < 0, id outside [0,n), bad
+                                   row offsets, invalid mode/algo, wrong device */
+    FG_ERR_NEGATIVE_WEIGHT = 2, /* some weight < 0 (create time) */
+    FG_ERR_OVERFLOW = 3,        /* a finite shortest distance is >= INT32_MAX */
+    FG_ERR_OUT_OF_MEMORY = 4,   /* device or host allocation failed */
+    FG_ERR_TIMEOUT = 5,         /* round cap reached, or a device-side wait ran out */
+    FG_ERR_CUDA = 6             /* any other CUDA runtime error */
+} fg_status;
+
+typedef enum {
+    FG_VERTEX_SYNC = 0,
+    FG_VERTEX_ASYNC = 1,
+    FG_EDGE_SYNC = 2,
+    FG_EDGE_ASYNC = 3,
+    FG_AUTO = 4                 /* the mode fg_select_mode picks */
+} fg_mode;
+
+typedef enum { FG_ALGO_SSSP = 0, FG_ALGO_BFS = 1, FG_ALGO_CC = 2 } fg_algo;
+
+/*
+ * Graph creation.
+ *
+ * fg_graph_create_csr: n vertices, m edges in compressed sparse rows (the
+ *   storage of vertex-based code, Sec. 3.1): row_off[n+1] int64, row_off[0]
+ *   = 0, non-decreasing, row_off[n] = m; col[m] int32 targets in [0,n);
+ *   w[m] int32 weights >= 0, or NULL for all-ones weights.
+ * fg_graph_create_coo: the same graph as an edge list (source, destination,
+ *   weight) in any order (the storage of edge-based code, Sec. 3.1).
+ *
+ * Both build, on the device: the CSR (uint32 offsets; m < 2^32 required),
+ * the source-sorted COO (its dst and w arrays are the CSR's col and w), the
+ * degree buckets of the vertex kernels (1..31, 32..1023, >= 1024 out-edges),
+ * and the symmetrised CSR/COO used by connected components (every edge also
+ * read backwards: the undirected nbrs iterator, Table "foreach iterators").
+ * Self-loops and duplicate edges are kept.  The handle is written to *out
+ * only on success.  Errors: FG_ERR_INVALID_ARG, FG_ERR_NEGATIVE_WEIGHT,
+ * FG_ERR_OUT_OF_MEMORY, FG_ERR_CUDA.
+ */
+fg_status fg_graph_create_csr(int32_t n, int64_t m, const int64_t *row_off, const int32_t *col,
+                              const int32_t *w, fg_graph **out);
+fg_status fg_graph_create_coo(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                              const int32_t *w, fg_graph **out);
+
+/* Frees the graph's device memory.  NULL is accepted (no-op). */
+fg_status fg_graph_destroy(fg_graph *g);
+
+/* Host-side facts about a graph, computed at creation. */
+typedef struct {
+    int32_t n;
+    int64_t m;
+    int64_t m_sym;              /* edges of the symmetrised graph (2m) */
+    int32_t max_out_degree;
+    int32_t n_zero_out;         /* vertices with no out-edge */
+    int32_t n_low, n_mid, n_high; /* degree-bucket sizes (1..31, 32..1023, >= 1024) */
+    int32_t n_high_chunks;      /* 2048-edge chunks of the high bucket */
+    int32_t n_isolated;         /* vertices with no edge in either direction */
+    int64_t device_bytes;       /* device memory held by the handle */
+} fg_graph_info_t;
+
+fg_status fg_graph_info(const fg_graph *g, fg_graph_info_t *out);
+
+/*
+ * Queries.  src in [0,n).  out is int32[n]:
+ *   fg_sssp: shortest distance from src (Alg. 1/2 fixpoint), FG_INF if
+ *            unreachable.  FG_ERR_OVERFLOW if a finite distance would be
+ *            >= INT32_MAX.
+ *   fg_bfs:  fewest edges on a path from src (Alg. 3 fixpoint), FG_INF if
+ *            unreachable; weights are ignored.
+ *   fg_cc:   smallest vertex id of the vertex's component in the symmetrised
+ *            graph (weak components of the directed input).
+ * The call blocks until out is written.  Uses the legacy default stream.
+ */
+fg_status fg_sssp(const fg_graph *g, int32_t src, int32_t *dist_out, fg_mode mode);
+fg_status fg_bfs(const fg_graph *g, int32_t src, int32_t *level_out, fg_mode mode);
+fg_status fg_cc(const fg_graph *g, int32_t *label_out, fg_mode mode);
+
+/*
+ * The runtime form of the paper's compile-time choice of vertex/edge and
+ * sync/async code (Sec. 2 "flexible processing", Sec. 4.3): picks a mode for
+ * this graph and algorithm from its degree skew and an estimate of its
+ * diameter (one BFS, run and cached on first use).
+ */
+fg_status fg_select_mode(const fg_graph *g, fg_algo algo, fg_mode *out);
+
+/* Options and statistics of fg_run.  Zero-initialised options mean defaults. */
+typedef struct {
+    void *stream;               /* cudaStream_t to run on; NULL = legacy default stream */
+    int32_t max_rounds;         /* round / generation cap; 0 = n + 2 */
+    int32_t wait_timeout_ms;    /* bound on any single device-side wait; 0 = 1000 ms */
+    int32_t blocks_per_sm;      /* persistent CTAs per SM; 0 = occupancy limit */
+    int32_t inject_missing_arrival; /* testing aid for failure detection: if nonzero, CTA 0
+                                   leaves the kernel without arriving at the first grid
+                                   barrier, so every other CTA's bounded wait runs out and
+                                   the call returns FG_ERR_TIMEOUT (the context stays
+                                   usable).  0 in normal use. */
+} fg_options;
+
+typedef struct {
+    int32_t mode;               /* mode that ran (FG_AUTO resolved) */
+    int32_t rounds;             /* sync rounds or async worklist generations, final
+                                   no-change round included */
+    int32_t jump_passes;        /* CC pointer-jumping passes */
+    int32_t grid_blocks;        /* persistent CTAs launched */
+    int64_t vertices_processed; /* active vertices expanded, summed over rounds */
+    int64_t edges_relaxed;      /* edges whose source was active, summed over rounds */
+    int64_t updates;            /* successful MIN updates */
+    int64_t pushes;             /* worklist appends (async modes) */
+    float kernel_ms;            /* device time of the fixpoint kernel (CUDA events on
+                                   the query's stream) */
+} fg_stats;
+
+/*
+ * General query: algo, src (ignored for CC), out, mode, options (NULL =
+ * defaults) and stats (NULL = not wanted).  Blocks until out is written or an
+ * error is known.  FG_ERR_TIMEOUT if max_rounds rounds were not enough or a
+ * device wait exceeded wait_timeout_ms.
+ */
+fg_status fg_run(const fg_graph *g, fg_algo algo, int32_t src, int32_t *out, fg_mode mode,
+                 const fg_options *opt, fg_stats *stats);
+
+/*
+ * One synchronous relaxation round with every vertex active, from caller
+ * state: the topology-driven sweep of Alg. 1 (FG_VERTEX_SYNC) or Alg. 2
+ * (FG_EDGE_SYNC) for SSSP.  cur and next are device int32[n]; next must
+ * hold values <= cur elementwise (e.g. a copy of cur); next receives
+ * min(next, cur[u] + w) over every edge.  Returns the number of lowered
+ * values in *updates (may be NULL).  Used to measure the sweep against the
+ * HBM roofline.
+ */
+fg_status fg_sweep(const fg_graph *g, fg_mode mode, const int32_t *cur, int32_t *next,
+                   void *stream, int64_t *updates, float *kernel_ms);
+
+/* Number of kernels this library has launched in this process so far (all
+   threads and devices); lets a caller count the device work of a region. */
+uint64_t fg_kernel_launches(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *fg_last_error(void);
+/* Name of a status code. */
+const char *fg_status_string(fg_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FG_H */

@@ -1,0 +1,506 @@
+// Graph construction on the device: validation, CSR + source-sorted COO by
+// counting sort, the symmetrised copy for connected components, and the
+// degree buckets of the vertex kernels.
+//
+// Storage follows Sec. 3.1: vertex-based code reads CSR (row offsets +
+// targets), edge-based code reads the edge list (source, destination,
+// weight).  The COO here is the CSR's edges in CSR order, so its dst and w
+// arrays are the CSR's col and w and only src is stored in addition.
+#include <algorithm>
+#include <vector>
+
+#include "fg_internal.cuh"
+
+namespace fg {
+
+namespace {
+
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kBlock * kScanItems;
+
+inline int grid_for(int64_t work, int per_block = kBlock) {
+    int64_t b = (work + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > 152 * 64) b = 152 * 64;   // grid-stride beyond this
+    return (int)b;
+}
+
+// ---------------------------------------------------------------- validation
+enum { kBadId = 1, kBadWeight = 2, kBadOffsets = 4 };
+
+__global__ void k_validate_coo(int64_t m, int32_t n, const int32_t *__restrict__ s,
+                               const int32_t *__restrict__ d, const int32_t *__restrict__ w,
+                               int *flags) {
+    int f = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int32_t a = s[e], b = d[e];
+        if (a < 0 || a >= n || b < 0 || b >= n) f |= kBadId;
+        if (w && w[e] < 0) f |= kBadWeight;
+    }
+    f = __reduce_or_sync(0xffffffffu, f);
+    if (f && lane_id() == 0) atomicOr(flags, f);
+}
+
+__global__ void k_validate_csr(int32_t n, int64_t m, const int64_t *__restrict__ ro,
+                               const int32_t *__restrict__ col, const int32_t *__restrict__ w,
+                               int *flags) {
+    int f = 0;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (int64_t v = t; v < n; v += stride)
+        if (ro[v] > ro[v + 1]) f |= kBadOffsets;
+    if (t == 0 && (ro[0] != 0 || ro[n] != m)) f |= kBadOffsets;
+    for (int64_t e = t; e < m; e += stride) {
+        int32_t b = col[e];
+        if (b < 0 || b >= n) f |= kBadId;
+        if (w && w[e] < 0) f |= kBadWeight;
+    }
+    f = __reduce_or_sync(0xffffffffu, f);
+    if (f && lane_id() == 0) atomicOr(flags, f);
+}
+
+// ---------------------------------------------------------------- counting sort
+__global__ void k_histogram(int64_t m, const int32_t *__restrict__ keys, uint32_t *cnt) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[keys[e]], 1u);
+}
+
+__global__ void k_scatter_coo(int64_t m, const int32_t *__restrict__ s, const int32_t *__restrict__ d,
+                              const int32_t *__restrict__ w, uint32_t *cursor, int32_t *col,
+                              int32_t *wout, int32_t *srcout) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int32_t u = s[e];
+        uint32_t pos = atomicAdd(&cursor[u], 1u);
+        col[pos] = d[e];
+        wout[pos] = w ? w[e] : 1;
+        srcout[pos] = u;
+    }
+}
+
+__global__ void k_offsets_to_u32(int32_t n, const int64_t *__restrict__ ro, uint32_t *out) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v <= n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        out[v] = (uint32_t)ro[v];
+}
+
+__global__ void k_fill_ones(int64_t m, int32_t *w) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        w[e] = 1;
+}
+
+// src[e] = owner row of edge e, one warp per vertex.
+__global__ void k_src_from_rows(int32_t n, const uint32_t *__restrict__ ro, int32_t *src) {
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < n; v += nwarps) {
+        uint32_t b = ro[v], e = ro[v + 1];
+        for (uint32_t k = b + lane_id(); k < e; k += 32) src[k] = (int32_t)v;
+    }
+}
+
+// symmetrised degree = out-degree + in-degree
+__global__ void k_sym_degree(int32_t n, const uint32_t *__restrict__ ro, uint32_t *deg) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        deg[v] += ro[v + 1] - ro[v];
+}
+
+__global__ void k_scatter_sym(int64_t m, const int32_t *__restrict__ src, const int32_t *__restrict__ col,
+                              uint32_t *cursor, int32_t *scol, int32_t *ssrc) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int32_t u = src[e], v = col[e];
+        uint32_t p = atomicAdd(&cursor[u], 1u);
+        scol[p] = v;
+        ssrc[p] = u;
+        uint32_t q = atomicAdd(&cursor[v], 1u);
+        scol[q] = u;
+        ssrc[q] = v;
+    }
+}
+
+// ---------------------------------------------------------------- scan
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *total) {
+    __shared__ uint32_t warp_tot[kWarps];
+    uint32_t inc = warp_inclusive_scan(x);
+    int wid = threadIdx.x >> 5;
+    if (lane_id() == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t t = lane_id() < kWarps ? warp_tot[lane_id()] : 0;
+        uint32_t ti = warp_inclusive_scan(t);
+        if (lane_id() < kWarps) warp_tot[lane_id()] = ti - t;
+        if (lane_id() == kWarps - 1) *total = ti;
+    }
+    __syncthreads();
+    uint32_t r = warp_tot[wid] + inc - x;
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_reduce(int64_t len, const uint32_t *__restrict__ in, uint32_t *bsum) {
+    int64_t base = blockIdx.x * (int64_t)kScanTile + threadIdx.x * (int64_t)kScanItems;
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++)
+        if (base + i < len) s += in[base + i];
+    __shared__ uint32_t tot;
+    block_exclusive_scan(s, &tot);
+    __syncthreads();
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_apply(int64_t len, const uint32_t *__restrict__ in, const uint32_t *__restrict__ boff,
+                             uint32_t *out) {
+    int64_t base = blockIdx.x * (int64_t)kScanTile + threadIdx.x * (int64_t)kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        v[i] = (base + i < len) ? in[base + i] : 0u;
+        s += v[i];
+    }
+    __shared__ uint32_t tot;
+    uint32_t run = block_exclusive_scan(s, &tot) + (boff ? boff[blockIdx.x] : 0u);
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        if (base + i < len) out[base + i] = run;
+        run += v[i];
+    }
+    if (base <= len - 1 && len - 1 < base + kScanItems) out[len] = run;   // owner of the last item
+}
+
+__global__ void k_set_u32(uint32_t *p, uint32_t v) { *p = v; }
+
+// out[0..len] = exclusive prefix sums of in[0..len), out[len] = total (uint32).
+cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t len, cudaStream_t st) {
+    if (len <= 0) {
+        k_set_u32<<<1, 1, 0, st>>>(out, 0u);
+        count_launch();
+        return cudaGetLastError();
+    }
+    int64_t nb = (len + kScanTile - 1) / kScanTile;
+    if (nb == 1) {
+        k_scan_apply<<<1, kBlock, 0, st>>>(len, in, nullptr, out);
+        count_launch();
+        return cudaGetLastError();
+    }
+    uint32_t *bsum = nullptr, *boff = nullptr;
+    cudaError_t e = cudaMallocAsync(&bsum, nb * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMallocAsync(&boff, (nb + 1) * sizeof(uint32_t), st);
+    if (e != cudaSuccess) { cudaFreeAsync(bsum, st); return e; }
+    k_scan_reduce<<<(unsigned)nb, kBlock, 0, st>>>(len, in, bsum);
+    count_launch();
+    e = exclusive_scan(bsum, boff, nb, st);
+    if (e == cudaSuccess) {
+        k_scan_apply<<<(unsigned)nb, kBlock, 0, st>>>(len, in, boff, out);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(bsum, st);
+    cudaFreeAsync(boff, st);
+    return e;
+}
+
+// ---------------------------------------------------------------- buckets
+__global__ void k_bucket_counts(int32_t n, const uint32_t *__restrict__ ro, uint32_t *f_low,
+                                uint32_t *f_mid, uint32_t *f_high, uint32_t *f_chunks, uint32_t *f_nz,
+                                uint32_t *f_zero, int *max_deg) {
+    int mx = 0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t d = ro[v + 1] - ro[v];
+        f_low[v] = (d >= 1 && d < (uint32_t)kLowMax);
+        f_mid[v] = (d >= (uint32_t)kLowMax && d < (uint32_t)kMidMax);
+        f_high[v] = (d >= (uint32_t)kMidMax);
+        f_chunks[v] = d >= (uint32_t)kMidMax ? (d + kChunk - 1) / kChunk : 0u;
+        f_nz[v] = (d >= 1);
+        f_zero[v] = (d == 0);
+        mx = max(mx, (int)min(d, (uint32_t)INT32_MAX));
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (lane_id() == 0) atomicMax(max_deg, mx);
+}
+
+__global__ void k_bucket_write(int32_t n, const uint32_t *__restrict__ ro, const uint32_t *p_low,
+                               const uint32_t *p_mid, const uint32_t *p_chunks, const uint32_t *p_nz,
+                               const uint32_t *p_zero, int32_t *low, int32_t *mid, int2 *high, int32_t *nz,
+                               int32_t *zero) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t b = ro[v], d = ro[v + 1] - b;
+        if (d == 0) {
+            zero[p_zero[v]] = (int32_t)v;
+            continue;
+        }
+        nz[p_nz[v]] = (int32_t)v;
+        if (d < (uint32_t)kLowMax) {
+            low[p_low[v]] = (int32_t)v;
+        } else if (d < (uint32_t)kMidMax) {
+            mid[p_mid[v]] = (int32_t)v;
+        } else {
+            uint32_t c0 = p_chunks[v];
+            for (uint32_t k = 0; k * (uint32_t)kChunk < d; k++)
+                high[c0 + k] = make_int2((int32_t)v, (int32_t)(b + k * (uint32_t)kChunk));
+        }
+    }
+}
+
+// RAII-free allocation helper recording into the graph for destroy
+struct Builder {
+    fg_graph *g;
+    cudaStream_t st;
+    fg_status status = FG_OK;
+    std::string msg;
+
+    template <typename T>
+    T *alloc_graph(int64_t count) {
+        if (status != FG_OK) return nullptr;
+        void *p = nullptr;
+        size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(T);
+        cudaError_t e = cudaMallocAsync(&p, bytes, st);
+        if (e != cudaSuccess) {
+            status = (e == cudaErrorMemoryAllocation) ? FG_ERR_OUT_OF_MEMORY : FG_ERR_CUDA;
+            msg = std::string("device allocation failed: ") + cudaGetErrorString(e);
+            cudaGetLastError();
+            return nullptr;
+        }
+        g->allocs[g->n_allocs++] = p;
+        g->info.device_bytes += (int64_t)bytes;
+        return (T *)p;
+    }
+    template <typename T>
+    T *alloc_tmp(int64_t count) {
+        if (status != FG_OK) return nullptr;
+        void *p = nullptr;
+        cudaError_t e = cudaMallocAsync(&p, (size_t)std::max<int64_t>(count, 1) * sizeof(T), st);
+        if (e != cudaSuccess) {
+            status = (e == cudaErrorMemoryAllocation) ? FG_ERR_OUT_OF_MEMORY : FG_ERR_CUDA;
+            msg = std::string("device allocation failed: ") + cudaGetErrorString(e);
+            cudaGetLastError();
+            return nullptr;
+        }
+        return (T *)p;
+    }
+    bool check(cudaError_t e, const char *what) {
+        if (status != FG_OK) return false;
+        if (e != cudaSuccess) {
+            status = (e == cudaErrorMemoryAllocation) ? FG_ERR_OUT_OF_MEMORY : FG_ERR_CUDA;
+            msg = std::string(what) + ": " + cudaGetErrorString(e);
+            cudaGetLastError();
+            return false;
+        }
+        return true;
+    }
+};
+
+// Degree buckets of one view (row offsets already set).
+void make_buckets(Builder &b, View &v) {
+    int32_t n = v.n;
+    uint32_t *f = b.alloc_tmp<uint32_t>(6 * (int64_t)n);
+    uint32_t *p = b.alloc_tmp<uint32_t>(6 * ((int64_t)n + 1));
+    int *mx = b.alloc_tmp<int>(1);
+    if (b.status != FG_OK) return;
+    b.check(cudaMemsetAsync(mx, 0, sizeof(int), b.st), "memset");
+    uint32_t *f_low = f, *f_mid = f + n, *f_high = f + 2 * (int64_t)n, *f_chunks = f + 3 * (int64_t)n,
+             *f_nz = f + 4 * (int64_t)n, *f_zero = f + 5 * (int64_t)n;
+    int64_t pn = (int64_t)n + 1;
+    uint32_t *p_low = p, *p_mid = p + pn, *p_high = p + 2 * pn, *p_chunks = p + 3 * pn, *p_nz = p + 4 * pn,
+             *p_zero = p + 5 * pn;
+    k_bucket_counts<<<grid_for(n), kBlock, 0, b.st>>>(n, v.row_off, f_low, f_mid, f_high, f_chunks, f_nz,
+                                                      f_zero, mx);
+    count_launch();
+    b.check(cudaGetLastError(), "bucket counts");
+    b.check(exclusive_scan(f_low, p_low, n, b.st), "scan");
+    b.check(exclusive_scan(f_mid, p_mid, n, b.st), "scan");
+    b.check(exclusive_scan(f_high, p_high, n, b.st), "scan");
+    b.check(exclusive_scan(f_chunks, p_chunks, n, b.st), "scan");
+    b.check(exclusive_scan(f_nz, p_nz, n, b.st), "scan");
+    b.check(exclusive_scan(f_zero, p_zero, n, b.st), "scan");
+    uint32_t tot[6];
+    int mxh = 0;
+    if (b.status != FG_OK) return;
+    for (int i = 0; i < 6; i++)
+        b.check(cudaMemcpyAsync(&tot[i], p + i * pn + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, b.st), "copy");
+    b.check(cudaMemcpyAsync(&mxh, mx, sizeof(int), cudaMemcpyDeviceToHost, b.st), "copy");
+    b.check(cudaStreamSynchronize(b.st), "sync");
+    if (b.status != FG_OK) return;
+    v.n_low = (int32_t)tot[0];
+    v.n_mid = (int32_t)tot[1];
+    v.n_high = (int32_t)tot[2];
+    v.n_high_chunks = (int32_t)tot[3];
+    v.n_nz = (int32_t)tot[4];
+    v.n_zero = (int32_t)tot[5];
+    v.max_deg = mxh;
+    int32_t *low = b.alloc_graph<int32_t>(v.n_low);
+    int32_t *mid = b.alloc_graph<int32_t>(v.n_mid);
+    int2 *high = b.alloc_graph<int2>(v.n_high_chunks);
+    int32_t *nz = b.alloc_graph<int32_t>(v.n_nz);
+    int32_t *zero = b.alloc_graph<int32_t>(v.n_zero);
+    if (b.status != FG_OK) return;
+    k_bucket_write<<<grid_for(n), kBlock, 0, b.st>>>(n, v.row_off, p_low, p_mid, p_chunks, p_nz, p_zero, low,
+                                                     mid, high, nz, zero);
+    count_launch();
+    b.check(cudaGetLastError(), "bucket write");
+    v.low = low;
+    v.mid = mid;
+    v.high = high;
+    v.nz = nz;
+    v.zero = zero;
+    cudaFreeAsync(f, b.st);
+    cudaFreeAsync(p, b.st);
+    cudaFreeAsync(mx, b.st);
+}
+
+template <typename T>
+const T *to_device(Builder &b, const T *p, int64_t count, T **tmp) {
+    *tmp = nullptr;
+    if (count == 0 || p == nullptr) return p;
+    if (is_device_pointer(p)) return p;
+    T *d = b.alloc_tmp<T>(count);
+    if (!d) return nullptr;
+    b.check(cudaMemcpyAsync(d, p, (size_t)count * sizeof(T), cudaMemcpyHostToDevice, b.st), "copy to device");
+    *tmp = d;
+    return d;
+}
+
+}  // namespace
+
+// Builds a graph from COO (row_off_in == nullptr) or from CSR (row_off_in,
+// with src == nullptr and dst == col).
+fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                               const int32_t *w, bool from_csr, const int64_t *row_off_in,
+                               fg_graph **out) {
+    fg_graph *g = new (std::nothrow) fg_graph();
+    if (!g) return fail(FG_ERR_OUT_OF_MEMORY, "host allocation failed");
+    cudaGetDevice(&g->device);
+    Builder b{g, (cudaStream_t)0};
+    int32_t *t_src = nullptr, *t_dst = nullptr, *t_w = nullptr;
+    int64_t *t_ro = nullptr;
+    const int32_t *d_src = nullptr;
+    const int32_t *d_dst = to_device(b, dst, m, &t_dst);
+    const int32_t *d_w = to_device(b, w, m, &t_w);
+    const int64_t *d_ro = nullptr;
+    if (from_csr) d_ro = to_device(b, row_off_in, (int64_t)n + 1, &t_ro);
+    else d_src = to_device(b, src, m, &t_src);
+    int *flags = b.alloc_tmp<int>(1);
+    if (b.status == FG_OK) {
+        b.check(cudaMemsetAsync(flags, 0, sizeof(int), b.st), "memset");
+        if (from_csr)
+            k_validate_csr<<<grid_for(std::max<int64_t>(m, n)), kBlock, 0, b.st>>>(n, m, d_ro, d_dst, d_w, flags);
+        else if (m > 0)
+            k_validate_coo<<<grid_for(m), kBlock, 0, b.st>>>(m, n, d_src, d_dst, d_w, flags);
+        if (from_csr || m > 0) count_launch();
+        b.check(cudaGetLastError(), "validate");
+        int hf = 0;
+        b.check(cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, b.st), "copy");
+        b.check(cudaStreamSynchronize(b.st), "sync");
+        if (b.status == FG_OK && hf) {
+            if (hf & kBadOffsets) { b.status = FG_ERR_INVALID_ARG; b.msg = "row offsets are not a valid CSR (row_off[0]=0, non-decreasing, row_off[n]=m)"; }
+            else if (hf & kBadId) { b.status = FG_ERR_INVALID_ARG; b.msg = "a vertex id is outside [0, n)"; }
+            else { b.status = FG_ERR_NEGATIVE_WEIGHT; b.msg = "a weight is negative"; }
+        }
+    }
+    View &v = g->g;
+    v.n = n;
+    v.m = m;
+    uint32_t *ro = b.alloc_graph<uint32_t>((int64_t)n + 1);
+    int32_t *col = b.alloc_graph<int32_t>(m);
+    int32_t *wt = b.alloc_graph<int32_t>(m);
+    int32_t *esrc = b.alloc_graph<int32_t>(m);
+    if (b.status == FG_OK) {
+        if (from_csr) {
+            k_offsets_to_u32<<<grid_for((int64_t)n + 1), kBlock, 0, b.st>>>(n, d_ro, ro);
+            count_launch();
+            if (m > 0) {
+                b.check(cudaMemcpyAsync(col, d_dst, m * sizeof(int32_t), cudaMemcpyDeviceToDevice, b.st), "copy");
+                if (d_w) b.check(cudaMemcpyAsync(wt, d_w, m * sizeof(int32_t), cudaMemcpyDeviceToDevice, b.st), "copy");
+                else { k_fill_ones<<<grid_for(m), kBlock, 0, b.st>>>(m, wt); count_launch(); }
+                k_src_from_rows<<<grid_for((int64_t)n * 32), kBlock, 0, b.st>>>(n, ro, esrc);
+                count_launch();
+            }
+        } else {
+            uint32_t *cnt = b.alloc_tmp<uint32_t>(n);
+            uint32_t *cursor = b.alloc_tmp<uint32_t>((int64_t)n + 1);
+            if (b.status == FG_OK) {
+                b.check(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(uint32_t), b.st), "memset");
+                if (m > 0) { k_histogram<<<grid_for(m), kBlock, 0, b.st>>>(m, d_src, cnt); count_launch(); }
+                b.check(exclusive_scan(cnt, ro, n, b.st), "scan");
+                b.check(cudaMemcpyAsync(cursor, ro, ((size_t)n + 1) * sizeof(uint32_t), cudaMemcpyDeviceToDevice, b.st), "copy");
+                if (m > 0) { k_scatter_coo<<<grid_for(m), kBlock, 0, b.st>>>(m, d_src, d_dst, d_w, cursor, col, wt, esrc); count_launch(); }
+                b.check(cudaGetLastError(), "scatter");
+            }
+            if (cnt) cudaFreeAsync(cnt, b.st);
+            if (cursor) cudaFreeAsync(cursor, b.st);
+        }
+        b.check(cudaGetLastError(), "csr");
+    }
+    v.row_off = ro;
+    v.col = col;
+    v.w = wt;
+    v.src = esrc;
+    if (b.status == FG_OK) make_buckets(b, v);
+
+    // symmetrised view: every edge u->v also stored as v->u
+    View &s = g->s;
+    s.n = n;
+    s.m = 2 * m;
+    uint32_t *sro = b.alloc_graph<uint32_t>((int64_t)n + 1);
+    int32_t *scol = b.alloc_graph<int32_t>(2 * m);
+    int32_t *ssrc = b.alloc_graph<int32_t>(2 * m);
+    if (b.status == FG_OK) {
+        uint32_t *deg = b.alloc_tmp<uint32_t>(n);
+        uint32_t *cursor = b.alloc_tmp<uint32_t>((int64_t)n + 1);
+        if (b.status == FG_OK) {
+            b.check(cudaMemsetAsync(deg, 0, (size_t)n * sizeof(uint32_t), b.st), "memset");
+            if (m > 0) { k_histogram<<<grid_for(m), kBlock, 0, b.st>>>(m, col, deg); count_launch(); }
+            k_sym_degree<<<grid_for(n), kBlock, 0, b.st>>>(n, ro, deg);
+            count_launch();
+            b.check(exclusive_scan(deg, sro, n, b.st), "scan");
+            b.check(cudaMemcpyAsync(cursor, sro, ((size_t)n + 1) * sizeof(uint32_t), cudaMemcpyDeviceToDevice, b.st), "copy");
+            if (m > 0) { k_scatter_sym<<<grid_for(m), kBlock, 0, b.st>>>(m, esrc, col, cursor, scol, ssrc); count_launch(); }
+            b.check(cudaGetLastError(), "symmetrise");
+        }
+        if (deg) cudaFreeAsync(deg, b.st);
+        if (cursor) cudaFreeAsync(cursor, b.st);
+    }
+    s.row_off = sro;
+    s.col = scol;
+    s.w = nullptr;
+    s.src = ssrc;
+    if (b.status == FG_OK) make_buckets(b, s);
+
+    if (t_src) cudaFreeAsync(t_src, b.st);
+    if (t_dst) cudaFreeAsync(t_dst, b.st);
+    if (t_w) cudaFreeAsync(t_w, b.st);
+    if (t_ro) cudaFreeAsync(t_ro, b.st);
+    if (flags) cudaFreeAsync(flags, b.st);
+    b.check(cudaStreamSynchronize(b.st), "graph build");
+    if (b.status != FG_OK) {
+        fg_status st = b.status;
+        std::string msg = b.msg;
+        for (int i = 0; i < g->n_allocs; i++) cudaFree(g->allocs[i]);
+        delete g;
+        return fail(st, msg);
+    }
+    fg_graph_info_t &I = g->info;
+    I.n = n;
+    I.m = m;
+    I.m_sym = 2 * m;
+    I.max_out_degree = v.max_deg;
+    I.n_zero_out = n - v.n_nz;
+    I.n_low = v.n_low;
+    I.n_mid = v.n_mid;
+    I.n_high = v.n_high;
+    I.n_high_chunks = v.n_high_chunks;
+    I.n_isolated = s.n_zero;
+    *out = g;
+    return FG_OK;
+}
+
+}  // namespace fg

@@ -1,0 +1,253 @@
+// extern "C" entry points of include/fg.h: argument checks, error plumbing,
+// and the runtime mode selection.
+#include <atomic>
+#include <cstdio>
+#include <new>
+#include <string>
+
+#include "fg_internal.cuh"
+
+namespace fg {
+
+namespace {
+thread_local std::string t_last_error;
+
+// Default device memory pool: keep freed blocks for reuse by later queries
+// instead of returning them to the driver after every synchronisation.
+void configure_pool_once(int dev) {
+    static std::mutex mu;
+    static bool done[64] = {};
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64 || done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t threshold = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+    }
+    cudaGetLastError();
+    done[dev] = true;
+}
+
+bool ensure_device(int *dev) {
+    int d = -1;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    configure_pool_once(d);
+    if (dev) *dev = d;
+    return true;
+}
+}  // namespace
+
+void set_last_error(const std::string &msg) { t_last_error = msg; }
+const char *last_error_cstr() { return t_last_error.c_str(); }
+
+fg_status fail(fg_status code, const std::string &msg) {
+    t_last_error = msg;
+    return code;
+}
+
+fg_status cuda_fail(cudaError_t e, const char *what) {
+    cudaGetLastError();
+    fg_status code = (e == cudaErrorMemoryAllocation) ? FG_ERR_OUT_OF_MEMORY : FG_ERR_CUDA;
+    return fail(code, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+}
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+bool is_device_pointer(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace fg
+
+using namespace fg;
+
+namespace {
+
+fg_status check_mode(fg_mode m) {
+    if (m < FG_VERTEX_SYNC || m > FG_AUTO) return fail(FG_ERR_INVALID_ARG, "invalid mode");
+    return FG_OK;
+}
+
+fg_status resolve_mode(const fg_graph *g, fg_algo algo, fg_mode m, Mode *out) {
+    if (m == FG_AUTO) {
+        fg_mode sel;
+        fg_status s = fg_select_mode(g, algo, &sel);
+        if (s != FG_OK) return s;
+        m = sel;
+    }
+    *out = (Mode)m;
+    return FG_OK;
+}
+
+fg_status query(const fg_graph *g, fg_algo algo, int32_t src, int32_t *out, fg_mode mode,
+                const fg_options *opt, fg_stats *stats) {
+    if (!g) return fail(FG_ERR_INVALID_ARG, "graph is NULL");
+    if (!out) return fail(FG_ERR_INVALID_ARG, "output buffer is NULL");
+    if (algo < FG_ALGO_SSSP || algo > FG_ALGO_CC) return fail(FG_ERR_INVALID_ARG, "invalid algorithm");
+    fg_status s = check_mode(mode);
+    if (s != FG_OK) return s;
+    if (algo != FG_ALGO_CC && (src < 0 || src >= g->info.n))
+        return fail(FG_ERR_INVALID_ARG, "source vertex outside [0, n)");
+    if (opt && (opt->max_rounds < 0 || opt->wait_timeout_ms < 0 || opt->blocks_per_sm < 0))
+        return fail(FG_ERR_INVALID_ARG, "negative option");
+    int dev;
+    if (!ensure_device(&dev)) return fail(FG_ERR_CUDA, "no CUDA device");
+    Mode m;
+    s = resolve_mode(g, algo, mode, &m);
+    if (s != FG_OK) return s;
+    return run_query(g, (Algo)algo, m, src, out, opt, stats);
+}
+
+}  // namespace
+
+extern "C" {
+
+fg_status fg_graph_create_coo(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                              const int32_t *w, fg_graph **out) {
+    if (!out) return fail(FG_ERR_INVALID_ARG, "out is NULL");
+    if (n <= 0) return fail(FG_ERR_INVALID_ARG, "n must be positive");
+    if (m < 0) return fail(FG_ERR_INVALID_ARG, "m must be non-negative");
+    if (m >= ((int64_t)1 << 31)) return fail(FG_ERR_INVALID_ARG, "m must be below 2^31 (the symmetrised copy uses 32-bit offsets)");
+    if (m > 0 && (!src || !dst)) return fail(FG_ERR_INVALID_ARG, "src or dst is NULL");
+    if (!ensure_device(nullptr)) return fail(FG_ERR_CUDA, "no CUDA device");
+    return build_graph_from_coo(n, m, src, dst, w, false, nullptr, out);
+}
+
+fg_status fg_graph_create_csr(int32_t n, int64_t m, const int64_t *row_off, const int32_t *col,
+                              const int32_t *w, fg_graph **out) {
+    if (!out) return fail(FG_ERR_INVALID_ARG, "out is NULL");
+    if (n <= 0) return fail(FG_ERR_INVALID_ARG, "n must be positive");
+    if (m < 0) return fail(FG_ERR_INVALID_ARG, "m must be non-negative");
+    if (m >= ((int64_t)1 << 31)) return fail(FG_ERR_INVALID_ARG, "m must be below 2^31 (the symmetrised copy uses 32-bit offsets)");
+    if (!row_off) return fail(FG_ERR_INVALID_ARG, "row_off is NULL");
+    if (m > 0 && !col) return fail(FG_ERR_INVALID_ARG, "col is NULL");
+    if (!ensure_device(nullptr)) return fail(FG_ERR_CUDA, "no CUDA device");
+    return build_graph_from_coo(n, m, nullptr, col, w, true, row_off, out);
+}
+
+fg_status fg_graph_destroy(fg_graph *g) {
+    if (!g) return FG_OK;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != g->device) cudaSetDevice(g->device);
+    for (int i = 0; i < g->n_allocs; i++) cudaFreeAsync(g->allocs[i], 0);
+    cudaError_t e = cudaStreamSynchronize(0);
+    if (dev != g->device && dev >= 0) cudaSetDevice(dev);
+    delete g;
+    if (e != cudaSuccess) return cuda_fail(e, "graph destroy");
+    return FG_OK;
+}
+
+fg_status fg_graph_info(const fg_graph *g, fg_graph_info_t *out) {
+    if (!g || !out) return fail(FG_ERR_INVALID_ARG, "NULL argument");
+    *out = g->info;
+    return FG_OK;
+}
+
+fg_status fg_sssp(const fg_graph *g, int32_t src, int32_t *dist_out, fg_mode mode) {
+    return query(g, FG_ALGO_SSSP, src, dist_out, mode, nullptr, nullptr);
+}
+
+fg_status fg_bfs(const fg_graph *g, int32_t src, int32_t *level_out, fg_mode mode) {
+    return query(g, FG_ALGO_BFS, src, level_out, mode, nullptr, nullptr);
+}
+
+fg_status fg_cc(const fg_graph *g, int32_t *label_out, fg_mode mode) {
+    return query(g, FG_ALGO_CC, 0, label_out, mode, nullptr, nullptr);
+}
+
+fg_status fg_run(const fg_graph *g, fg_algo algo, int32_t src, int32_t *out, fg_mode mode,
+                 const fg_options *opt, fg_stats *stats) {
+    return query(g, algo, src, out, mode, opt, stats);
+}
+
+fg_status fg_sweep(const fg_graph *g, fg_mode mode, const int32_t *cur, int32_t *next, void *stream,
+                   int64_t *updates, float *kernel_ms) {
+    if (!g || !cur || !next) return fail(FG_ERR_INVALID_ARG, "NULL argument");
+    if (mode != FG_VERTEX_SYNC && mode != FG_EDGE_SYNC)
+        return fail(FG_ERR_INVALID_ARG, "a sweep is FG_VERTEX_SYNC or FG_EDGE_SYNC");
+    if (!ensure_device(nullptr)) return fail(FG_ERR_CUDA, "no CUDA device");
+    if (!is_device_pointer(cur) || !is_device_pointer(next))
+        return fail(FG_ERR_INVALID_ARG, "cur and next must be device memory");
+    return run_sweep(g, (Mode)mode, cur, next, (cudaStream_t)stream, updates, kernel_ms);
+}
+
+// Degree skew and diameter decide (Sec. 2 and Sec. 4.3 of the paper: edge-based
+// code wins on skewed graphs on the GPU, vertex-based on near-uniform ones; a
+// data-driven worklist pays off when many rounds have little work, i.e. on
+// high-diameter graphs).  The diameter estimate is the eccentricity of the
+// highest-degree vertex, from one BFS run and cached on the handle.
+fg_status fg_select_mode(const fg_graph *g, fg_algo algo, fg_mode *out) {
+    if (!g || !out) return fail(FG_ERR_INVALID_ARG, "NULL argument");
+    if (algo < FG_ALGO_SSSP || algo > FG_ALGO_CC) return fail(FG_ERR_INVALID_ARG, "invalid algorithm");
+    int32_t diam;
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        diam = g->diam_est;
+    }
+    if (diam < 0) {
+        // BFS from a vertex of the mid or high bucket if any, else vertex 0
+        int32_t n = g->info.n;
+        int32_t *level = nullptr;
+        if (!ensure_device(nullptr)) return fail(FG_ERR_CUDA, "no CUDA device");
+        cudaError_t e = cudaMalloc(&level, (size_t)n * sizeof(int32_t));
+        if (e != cudaSuccess) return cuda_fail(e, "select_mode workspace");
+        int32_t start = 0;
+        if (g->g.n_high_chunks > 0) {
+            int2 h;
+            cudaMemcpy(&h, g->g.high, sizeof(int2), cudaMemcpyDeviceToHost);
+            start = h.x;
+        } else if (g->g.n_mid > 0) {
+            cudaMemcpy(&start, g->g.mid, sizeof(int32_t), cudaMemcpyDeviceToHost);
+        } else if (g->g.n_low > 0) {
+            cudaMemcpy(&start, g->g.low, sizeof(int32_t), cudaMemcpyDeviceToHost);
+        }
+        fg_stats st{};
+        fg_status s = run_query(g, kBFS, kVertexAsync, start, level, nullptr, &st);
+        cudaFree(level);
+        if (s != FG_OK) return s;
+        diam = st.rounds;
+        std::lock_guard<std::mutex> lk(g->mu);
+        g->diam_est = diam;
+    }
+    double avg = g->info.n > 0 ? (double)g->info.m / g->info.n : 0.0;
+    bool skewed = g->info.max_out_degree > 64.0 * (avg > 1.0 ? avg : 1.0);
+    bool deep = diam > 64;
+    fg_mode m;
+    if (deep) m = skewed ? FG_EDGE_ASYNC : FG_VERTEX_ASYNC;
+    else m = skewed ? FG_EDGE_SYNC : FG_VERTEX_SYNC;
+    (void)algo;
+    *out = m;
+    return FG_OK;
+}
+
+const char *fg_last_error(void) { return fg::last_error_cstr(); }
+
+uint64_t fg_kernel_launches(void) { return fg::g_launches.load(std::memory_order_relaxed); }
+
+const char *fg_status_string(fg_status s) {
+    switch (s) {
+        case FG_OK: return "FG_OK";
+        case FG_ERR_INVALID_ARG: return "FG_ERR_INVALID_ARG";
+        case FG_ERR_NEGATIVE_WEIGHT: return "FG_ERR_NEGATIVE_WEIGHT";
+        case FG_ERR_OVERFLOW: return "FG_ERR_OVERFLOW";
+        case FG_ERR_OUT_OF_MEMORY: return "FG_ERR_OUT_OF_MEMORY";
+        case FG_ERR_TIMEOUT: return "FG_ERR_TIMEOUT";
+        case FG_ERR_CUDA: return "FG_ERR_CUDA";
+    }
+    return "FG_UNKNOWN_STATUS";
+}
+
+}  // extern "C"

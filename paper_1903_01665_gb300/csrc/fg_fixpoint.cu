@@ -1,0 +1,1034 @@
+// The fixpoint relaxation sweep (Sec. 2, Alg. 1-3) in the four variants of
+// Sec. 3.1-3.3, as persistent cooperative kernels: one launch runs init,
+// every round and the convergence test on the device.  Rounds are separated
+// by a grid barrier whose waits are bounded in time.
+//
+//   vertex-sync  : Alg. 1 -- every round scans the degree-bucketed vertex
+//                  lists (topology-driven) and expands the vertices that
+//                  changed in the previous round; reads cur, atomic MIN into
+//                  next (double-buffered, Jacobi), barrier, swap.
+//   edge-sync    : Alg. 2 -- every round streams all edges (src,dst,w) with
+//                  128-bit loads and relaxes those whose source changed.
+//   vertex-async : data-driven (Sec. 3.3) -- worklists of vertices by degree
+//                  class, in-place atomic MIN, changed targets appended with
+//                  warp-aggregated atomics, until the worklist is empty.
+//   edge-async   : the worklist's out-edges, load-balanced edge-parallel by a
+//                  prefix sum of the items' degrees, in place.
+//
+// BFS uses Alg. 3's level filter (dist == lev, plain store of lev+1); CC is
+// min-label propagation on the symmetrised graph plus pointer jumping
+// (label[v] = label[label[v]]).
+#include <algorithm>
+
+#include "fg_internal.cuh"
+
+namespace fg {
+
+namespace {
+
+struct Acc {
+    unsigned long long edges = 0, verts = 0, updates = 0, pushes = 0;
+    int changed = 0;
+    int overflow = 0;
+};
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T x) {
+    __shared__ T sh[kWarps];
+    x = warp_sum(x);
+    if (lane_id() == 0) sh[threadIdx.x >> 5] = x;
+    __syncthreads();
+    T r = 0;
+    if (threadIdx.x < 32) {
+        r = lane_id() < (unsigned)kWarps ? sh[lane_id()] : (T)0;
+        r = warp_sum(r);
+    }
+    __syncthreads();
+    return r;
+}
+
+// ================================================================ edge ops
+// Each op provides:
+//   active(u, val)  -- is u expanded this round; its value (may update state)
+//   own(u, val)     -- once per expanded vertex (sync: carry cur[u] into next)
+//   edge(e, val, a, v) -- relax edge e from a source with value val; returns
+//                      true if target v must be appended to the worklist.
+
+// Synchronous SSSP / CC: Jacobi round r reads cur, lowers next.
+template <int ALGO>
+struct SyncOp {
+    const int32_t *__restrict__ col;
+    const int32_t *__restrict__ w;
+    const int32_t *cur;
+    int32_t *next;
+    const int32_t *scur;
+    int32_t *snext;
+    int32_t r;
+
+    __device__ __forceinline__ bool active(int32_t u, int32_t &val) const {
+        if (ldcg(scur + u) != r) return false;
+        val = ldcg(cur + u);
+        return true;
+    }
+    __device__ __forceinline__ void own(int32_t u, int32_t val) const {
+        if (ldcg(next + u) > val) atomicMin(next + u, val);
+    }
+    __device__ __forceinline__ bool edge(uint32_t e, int32_t val, Acc &a, int32_t &v) const {
+        v = __ldg(col + e);
+        int32_t cand;
+        if (ALGO == kSSSP) {
+            uint32_t c = (uint32_t)val + (uint32_t)__ldg(w + e);
+            if (c >= (uint32_t)kInf) { a.overflow = 1; return false; }
+            cand = (int32_t)c;
+        } else {
+            cand = val;
+        }
+        if (cand < ldcg(cur + v)) {
+            int32_t old = atomicMin(next + v, cand);
+            if (old > cand) {
+                stcg(snext + v, r + 1);
+                a.changed++;
+                a.updates++;
+            }
+        }
+        return false;
+    }
+};
+
+// Level-synchronous BFS (Alg. 3): in place, filter dist == lev.
+struct BfsSyncOp {
+    const int32_t *__restrict__ col;
+    int32_t *L;
+    int32_t lev;
+
+    __device__ __forceinline__ bool active(int32_t u, int32_t &val) const {
+        val = lev;
+        return ldcg(L + u) == lev;
+    }
+    __device__ __forceinline__ void own(int32_t, int32_t) const {}
+    __device__ __forceinline__ bool edge(uint32_t e, int32_t, Acc &a, int32_t &v) const {
+        v = __ldg(col + e);
+        if (ldcg(L + v) > lev + 1) {
+            stcg(L + v, lev + 1);
+            a.changed++;
+            a.updates++;
+        }
+        return false;
+    }
+};
+
+// Asynchronous SSSP / CC: in place, push on decrease, dedup by generation stamp.
+template <int ALGO>
+struct AsyncOp {
+    const int32_t *__restrict__ col;
+    const int32_t *__restrict__ w;
+    int32_t *D;
+    int32_t *stamp;
+    int32_t gen;
+
+    __device__ __forceinline__ bool active(int32_t u, int32_t &val) const {
+        val = ldcg(D + u);
+        if (ALGO == kCC) {
+            // pointer jumping: follow label[label[...]] while it decreases
+            int32_t l = val;
+#pragma unroll 1
+            for (int k = 0; k < 8; k++) {
+                int32_t ll = ldcg(D + l);
+                if (ll >= l) break;
+                l = ll;
+            }
+            if (l < val) {
+                atomicMin(D + u, l);
+                val = l;
+            }
+        }
+        return true;
+    }
+    __device__ __forceinline__ void own(int32_t, int32_t) const {}
+    __device__ __forceinline__ bool edge(uint32_t e, int32_t val, Acc &a, int32_t &v) const {
+        v = __ldg(col + e);
+        int32_t cand;
+        if (ALGO == kSSSP) {
+            uint32_t c = (uint32_t)val + (uint32_t)__ldg(w + e);
+            if (c >= (uint32_t)kInf) { a.overflow = 1; return false; }
+            cand = (int32_t)c;
+        } else {
+            cand = val;
+        }
+        if (cand < ldcg(D + v)) {
+            int32_t old = atomicMin(D + v, cand);
+            if (old > cand) {
+                a.updates++;
+                return atomicExch(stamp + v, gen + 1) != gen + 1;
+            }
+        }
+        return false;
+    }
+};
+
+// Asynchronous BFS: frontier queue; a vertex is claimed once by CAS from INF.
+struct BfsAsyncOp {
+    const int32_t *__restrict__ col;
+    int32_t *L;
+    int32_t gen;
+
+    __device__ __forceinline__ bool active(int32_t, int32_t &val) const {
+        val = gen;
+        return true;
+    }
+    __device__ __forceinline__ void own(int32_t, int32_t) const {}
+    __device__ __forceinline__ bool edge(uint32_t e, int32_t, Acc &a, int32_t &v) const {
+        v = __ldg(col + e);
+        if (ldcg(L + v) != kInf) return false;
+        if (atomicCAS(L + v, kInf, gen + 1) == kInf) {
+            a.updates++;
+            return true;
+        }
+        return false;
+    }
+};
+
+// One full sweep with every vertex active (roofline measurement).
+struct SweepOp {
+    const int32_t *__restrict__ col;
+    const int32_t *__restrict__ w;
+    const int32_t *cur;
+    int32_t *next;
+
+    __device__ __forceinline__ bool active(int32_t u, int32_t &val) const {
+        val = ldcg(cur + u);
+        return val != kInf;
+    }
+    __device__ __forceinline__ void own(int32_t, int32_t) const {}
+    __device__ __forceinline__ bool edge(uint32_t e, int32_t val, Acc &a, int32_t &v) const {
+        v = __ldg(col + e);
+        uint32_t c = (uint32_t)val + (uint32_t)__ldg(w + e);
+        if (c >= (uint32_t)kInf) { a.overflow = 1; return false; }
+        int32_t cand = (int32_t)c;
+        if (cand < ldcg(next + v)) {
+            int32_t old = atomicMin(next + v, cand);
+            if (old > cand) a.updates++;
+        }
+        return false;
+    }
+};
+
+// ================================================================ appenders
+struct NoPush {
+    __device__ __forceinline__ void operator()(bool, int32_t, Acc &) const {}
+};
+
+// vertex-async: append to the class list of the target's out-degree
+struct ClassPush {
+    const uint32_t *__restrict__ row_off;
+    int32_t *low, *mid;
+    int2 *high;
+    int *size;          // [3]
+    int32_t cap_low, cap_mid, cap_high;
+    Ctrl *c;
+
+    __device__ __forceinline__ void operator()(bool want, int32_t v, Acc &a) const {
+        int cls = -1;
+        uint32_t b = 0, d = 0;
+        if (want) {
+            b = __ldg(row_off + v);
+            d = __ldg(row_off + v + 1) - b;
+            cls = d == 0 ? -1 : d < (uint32_t)kLowMax ? kWlLow : d < (uint32_t)kMidMax ? kWlMid : kWlHigh;
+            if (cls >= 0) a.pushes++;
+        }
+        warp_append(0xffffffffu, cls == kWlLow, v, low, &size[kWlLow], cap_low, c);
+        warp_append(0xffffffffu, cls == kWlMid, v, mid, &size[kWlMid], cap_mid, c);
+        if (cls == kWlHigh) {
+            int nck = (int)((d + kChunk - 1) / kChunk);
+            int base = atomicAdd(&size[kWlHigh], nck);
+            if (base + nck <= cap_high) {
+                for (int k = 0; k < nck; k++) high[base + k] = make_int2(v, (int32_t)(b + (uint32_t)k * kChunk));
+            } else {
+                atomicOr(&c->status, kStWorklist);
+            }
+        }
+    }
+};
+
+// edge-async: one list of vertices with >= 1 out-edge
+struct ListPush {
+    const uint32_t *__restrict__ row_off;
+    int32_t *list;
+    int *size;
+    int32_t cap;
+    Ctrl *c;
+
+    __device__ __forceinline__ void operator()(bool want, int32_t v, Acc &a) const {
+        bool ok = false;
+        if (want) {
+            ok = __ldg(row_off + v + 1) > __ldg(row_off + v);
+            if (ok) a.pushes++;
+        }
+        warp_append(0xffffffffu, ok, v, list, size, cap, c);
+    }
+};
+
+// ================================================================ expansions
+// Bucketed vertex expansion: high chunks by whole CTAs, mid vertices by warps,
+// low vertices by threads with the warp's edges redistributed over its lanes
+// (a warp-wide prefix sum of the degrees; each lane finds the owner of its
+// edge by a 5-step shuffle search), so edge loads are contiguous.
+template <class OP, class PUSH>
+__device__ __forceinline__ void expand_vertices(const uint32_t *__restrict__ row_off, const int32_t *low,
+                                                int n_low, const int32_t *mid, int n_mid, const int2 *high,
+                                                int n_high, const OP &op, const PUSH &push, Acc &a) {
+    __shared__ int32_t s_val;
+    __shared__ int s_act;
+    const unsigned lane = lane_id();
+    // high-degree chunks: one CTA per 2048-edge chunk
+    for (int ci = blockIdx.x; ci < n_high; ci += gridDim.x) {
+        int2 ch;
+        ch.x = ldcg(&high[ci].x);
+        ch.y = ldcg(&high[ci].y);
+        uint32_t rb = __ldg(row_off + ch.x), re = __ldg(row_off + ch.x + 1);
+        if (threadIdx.x == 0) {
+            int32_t val = 0;
+            bool act = op.active(ch.x, val);
+            if (act && (uint32_t)ch.y == rb) {
+                op.own(ch.x, val);
+                a.verts++;
+            }
+            s_act = act;
+            s_val = val;
+        }
+        __syncthreads();
+        if (s_act) {
+            int32_t val = s_val;
+            uint32_t e0 = (uint32_t)ch.y, e1 = min(e0 + (uint32_t)kChunk, re);
+            if (threadIdx.x == 0) a.edges += e1 - e0;
+            for (uint32_t base = e0; base < e1; base += kBlock) {
+                uint32_t e = base + threadIdx.x;
+                int32_t v = 0;
+                bool want = false;
+                if (e < e1) want = op.edge(e, val, a, v);
+                push(want, v, a);
+            }
+        }
+        __syncthreads();
+    }
+    const int gw = (int)((blockIdx.x * (unsigned)kBlock + threadIdx.x) >> 5);
+    const int nw = (int)(gridDim.x * (unsigned)kWarps);
+    // mid-degree vertices: one warp each
+    for (int i = gw; i < n_mid; i += nw) {
+        int32_t u = ldcg(mid + i);
+        int32_t val = 0;
+        int act = 0;
+        if (lane == 0) {
+            act = op.active(u, val);
+            if (act) op.own(u, val);
+        }
+        act = __shfl_sync(0xffffffffu, act, 0);
+        if (!act) continue;
+        val = __shfl_sync(0xffffffffu, val, 0);
+        uint32_t b = __ldg(row_off + u), e = __ldg(row_off + u + 1);
+        if (lane == 0) {
+            a.verts++;
+            a.edges += e - b;
+        }
+        for (uint32_t base = b; base < e; base += 32) {
+            uint32_t k = base + lane;
+            int32_t v = 0;
+            bool want = false;
+            if (k < e) want = op.edge(k, val, a, v);
+            push(want, v, a);
+        }
+    }
+    // low-degree vertices: a thread each, edges redistributed over the warp
+    for (int base = gw * 32; base < n_low; base += nw * 32) {
+        int i = base + (int)lane;
+        int32_t val = 0;
+        uint32_t rb = 0, d = 0;
+        if (i < n_low) {
+            int32_t u = ldcg(low + i);
+            if (op.active(u, val)) {
+                op.own(u, val);
+                rb = __ldg(row_off + u);
+                d = __ldg(row_off + u + 1) - rb;
+                a.verts++;
+            }
+        }
+        uint32_t incl = warp_inclusive_scan(d);
+        uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t excl = incl - d;
+        if (lane == 0) a.edges += total;
+        for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+            uint32_t k = k0 + lane;
+            int owner = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                uint32_t pv = __shfl_sync(0xffffffffu, incl, owner + step - 1);
+                if (pv <= k) owner += step;
+            }
+            uint32_t ob = __shfl_sync(0xffffffffu, rb, owner);
+            uint32_t oe = __shfl_sync(0xffffffffu, excl, owner);
+            int32_t ov = __shfl_sync(0xffffffffu, val, owner);
+            int32_t v = 0;
+            bool want = false;
+            if (k < total) want = op.edge(ob + (k - oe), ov, a, v);
+            push(want, v, a);
+        }
+    }
+}
+
+// Edge-parallel sweep over the source-sorted COO with 128-bit loads of src
+// (four edges per load); the activity test of a source is reused across
+// consecutive edges of the same source.
+template <class OP>
+__device__ __forceinline__ void expand_edges(const int32_t *__restrict__ src, int64_t m, const OP &op,
+                                             Acc &a) {
+    const int64_t tid = blockIdx.x * (int64_t)kBlock + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * kBlock;
+    const int64_t m4 = m >> 2;
+    const int4 *src4 = reinterpret_cast<const int4 *>(src);
+    for (int64_t q = tid; q < m4; q += nth) {
+        int4 s = __ldg(src4 + q);
+        int32_t us[4] = {s.x, s.y, s.z, s.w};
+        int32_t prev = -1, pval = 0;
+        bool pact = false;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            int32_t u = us[j];
+            if (u != prev) {
+                pact = op.active(u, pval);
+                prev = u;
+            }
+            if (pact) {
+                int32_t v;
+                op.edge((uint32_t)(4 * q + j), pval, a, v);
+                a.edges++;
+            }
+        }
+    }
+    for (int64_t e = 4 * m4 + tid; e < m; e += nth) {
+        int32_t val;
+        int32_t u = __ldg(src + e);
+        if (op.active(u, val)) {
+            int32_t v;
+            op.edge((uint32_t)e, val, a, v);
+            a.edges++;
+        }
+    }
+}
+
+// Load-balanced expansion of a vertex worklist to its out-edges (edge-async).
+// Phase 1 (before the caller's grid barrier): each CTA takes a contiguous
+// slice of the worklist and writes the exclusive prefix sum of its items'
+// degrees (lb_off) and its slice total (lb_blk).
+__device__ __forceinline__ void lb_prefix(const uint32_t *__restrict__ row_off, const int32_t *items, int n_items,
+                                          uint32_t *lb_off, uint32_t *lb_blk) {
+    __shared__ uint32_t s_tot;
+    __shared__ uint32_t warp_tot[kWarps];
+    int S = (n_items + gridDim.x - 1) / gridDim.x;
+    int lo = min(n_items, (int)blockIdx.x * S), hi = min(n_items, lo + S);
+    uint32_t run = 0;
+    for (int t0 = lo; t0 < hi; t0 += kBlock) {
+        int i = t0 + threadIdx.x;
+        uint32_t d = 0;
+        if (i < hi) {
+            int32_t u = ldcg(items + i);
+            d = __ldg(row_off + u + 1) - __ldg(row_off + u);
+        }
+        uint32_t inc = warp_inclusive_scan(d);
+        int wid = threadIdx.x >> 5;
+        if (lane_id() == 31) warp_tot[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            uint32_t t = lane_id() < (unsigned)kWarps ? warp_tot[lane_id()] : 0u;
+            uint32_t ti = warp_inclusive_scan(t);
+            if (lane_id() < (unsigned)kWarps) warp_tot[lane_id()] = ti - t;
+            if (lane_id() == kWarps - 1) s_tot = ti;
+        }
+        __syncthreads();
+        if (i < hi) lb_off[i] = run + warp_tot[wid] + inc - d;
+        run += s_tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) lb_blk[blockIdx.x] = run;
+}
+
+constexpr int kMaxGrid = 152 * 8;   // persistent CTAs (lb prefix table size)
+constexpr int kLbEdgesPerThread = 4;
+
+// Phase 2 (after the barrier): the edge space [0, T) is split evenly over the
+// CTAs; each CTA walks its range in tiles, staging up to kBlock items'
+// offsets, row starts and values in shared memory, and every thread finds the
+// owner of its edges by binary search in shared memory.
+template <class OP, class PUSH>
+__device__ __forceinline__ void lb_expand(const uint32_t *__restrict__ row_off, const int32_t *items, int n_items,
+                                          const uint32_t *lb_off, const uint32_t *lb_blk, const OP &op,
+                                          const PUSH &push, Acc &a) {
+    __shared__ uint32_t sP[kMaxGrid + 1];
+    __shared__ uint32_t s_goff[kBlock + 1];
+    __shared__ uint32_t s_rb[kBlock];
+    __shared__ int32_t s_val[kBlock];
+    __shared__ int s_i0;
+    __shared__ uint32_t s_t1;
+    const int G = gridDim.x;
+    // exclusive scan of the slice totals, redundantly in every CTA
+    {
+        __shared__ uint32_t warp_tot[kWarps];
+        __shared__ uint32_t carry;
+        if (threadIdx.x == 0) carry = 0;
+        __syncthreads();
+        for (int t0 = 0; t0 < G; t0 += kBlock) {
+            int i = t0 + threadIdx.x;
+            uint32_t x = i < G ? ldcg((const int32_t *)lb_blk + i) : 0u;
+            uint32_t inc = warp_inclusive_scan(x);
+            int wid = threadIdx.x >> 5;
+            if (lane_id() == 31) warp_tot[wid] = inc;
+            __syncthreads();
+            if (wid == 0) {
+                uint32_t t = lane_id() < (unsigned)kWarps ? warp_tot[lane_id()] : 0u;
+                uint32_t ti = warp_inclusive_scan(t);
+                if (lane_id() < (unsigned)kWarps) warp_tot[lane_id()] = ti - t;
+            }
+            __syncthreads();
+            if (i < G) sP[i] = carry + warp_tot[wid] + inc - x;
+            __syncthreads();
+            if (threadIdx.x == kBlock - 1) carry += warp_tot[wid] + inc;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) sP[G] = carry;
+        __syncthreads();
+    }
+    const uint32_t T = sP[G];
+    if (T == 0) return;
+    const int S = (n_items + G - 1) / G;
+    const uint64_t lo = (uint64_t)T * blockIdx.x / G, hi = (uint64_t)T * (blockIdx.x + 1) / G;
+    if (lo >= hi) return;
+    // global offset of item i
+    auto goff = [&](int i) -> uint32_t { return sP[i / S] + (uint32_t)ldcg((const int32_t *)lb_off + i); };
+    if (threadIdx.x == 0) {
+        // item containing edge lo: last item with goff <= lo
+        int l = 0, r = n_items - 1;
+        while (l < r) {
+            int mdl = (l + r + 1) >> 1;
+            if (goff(mdl) <= (uint32_t)lo) l = mdl; else r = mdl - 1;
+        }
+        s_i0 = l;
+    }
+    __syncthreads();
+    uint32_t t0 = (uint32_t)lo;
+    while (t0 < (uint32_t)hi) {
+        int i0 = s_i0;
+        int cnt = min(kBlock, n_items - i0);
+        if ((int)threadIdx.x < cnt) {
+            int i = i0 + threadIdx.x;
+            int32_t u = ldcg(items + i);
+            s_goff[threadIdx.x] = goff(i);
+            s_rb[threadIdx.x] = __ldg(row_off + u);
+            int32_t val = 0;
+            op.active(u, val);
+            s_val[threadIdx.x] = val;
+        }
+        if (threadIdx.x == 0) s_goff[cnt] = (i0 + cnt < n_items) ? goff(i0 + cnt) : T;
+        __syncthreads();
+        uint32_t t1 = min((uint32_t)hi, min(t0 + (uint32_t)(kBlock * kLbEdgesPerThread), s_goff[cnt]));
+#pragma unroll
+        for (int j = 0; j < kLbEdgesPerThread; j++) {
+            uint32_t x = t0 + j * kBlock + threadIdx.x;
+            bool in = x < t1;
+            int32_t v = 0;
+            bool want = false;
+            if (in) {
+                int l = 0, r = cnt - 1;
+                while (l < r) {
+                    int mdl = (l + r + 1) >> 1;
+                    if (s_goff[mdl] <= x) l = mdl; else r = mdl - 1;
+                }
+                want = op.edge(s_rb[l] + (x - s_goff[l]), s_val[l], a, v);
+                a.edges++;
+            }
+            push(want, v, a);
+        }
+        if (threadIdx.x == 0) {
+            // next tile starts at edge t1; find its item among the staged ones
+            int l = 0, r = cnt;   // s_goff[cnt] may equal t1 (then item i0 + cnt)
+            while (l < r) {
+                int mdl = (l + r + 1) >> 1;
+                if (s_goff[mdl] <= t1) l = mdl; else r = mdl - 1;
+            }
+            s_i0 = i0 + l;
+            s_t1 = t1;
+        }
+        __syncthreads();
+        t0 = s_t1;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) a.verts += 0;
+}
+
+// ================================================================ the kernel
+template <int ALGO, int MODE>
+__global__ void __launch_bounds__(kBlock) fixpoint_kernel(Params p) {
+    constexpr bool SYNC = (MODE == kVertexSync || MODE == kEdgeSync);
+    Ctrl *c = p.ctrl;
+    const View &g = p.g;
+    const int32_t n = g.n;
+    const int64_t tid = blockIdx.x * (int64_t)kBlock + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * kBlock;
+    Acc a;
+    int rounds = 0;
+
+    // ---- init: values, stamps, initial worklist (a2)
+    for (int64_t v = tid; v < n; v += nth) {
+        int32_t x = (ALGO == kCC) ? (int32_t)v : (v == p.source ? 0 : kInf);
+        p.A[v] = x;
+        if (SYNC && ALGO != kBFS) {
+            p.B[v] = x;
+            p.S1[v] = (ALGO == kCC || v == p.source) ? 1 : 0;   // active in round 1
+            p.S0[v] = 0;
+        }
+        if (!SYNC && ALGO != kBFS) p.S0[v] = 0;
+    }
+    if (!SYNC && ALGO != kCC && tid == 0) {
+        int32_t s = p.source;
+        uint32_t b = g.row_off[s], d = g.row_off[s + 1] - b;
+        if (d > 0) {
+            if (MODE == kEdgeAsync) {
+                p.wl[0][0][0] = s;
+                c->wl_size[0][0] = 1;
+            } else if (d < (uint32_t)kLowMax) {
+                p.wl[0][kWlLow][0] = s;
+                c->wl_size[0][kWlLow] = 1;
+            } else if (d < (uint32_t)kMidMax) {
+                p.wl[0][kWlMid][0] = s;
+                c->wl_size[0][kWlMid] = 1;
+            } else {
+                int nck = (int)((d + kChunk - 1) / kChunk);
+                int2 *h = reinterpret_cast<int2 *>(p.wl[0][kWlHigh]);
+                for (int k = 0; k < nck; k++) h[k] = make_int2(s, (int32_t)(b + (uint32_t)k * kChunk));
+                c->wl_size[0][kWlHigh] = nck;
+            }
+        }
+    }
+    // failure-detection test: CTA 0 never arrives, the others' waits run out
+    if (p.inject_missing_arrival && blockIdx.x == 0) return;
+    bool ok = grid_sync(c, p.timeout_ns);
+
+    if (SYNC && ok) {
+        int pass_ctr = 0;
+        for (int r = 1;; r++) {
+            if (r > p.max_rounds) {
+                if (tid == 0) atomicOr(&c->status, kStRoundCap);
+                break;
+            }
+            if (tid == 0) c->changed[(r + 1) % 3] = 0;
+            rounds = r;
+            if (ALGO == kBFS) {
+                BfsSyncOp op{g.col, p.A, r - 1};
+                if (MODE == kVertexSync)
+                    expand_vertices(g.row_off, g.low, g.n_low, g.mid, g.n_mid, g.high, g.n_high_chunks, op,
+                                    NoPush{}, a);
+                else
+                    expand_edges(g.src, g.m, op, a);
+            } else {
+                const int32_t *cur = (r & 1) ? p.A : p.B;
+                int32_t *next = (r & 1) ? p.B : p.A;
+                const int32_t *scur = (r & 1) ? p.S1 : p.S0;
+                int32_t *snext = (r & 1) ? p.S0 : p.S1;
+                SyncOp<ALGO> op{g.col, g.w, cur, next, scur, snext, r};
+                if (MODE == kVertexSync) {
+                    expand_vertices(g.row_off, g.low, g.n_low, g.mid, g.n_mid, g.high, g.n_high_chunks, op,
+                                    NoPush{}, a);
+                } else {
+                    expand_edges(g.src, g.m, op, a);
+                    // carry the values of last round's changed vertices into next
+                    for (int64_t v = tid; v < n; v += nth) {
+                        int32_t val;
+                        if (op.active((int32_t)v, val)) {
+                            op.own((int32_t)v, val);
+                            a.verts++;
+                        }
+                    }
+                }
+            }
+            int ch = block_sum(a.changed);
+            a.changed = 0;
+            if (threadIdx.x == 0 && ch) atomicAdd(&c->changed[r % 3], ch);
+            if (!grid_sync(c, p.timeout_ns)) break;
+            if (__ldcg(&c->changed[r % 3]) == 0) {
+                if (tid == 0) c->result_in_b = (ALGO != kBFS) && (r & 1);
+                if (ALGO == kSSSP && MODE == kVertexSync) {
+                    // A vertex without out-edges belongs to no bucket, so its
+                    // last improvement sits in one buffer only: take the min.
+                    int32_t *res = (r & 1) ? p.B : p.A;
+                    const int32_t *oth = (r & 1) ? p.A : p.B;
+                    for (int64_t i = tid; i < g.n_zero; i += nth) {
+                        int32_t v = __ldg(g.zero + i);
+                        int32_t x = ldcg(oth + v);
+                        if (x < ldcg(res + v)) stcg(res + v, x);
+                    }
+                }
+                break;
+            }
+            if (ALGO == kCC) {
+                // pointer jumping on next until a pass changes nothing
+                int32_t *next = (r & 1) ? p.B : p.A;
+                int32_t *snext = (r & 1) ? p.S0 : p.S1;
+                bool jok = true;
+                for (int pass = 0; pass < 16; pass++) {
+                    int slot = pass_ctr % 3;
+                    if (tid == 0) c->jchanged[(pass_ctr + 1) % 3] = 0;
+                    pass_ctr++;
+                    int jc = 0;
+                    for (int64_t v = tid; v < n; v += nth) {
+                        int32_t l = ldcg(next + v);
+                        if (l == (int32_t)v) continue;
+                        int32_t ll = ldcg(next + l);
+                        if (ll < l) {
+                            atomicMin(next + v, ll);
+                            stcg(snext + v, r + 1);
+                            jc++;
+                        }
+                    }
+                    jc = block_sum(jc);
+                    if (threadIdx.x == 0 && jc) atomicAdd(&c->jchanged[slot], jc);
+                    if (!grid_sync(c, p.timeout_ns)) { jok = false; break; }
+                    if (tid == 0) c->jump_passes++;
+                    if (__ldcg(&c->jchanged[slot]) == 0) break;
+                }
+                if (!jok) break;
+            }
+        }
+    } else if (!SYNC && ok) {
+        for (int gen = 0;; gen++) {
+            const int in_slot = gen % 3, out_slot = (gen + 1) % 3;
+            const bool initial_cc = (ALGO == kCC && gen == 0);
+            int n_in[3];
+            for (int k = 0; k < 3; k++) n_in[k] = __ldcg(&c->wl_size[in_slot][k]);
+            if (initial_cc) {
+                if (MODE == kEdgeAsync) {
+                    n_in[0] = g.n_nz; n_in[1] = n_in[2] = 0;
+                } else {
+                    n_in[kWlLow] = g.n_low; n_in[kWlMid] = g.n_mid; n_in[kWlHigh] = g.n_high_chunks;
+                }
+            }
+            if (n_in[0] + n_in[1] + n_in[2] == 0) break;
+            if (gen >= p.max_rounds) {
+                if (tid == 0) atomicOr(&c->status, kStRoundCap);
+                break;
+            }
+            rounds = gen + 1;
+            if (tid == 0)
+                for (int k = 0; k < 3; k++) c->wl_size[(gen + 2) % 3][k] = 0;
+            const int pi = gen & 1, po = pi ^ 1;
+            int *osize = c->wl_size[out_slot];
+            if (MODE == kVertexAsync) {
+                const int32_t *low = initial_cc ? g.low : p.wl[pi][kWlLow];
+                const int32_t *mid = initial_cc ? g.mid : p.wl[pi][kWlMid];
+                const int2 *high = initial_cc ? g.high : reinterpret_cast<const int2 *>(p.wl[pi][kWlHigh]);
+                ClassPush push{g.row_off, p.wl[po][kWlLow], p.wl[po][kWlMid],
+                               reinterpret_cast<int2 *>(p.wl[po][kWlHigh]), osize,
+                               p.wl_cap[kWlLow], p.wl_cap[kWlMid], p.wl_cap[kWlHigh] / 2, c};
+                if (ALGO == kBFS) {
+                    BfsAsyncOp op{g.col, p.A, gen};
+                    expand_vertices(g.row_off, low, n_in[kWlLow], mid, n_in[kWlMid], high, n_in[kWlHigh], op,
+                                    push, a);
+                } else {
+                    AsyncOp<ALGO> op{g.col, g.w, p.A, p.S0, gen};
+                    expand_vertices(g.row_off, low, n_in[kWlLow], mid, n_in[kWlMid], high, n_in[kWlHigh], op,
+                                    push, a);
+                }
+            } else {
+                const int32_t *items = initial_cc ? g.nz : p.wl[pi][0];
+                lb_prefix(g.row_off, items, n_in[0], p.lb_off, p.lb_blk);
+                if (!grid_sync(c, p.timeout_ns)) break;
+                ListPush push{g.row_off, p.wl[po][0], &osize[0], p.wl_cap[0], c};
+                a.verts += 0;
+                if (ALGO == kBFS) {
+                    BfsAsyncOp op{g.col, p.A, gen};
+                    lb_expand(g.row_off, items, n_in[0], p.lb_off, p.lb_blk, op, push, a);
+                } else {
+                    AsyncOp<ALGO> op{g.col, g.w, p.A, p.S0, gen};
+                    lb_expand(g.row_off, items, n_in[0], p.lb_off, p.lb_blk, op, push, a);
+                }
+                if (tid == 0) a.verts += (unsigned long long)n_in[0];
+            }
+            if (!grid_sync(c, p.timeout_ns)) break;
+        }
+    }
+
+    // ---- statistics
+    unsigned long long ev = block_sum(a.verts), ee = block_sum(a.edges), eu = block_sum(a.updates),
+                       ep = block_sum(a.pushes);
+    int of = block_sum(a.overflow);
+    if (threadIdx.x == 0) {
+        if (ev) atomicAdd(&c->st_vertices, ev);
+        if (ee) atomicAdd(&c->st_edges, ee);
+        if (eu) atomicAdd(&c->st_updates, eu);
+        if (ep) atomicAdd(&c->st_pushes, ep);
+        if (of) atomicOr(&c->status, kStOverflow);
+    }
+    if (tid == 0) c->rounds = rounds;
+}
+
+// One all-active sweep: vertex variant over the buckets, edge variant over
+// the COO.  Ordinary launch (no grid barrier).
+template <int MODE>
+__global__ void __launch_bounds__(kBlock) sweep_kernel(View g, const int32_t *cur, int32_t *next, Ctrl *c) {
+    Acc a;
+    SweepOp op{g.col, g.w, cur, next};
+    if (MODE == kVertexSync)
+        expand_vertices(g.row_off, g.low, g.n_low, g.mid, g.n_mid, g.high, g.n_high_chunks, op, NoPush{}, a);
+    else
+        expand_edges(g.src, g.m, op, a);
+    unsigned long long eu = block_sum(a.updates);
+    int of = block_sum(a.overflow);
+    if (threadIdx.x == 0) {
+        if (eu) atomicAdd(&c->st_updates, eu);
+        if (of) atomicOr(&c->status, kStOverflow);
+    }
+}
+
+// FG_ERR_OVERFLOW test: some edge u->v with dist[u] finite and dist[v] still
+// INF means v's true distance is finite but >= INT32_MAX.
+__global__ void overflow_check_kernel(View g, const int32_t *D, int *flag) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < g.m; e += (int64_t)gridDim.x * blockDim.x) {
+        if (__ldg(D + g.src[e]) != kInf && __ldg(D + g.col[e]) == kInf) {
+            *flag = 1;
+            return;
+        }
+    }
+}
+
+// ================================================================ host side
+using KernelFn = void (*)(Params);
+
+KernelFn kernel_for(Algo algo, Mode mode) {
+#define FG_K(A, M) \
+    if (algo == A && mode == M) return fixpoint_kernel<A, M>;
+    FG_K(kSSSP, kVertexSync) FG_K(kSSSP, kVertexAsync) FG_K(kSSSP, kEdgeSync) FG_K(kSSSP, kEdgeAsync)
+    FG_K(kBFS, kVertexSync) FG_K(kBFS, kVertexAsync) FG_K(kBFS, kEdgeSync) FG_K(kBFS, kEdgeAsync)
+    FG_K(kCC, kVertexSync) FG_K(kCC, kVertexAsync) FG_K(kCC, kEdgeSync) FG_K(kCC, kEdgeAsync)
+#undef FG_K
+    return nullptr;
+}
+
+struct DeviceProps {
+    int sms = 0;
+    bool coop = false;
+};
+
+DeviceProps device_props(int dev) {
+    static std::mutex mu;
+    static DeviceProps cache[64];
+    static bool have[64] = {};
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev >= 0 && dev < 64 && have[dev]) return cache[dev];
+    DeviceProps p;
+    cudaDeviceGetAttribute(&p.sms, cudaDevAttrMultiProcessorCount, dev);
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    p.coop = coop != 0;
+    if (dev >= 0 && dev < 64) { cache[dev] = p; have[dev] = true; }
+    return p;
+}
+
+struct Workspace {
+    char *base = nullptr;
+    size_t off = 0, size = 0;
+    template <typename T>
+    T *take(int64_t count) {
+        size_t bytes = ((size_t)std::max<int64_t>(count, 1) * sizeof(T) + 255) & ~(size_t)255;
+        T *p = reinterpret_cast<T *>(base + off);
+        off += bytes;
+        return p;
+    }
+    static size_t need(int64_t count, size_t elem) { return ((size_t)std::max<int64_t>(count, 1) * elem + 255) & ~(size_t)255; }
+};
+
+}  // namespace
+
+fg_status run_query(const fg_graph *G, Algo algo, Mode mode, int32_t source, int32_t *out,
+                    const fg_options *opt, fg_stats *stats) {
+    const View &g = (algo == kCC) ? G->s : G->g;
+    const int32_t n = g.n;
+    cudaStream_t st = opt && opt->stream ? (cudaStream_t)opt->stream : (cudaStream_t)0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != G->device) return fail(FG_ERR_INVALID_ARG, "the current device is not the graph's device");
+    DeviceProps dp = device_props(dev);
+    if (!dp.coop) return fail(FG_ERR_CUDA, "device does not support cooperative launches");
+    KernelFn fn = kernel_for(algo, mode);
+    if (!fn) return fail(FG_ERR_INVALID_ARG, "invalid algorithm or mode");
+
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, kBlock, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (opt && opt->blocks_per_sm > 0) per_sm = std::min(per_sm, (int)opt->blocks_per_sm);
+    int grid = std::min(per_sm * dp.sms, kMaxGrid);
+    if (grid < 1) return fail(FG_ERR_CUDA, "kernel does not fit on an SM");
+
+    const bool sync = (mode == kVertexSync || mode == kEdgeSync);
+    // per-query state, carved from one stream-ordered allocation
+    size_t need = Workspace::need(1, sizeof(Ctrl)) + Workspace::need(n, 4);
+    int64_t cap[3] = {0, 0, 0};
+    if (sync && algo != kBFS) need += 3 * Workspace::need(n, 4);
+    if (!sync) {
+        if (algo != kBFS) need += Workspace::need(n, 4);
+        if (mode == kVertexAsync) {
+            cap[kWlLow] = std::max(g.n_low, 1);
+            cap[kWlMid] = std::max(g.n_mid, 1);
+            cap[kWlHigh] = 2 * (int64_t)std::max(g.n_high_chunks, 1);
+        } else {
+            cap[0] = std::max(g.n_nz, 1);
+            need += Workspace::need(cap[0], 4) + Workspace::need(kMaxGrid, 4);
+        }
+        for (int k = 0; k < 3; k++) need += 2 * Workspace::need(cap[k], 4);
+    }
+    Workspace ws;
+    ws.size = need;
+    e = cudaMallocAsync((void **)&ws.base, need, st);
+    if (e != cudaSuccess) return cuda_fail(e, "query workspace");
+
+    Params p;
+    p.g = g;
+    p.ctrl = ws.take<Ctrl>(1);
+    p.A = ws.take<int32_t>(n);
+    if (sync && algo != kBFS) {
+        p.B = ws.take<int32_t>(n);
+        p.S0 = ws.take<int32_t>(n);
+        p.S1 = ws.take<int32_t>(n);
+    }
+    if (!sync) {
+        if (algo != kBFS) p.S0 = ws.take<int32_t>(n);
+        for (int par = 0; par < 2; par++)
+            for (int k = 0; k < 3; k++) p.wl[par][k] = ws.take<int32_t>(cap[k]);
+        for (int k = 0; k < 3; k++) p.wl_cap[k] = (int32_t)cap[k];
+        if (mode == kEdgeAsync) {
+            p.lb_off = ws.take<uint32_t>(cap[0]);
+            p.lb_blk = ws.take<uint32_t>(kMaxGrid);
+        }
+    }
+    p.source = source;
+    p.max_rounds = (opt && opt->max_rounds > 0) ? opt->max_rounds : (n > INT32_MAX - 2 ? INT32_MAX : n + 2);
+    int tmo = (opt && opt->wait_timeout_ms > 0) ? opt->wait_timeout_ms : 1000;
+    p.timeout_ns = (unsigned long long)tmo * 1000000ull;
+    p.inject_missing_arrival = (opt && opt->inject_missing_arrival) ? 1 : 0;
+
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    fg_status status = FG_OK;
+    std::string msg;
+    Ctrl hc;
+    e = cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev0, st);
+    if (e == cudaSuccess) {
+        void *args[] = {&p};
+        e = cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(kBlock), args, 0, st);
+        if (e == cudaSuccess) count_launch();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev1, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        status = (e == cudaErrorMemoryAllocation) ? FG_ERR_OUT_OF_MEMORY : FG_ERR_CUDA;
+        msg = std::string("fixpoint kernel: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+    }
+    const int32_t *result = (hc.result_in_b && p.B) ? p.B : p.A;
+    if (status == FG_OK) {
+        if (hc.status & kStTimeout) {
+            status = FG_ERR_TIMEOUT;
+            msg = "a device-side wait exceeded the timeout";
+        } else if (hc.status & kStRoundCap) {
+            status = FG_ERR_TIMEOUT;
+            msg = "round cap reached before the fixpoint";
+        } else if (hc.status & kStWorklist) {
+            status = FG_ERR_CUDA;
+            msg = "internal error: worklist capacity exceeded";
+        } else if ((hc.status & kStOverflow) && algo == kSSSP) {
+            int *flag = reinterpret_cast<int *>(p.ctrl);   // reuse the control block
+            int hf = 0;
+            e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+            if (e == cudaSuccess) {
+                overflow_check_kernel<<<dp.sms * 8, kBlock, 0, st>>>(g, result, flag);
+                count_launch();
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) {
+                status = FG_ERR_CUDA;
+                msg = std::string("overflow check: ") + cudaGetErrorString(e);
+            } else if (hf) {
+                status = FG_ERR_OVERFLOW;
+                msg = "a finite shortest distance is >= INT32_MAX";
+            }
+        }
+    }
+    if (status == FG_OK) {
+        e = cudaMemcpyAsync(out, result, (size_t)n * sizeof(int32_t), cudaMemcpyDefault, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            status = FG_ERR_CUDA;
+            msg = std::string("result copy: ") + cudaGetErrorString(e);
+        }
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    cudaFreeAsync(ws.base, st);
+    if (stats) {
+        stats->mode = (int32_t)mode;
+        stats->rounds = hc.rounds;
+        stats->jump_passes = hc.jump_passes;
+        stats->grid_blocks = grid;
+        stats->vertices_processed = (int64_t)hc.st_vertices;
+        stats->edges_relaxed = (int64_t)hc.st_edges;
+        stats->updates = (int64_t)hc.st_updates;
+        stats->pushes = (int64_t)hc.st_pushes;
+        stats->kernel_ms = ms;
+    }
+    if (status != FG_OK) return fail(status, msg);
+    return FG_OK;
+}
+
+fg_status run_sweep(const fg_graph *G, Mode mode, const int32_t *cur, int32_t *next, cudaStream_t st,
+                    int64_t *updates, float *kernel_ms) {
+    const View &g = G->g;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != G->device) return fail(FG_ERR_INVALID_ARG, "the current device is not the graph's device");
+    DeviceProps dp = device_props(dev);
+    auto fn = (mode == kVertexSync) ? sweep_kernel<kVertexSync> : sweep_kernel<kEdgeSync>;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, kBlock, 0);
+    int grid = std::max(1, per_sm * dp.sms);
+    Ctrl *c = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&c, sizeof(Ctrl), st);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep workspace");
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    Ctrl hc;
+    e = cudaMemsetAsync(c, 0, sizeof(Ctrl), st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev0, st);
+    if (e == cudaSuccess) {
+        fn<<<grid, kBlock, 0, st>>>(g, cur, next, c);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev1, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, c, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    cudaFreeAsync(c, st);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep");
+    if (updates) *updates = (int64_t)hc.st_updates;
+    if (kernel_ms) *kernel_ms = ms;
+    return FG_OK;
+}
+
+}  // namespace fg

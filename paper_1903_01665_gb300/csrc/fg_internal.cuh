@@ -1,0 +1,240 @@
+// Internal declarations of the fg library: device graph layout, per-query
+// control block and the device helpers shared by the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+
+#include "../../include/fg.h"
+
+namespace fg {
+
+// ---------------------------------------------------------------- constants
+constexpr int kBlock = 256;            // threads per persistent CTA
+constexpr int kWarps = kBlock / 32;
+constexpr int kLowMax = 32;            // low bucket: 1 .. 31 out-edges (thread per vertex)
+constexpr int kMidMax = 1024;          // mid bucket: 32 .. 1023 (warp per vertex)
+constexpr int kChunk = 2048;           // high bucket: >= 1024, split in 2048-edge chunks (CTA each)
+constexpr int32_t kInf = FG_INF;
+
+// device status bits (Ctrl::status)
+constexpr int kStTimeout = 1;          // a grid barrier wait ran out
+constexpr int kStRoundCap = 2;         // max_rounds reached
+constexpr int kStOverflow = 4;         // a candidate >= INT32_MAX was formed (checked on host)
+constexpr int kStWorklist = 8;         // a worklist append exceeded its capacity
+
+// ---------------------------------------------------------------- graph
+// One adjacency: the directed graph, or its symmetrised copy for CC.
+struct View {
+    int32_t n = 0;
+    int64_t m = 0;
+    const uint32_t *row_off = nullptr;  // [n+1]
+    const int32_t *col = nullptr;       // [m]  CSR targets == COO dst (source-sorted)
+    const int32_t *w = nullptr;         // [m]  weights (nullptr in the symmetrised view)
+    const int32_t *src = nullptr;       // [m]  COO sources, non-decreasing
+    const int32_t *low = nullptr;       // vertices with 1..31 out-edges, ascending
+    const int32_t *mid = nullptr;       // 32..1023, ascending
+    const int2 *high = nullptr;         // {vertex, first edge} per 2048-edge chunk of >= 1024
+    const int32_t *nz = nullptr;        // all vertices with >= 1 out-edge, ascending
+    const int32_t *zero = nullptr;      // vertices with no out-edge, ascending
+    int32_t n_low = 0, n_mid = 0, n_high = 0, n_high_chunks = 0, n_nz = 0, n_zero = 0;
+    int32_t max_deg = 0;
+};
+
+}  // namespace fg
+
+struct fg_graph {
+    int device = 0;
+    fg::View g;      // directed
+    fg::View s;      // symmetrised
+    fg_graph_info_t info{};
+    void *allocs[24] = {};
+    int n_allocs = 0;
+    // lazily computed diameter estimate for fg_select_mode
+    mutable std::mutex mu;
+    mutable int32_t diam_est = -1;
+};
+
+namespace fg {
+
+// ---------------------------------------------------------------- per query
+// Device control block, zeroed before each launch.
+struct Ctrl {
+    unsigned bar_count;
+    unsigned bar_gen;
+    int status;
+    int rounds;                 // rounds / generations executed
+    int jump_passes;
+    int result_in_b;            // sync: 1 if the result is in buffer B
+    int changed[3];             // per-round change counters, rotating slots
+    int jchanged[3];            // per-pass pointer-jumping change counters
+    int wl_size[3][4];          // async: worklist sizes per generation slot and class
+    unsigned long long st_vertices, st_edges, st_updates, st_pushes;
+};
+
+enum Algo { kSSSP = 0, kBFS = 1, kCC = 2 };
+enum Mode { kVertexSync = 0, kVertexAsync = 1, kEdgeSync = 2, kEdgeAsync = 3 };
+
+// worklist classes (vertex-async): low, mid, high chunks; edge-async uses class 0 only
+enum { kWlLow = 0, kWlMid = 1, kWlHigh = 2 };
+
+struct Params {
+    View g;
+    int32_t *A = nullptr;       // values (dist / level / label); the result for async
+    int32_t *B = nullptr;       // second buffer of the sync modes
+    int32_t *S0 = nullptr;      // activity stamps (sync: read in odd/even rounds)
+    int32_t *S1 = nullptr;      //   async: S0 = push stamp (dedup)
+    int32_t *wl[2][3] = {};     // async worklists [in/out parity][class]; high as int2 pairs
+    int32_t wl_cap[3] = {};     // capacity per class (in int32 slots)
+    uint32_t *lb_off = nullptr; // edge-async: per-item local offsets
+    uint32_t *lb_blk = nullptr; // edge-async: per-CTA totals
+    int32_t source = 0;
+    int32_t max_rounds = 0;
+    unsigned long long timeout_ns = 0;
+    int32_t inject_missing_arrival = 0;
+    Ctrl *ctrl = nullptr;
+};
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_acquire_i(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Mutable arrays are read through L2 (ld.global.cg): other CTAs write them
+// during the kernel, so L1 copies could be stale.
+__device__ __forceinline__ int32_t ldcg(const int32_t *p) { return __ldcg(p); }
+__device__ __forceinline__ void stcg(int32_t *p, int32_t v) { __stcg(p, v); }
+
+// ---------------------------------------------------------------- grid barrier
+// Sense-by-generation barrier over all CTAs of a cooperative launch.  The
+// wait is bounded by timeout_ns; on expiry the CTA records kStTimeout and
+// returns false.  It also returns false once any error bit is set, so every
+// CTA leaves the kernel at its next barrier.
+__device__ __forceinline__ bool grid_sync(Ctrl *c, unsigned long long timeout_ns) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        unsigned gen = ld_acquire(&c->bar_gen);
+        unsigned arrived = atom_add_acq_rel(&c->bar_count, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            c->bar_count = 0;
+            st_release(&c->bar_gen, gen + 1u);
+        } else {
+            unsigned long long t0 = global_ns();
+            unsigned spins = 0;
+            while (ld_acquire(&c->bar_gen) == gen) {
+                if (++spins > 64) {
+                    __nanosleep(32);
+                    if (global_ns() - t0 > timeout_ns) {
+                        atomicOr(&c->status, kStTimeout);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+        if (ld_acquire_i(&c->status) & (kStTimeout | kStRoundCap | kStWorklist)) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ---------------------------------------------------------------- warp helpers
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Warp-aggregated append: every lane of `mask` calls it together; lanes with
+// want != 0 get consecutive slots of list[*size]; one atomicAdd per warp.
+// Returns false (and sets kStWorklist) on overflow.
+__device__ __forceinline__ void warp_append(unsigned mask, bool want, int32_t value, int32_t *list,
+                                            int *size, int32_t cap, Ctrl *c) {
+    unsigned b = __ballot_sync(mask, want);
+    if (b == 0) return;
+    int leader = __ffs(b) - 1;
+    int base = 0;
+    if ((int)lane_id() == leader) base = atomicAdd(size, __popc(b));
+    base = __shfl_sync(mask, base, leader);
+    if (want) {
+        int pos = base + __popc(b & lanemask_lt());
+        if (pos < cap) list[pos] = value;
+        else atomicOr(&c->status, kStWorklist);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_scan(T x) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, d);
+        if ((int)lane_id() >= d) x += y;
+    }
+    return x;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T x) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+    return x;
+}
+
+// ---------------------------------------------------------------- host side
+struct Error {
+    fg_status code;
+    std::string msg;
+};
+
+void set_last_error(const std::string &msg);
+const char *last_error_cstr();
+fg_status fail(fg_status code, const std::string &msg);
+fg_status cuda_fail(cudaError_t e, const char *what);
+
+// graph construction (fg_build.cu)
+fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                               const int32_t *w, bool src_sorted_csr, const int64_t *row_off_in,
+                               fg_graph **out);
+
+// queries (fg_fixpoint.cu)
+fg_status run_query(const fg_graph *g, Algo algo, Mode mode, int32_t source, int32_t *out,
+                    const fg_options *opt, fg_stats *stats);
+fg_status run_sweep(const fg_graph *g, Mode mode, const int32_t *cur, int32_t *next,
+                    cudaStream_t stream, int64_t *updates, float *kernel_ms);
+
+// whether a pointer is device-accessible memory of the current device
+bool is_device_pointer(const void *p);
+
+// process-wide count of kernels this library has launched
+void count_launch();
+
+}  // namespace fg

@@ -1,0 +1,58 @@
+"""Helpers of the GPU tests: create graphs through the C ABI and run queries."""
+from __future__ import annotations
+
+import contextlib
+
+import numpy as np
+
+import paper_1903_01665_gb300 as fg
+
+MODES = [fg.FG_VERTEX_SYNC, fg.FG_VERTEX_ASYNC, fg.FG_EDGE_SYNC, fg.FG_EDGE_ASYNC]
+MODE_IDS = ["vertex_sync", "vertex_async", "edge_sync", "edge_async"]
+ALGOS = {"sssp": fg.FG_ALGO_SSSP, "bfs": fg.FG_ALGO_BFS, "cc": fg.FG_ALGO_CC}
+
+
+def to_csr(g):
+    """Host CSR (int64 offsets) of a graphgen.Graph, stable by input order."""
+    order = np.argsort(g.src, kind="stable")
+    deg = np.bincount(g.src, minlength=g.n).astype(np.int64)
+    row_off = np.zeros(g.n + 1, np.int64)
+    np.cumsum(deg, out=row_off[1:])
+    return row_off, g.dst[order].copy(), g.w[order].copy()
+
+
+@contextlib.contextmanager
+def graph_handle(g, kind="coo", where="host", weights=True):
+    """Create a device graph from a graphgen.Graph; destroyed on exit."""
+    import torch
+    w = g.w if weights else None
+    if kind == "coo":
+        arrs = [g.src, g.dst, w]
+    else:
+        arrs = list(to_csr(g))
+        if not weights:
+            arrs[2] = None
+    if where == "device":
+        arrs = [None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+    if kind == "coo":
+        st, h = fg.fg_graph_create_coo(g.n, *arrs)
+    else:
+        st, h = fg.fg_graph_create_csr(g.n, *arrs)
+    fg.check(st)
+    try:
+        yield h
+    finally:
+        fg.check(fg.fg_graph_destroy(h))
+
+
+def run(h, n, algo, src, mode, where="device", **kw):
+    """Run one query; returns (result as numpy int32[n], stats)."""
+    import torch
+    if where == "device":
+        out = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    else:
+        out = np.full(n, -7, np.int32)
+    st, stats = fg.fg_run(h, algo, int(src), out, mode, **kw)
+    fg.check(st)
+    res = out.cpu().numpy() if where == "device" else out
+    return res, stats

@@ -1,0 +1,105 @@
+"""The C ABI without a GPU: the library loads, exports every function that
+include/fg.h declares, the binding's struct layouts match a C compiler's, and
+host-side argument checks fail before any device work."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_1903_01665_gb300 as fg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fg.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fg_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["fg_graph_create_csr", "fg_graph_create_coo", "fg_graph_destroy", "fg_sssp",
+                     "fg_bfs", "fg_cc", "fg_select_mode", "fg_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = fg.load()
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", fg.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (fg_[a-z_]+)$", out, flags=re.M))
+    assert set(declared_functions()) <= exported
+
+
+def test_struct_layout_matches_c(tmp_path):
+    prog = tmp_path / "layout.c"
+    prog.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "fg.h"
+#define P(T, f) printf(#T "." #f " %zu\n", offsetof(T, f))
+int main(void) {
+  printf("fg_options %zu\nfg_stats %zu\nfg_graph_info_t %zu\n", sizeof(fg_options), sizeof(fg_stats), sizeof(fg_graph_info_t));
+  P(fg_options, stream); P(fg_options, max_rounds); P(fg_options, wait_timeout_ms);
+  P(fg_options, blocks_per_sm); P(fg_options, inject_missing_arrival);
+  P(fg_stats, mode); P(fg_stats, rounds); P(fg_stats, jump_passes); P(fg_stats, grid_blocks);
+  P(fg_stats, vertices_processed); P(fg_stats, edges_relaxed); P(fg_stats, updates);
+  P(fg_stats, pushes); P(fg_stats, kernel_ms);
+  P(fg_graph_info_t, n); P(fg_graph_info_t, m); P(fg_graph_info_t, m_sym);
+  P(fg_graph_info_t, max_out_degree); P(fg_graph_info_t, n_zero_out); P(fg_graph_info_t, n_low);
+  P(fg_graph_info_t, n_mid); P(fg_graph_info_t, n_high); P(fg_graph_info_t, n_high_chunks);
+  P(fg_graph_info_t, n_isolated);
+  P(fg_graph_info_t, device_bytes);
+  return 0;
+}
+''')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)],
+                   check=True)
+    c = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        k, v = line.split()
+        c[k] = int(v)
+    for cls in (fg.fg_options, fg.fg_stats, fg.fg_graph_info_t):
+        assert ctypes.sizeof(cls) == c[cls.__name__]
+        for name, _ in cls._fields_:
+            assert getattr(cls, name).offset == c[f"{cls.__name__}.{name}"], (cls.__name__, name)
+
+
+def test_host_side_argument_checks():
+    src = np.array([0, 1], np.int32)
+    dst = np.array([1, 2], np.int32)
+    st, g = fg.fg_graph_create_coo(0, src, dst)
+    assert st == fg.FG_ERR_INVALID_ARG and g is None
+    assert "positive" in fg.fg_last_error()
+    st = fg.load().fg_graph_create_coo(3, 2, None, dst.ctypes.data, None, ctypes.byref(ctypes.c_void_p()))
+    assert st == fg.FG_ERR_INVALID_ARG
+    st = fg.load().fg_graph_create_csr(3, 2, None, dst.ctypes.data, None, ctypes.byref(ctypes.c_void_p()))
+    assert st == fg.FG_ERR_INVALID_ARG
+    st = fg.load().fg_graph_create_coo(3, -1, src.ctypes.data, dst.ctypes.data, None,
+                                       ctypes.byref(ctypes.c_void_p()))
+    assert st == fg.FG_ERR_INVALID_ARG
+    st = fg.load().fg_graph_create_coo(3, 1 << 31, src.ctypes.data, dst.ctypes.data, None,
+                                       ctypes.byref(ctypes.c_void_p()))
+    assert st == fg.FG_ERR_INVALID_ARG
+    out = np.zeros(3, np.int32)
+    assert fg.fg_sssp(None, 0, out) == fg.FG_ERR_INVALID_ARG
+    assert fg.fg_cc(None, out) == fg.FG_ERR_INVALID_ARG
+    st, _ = fg.fg_select_mode(None, fg.FG_ALGO_BFS)
+    assert st == fg.FG_ERR_INVALID_ARG
+    assert fg.fg_graph_destroy(None) == fg.FG_OK
+    assert fg.fg_status_string(fg.FG_ERR_OVERFLOW) == "FG_ERR_OVERFLOW"
+    assert fg.fg_status_string(fg.FG_ERR_TIMEOUT) == "FG_ERR_TIMEOUT"
+
+
+def test_binding_rejects_wrong_dtypes():
+    with pytest.raises(TypeError):
+        fg.fg_graph_create_coo(3, np.array([0], np.int64), np.array([1], np.int32))
+    with pytest.raises(TypeError):
+        fg.fg_sssp(None, 0, np.zeros(3, np.float32))
