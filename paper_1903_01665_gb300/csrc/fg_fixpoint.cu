@@ -49,7 +49,9 @@ __device__ __forceinline__ T block_sum(T x) {
 
 // ================================================================ edge ops
 // Each op provides:
-//   active(u, val)  -- is u expanded this round; its value (may update state)
+//   active(u, val, rq) -- is u expanded this round; its value.  An op may
+//                      lower u's own value here (CC pointer jumping); it then
+//                      sets rq if u must be re-queued for the next generation.
 //   own(u, val)     -- once per expanded vertex (sync: carry cur[u] into next)
 //   edge(e, val, a, v) -- relax edge e from a source with value val; returns
 //                      true if target v must be appended to the worklist.
@@ -65,7 +67,7 @@ struct SyncOp {
     int32_t *snext;
     int32_t r;
 
-    __device__ __forceinline__ bool active(int32_t u, int32_t &val) const {
+    __device__ __forceinline__ bool active(int32_t u, int32_t &val, bool &) const {
         if (ldcg(scur + u) != r) return false;
         val = ldcg(cur + u);
         return true;
@@ -101,7 +103,7 @@ struct BfsSyncOp {
     int32_t *L;
     int32_t lev;
 
-    __device__ __forceinline__ bool active(int32_t u, int32_t &val) const {
+    __device__ __forceinline__ bool active(int32_t u, int32_t &val, bool &) const {
         val = lev;
         return ldcg(L + u) == lev;
     }
@@ -126,7 +128,7 @@ struct AsyncOp {
     int32_t *stamp;
     int32_t gen;
 
-    __device__ __forceinline__ bool active(int32_t u, int32_t &val) const {
+    __device__ __forceinline__ bool active(int32_t u, int32_t &val, bool &rq) const {
         val = ldcg(D + u);
         if (ALGO == kCC) {
             // pointer jumping: follow label[label[...]] while it decreases
@@ -138,7 +140,9 @@ struct AsyncOp {
                 l = ll;
             }
             if (l < val) {
-                atomicMin(D + u, l);
+                // u's other edges may be relaxed elsewhere with the old label,
+                // so u is queued again to pass the new one to all neighbours
+                if (atomicMin(D + u, l) > l) rq = atomicExch(stamp + u, gen + 1) != gen + 1;
                 val = l;
             }
         }
@@ -172,7 +176,7 @@ struct BfsAsyncOp {
     int32_t *L;
     int32_t gen;
 
-    __device__ __forceinline__ bool active(int32_t, int32_t &val) const {
+    __device__ __forceinline__ bool active(int32_t, int32_t &val, bool &) const {
         val = gen;
         return true;
     }
@@ -195,7 +199,7 @@ struct SweepOp {
     const int32_t *cur;
     int32_t *next;
 
-    __device__ __forceinline__ bool active(int32_t u, int32_t &val) const {
+    __device__ __forceinline__ bool active(int32_t u, int32_t &val, bool &) const {
         val = ldcg(cur + u);
         return val != kInf;
     }
@@ -278,7 +282,7 @@ __device__ __forceinline__ void expand_vertices(const uint32_t *__restrict__ row
                                                 int n_low, const int32_t *mid, int n_mid, const int2 *high,
                                                 int n_high, const OP &op, const PUSH &push, Acc &a) {
     __shared__ int32_t s_val;
-    __shared__ int s_act;
+    __shared__ int s_act, s_rq;
     const unsigned lane = lane_id();
     // high-degree chunks: one CTA per 2048-edge chunk
     for (int ci = blockIdx.x; ci < n_high; ci += gridDim.x) {
@@ -288,15 +292,18 @@ __device__ __forceinline__ void expand_vertices(const uint32_t *__restrict__ row
         uint32_t rb = __ldg(row_off + ch.x), re = __ldg(row_off + ch.x + 1);
         if (threadIdx.x == 0) {
             int32_t val = 0;
-            bool act = op.active(ch.x, val);
+            bool rq = false;
+            bool act = op.active(ch.x, val, rq);
             if (act && (uint32_t)ch.y == rb) {
                 op.own(ch.x, val);
                 a.verts++;
             }
             s_act = act;
             s_val = val;
+            s_rq = rq;
         }
         __syncthreads();
+        push(threadIdx.x == 0 && s_rq, ch.x, a);
         if (s_act) {
             int32_t val = s_val;
             uint32_t e0 = (uint32_t)ch.y, e1 = min(e0 + (uint32_t)kChunk, re);
@@ -318,10 +325,12 @@ __device__ __forceinline__ void expand_vertices(const uint32_t *__restrict__ row
         int32_t u = ldcg(mid + i);
         int32_t val = 0;
         int act = 0;
+        bool rq = false;
         if (lane == 0) {
-            act = op.active(u, val);
+            act = op.active(u, val, rq);
             if (act) op.own(u, val);
         }
+        push(lane == 0 && rq, u, a);
         act = __shfl_sync(0xffffffffu, act, 0);
         if (!act) continue;
         val = __shfl_sync(0xffffffffu, val, 0);
@@ -341,17 +350,19 @@ __device__ __forceinline__ void expand_vertices(const uint32_t *__restrict__ row
     // low-degree vertices: a thread each, edges redistributed over the warp
     for (int base = gw * 32; base < n_low; base += nw * 32) {
         int i = base + (int)lane;
-        int32_t val = 0;
+        int32_t val = 0, u = 0;
         uint32_t rb = 0, d = 0;
+        bool rq = false;
         if (i < n_low) {
-            int32_t u = ldcg(low + i);
-            if (op.active(u, val)) {
+            u = ldcg(low + i);
+            if (op.active(u, val, rq)) {
                 op.own(u, val);
                 rb = __ldg(row_off + u);
                 d = __ldg(row_off + u + 1) - rb;
                 a.verts++;
             }
         }
+        push(rq, u, a);
         uint32_t incl = warp_inclusive_scan(d);
         uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
         uint32_t excl = incl - d;
@@ -394,7 +405,8 @@ __device__ __forceinline__ void expand_edges(const int32_t *__restrict__ src, in
         for (int j = 0; j < 4; j++) {
             int32_t u = us[j];
             if (u != prev) {
-                pact = op.active(u, pval);
+                bool rq;
+                pact = op.active(u, pval, rq);
                 prev = u;
             }
             if (pact) {
@@ -406,8 +418,9 @@ __device__ __forceinline__ void expand_edges(const int32_t *__restrict__ src, in
     }
     for (int64_t e = 4 * m4 + tid; e < m; e += nth) {
         int32_t val;
+        bool rq;
         int32_t u = __ldg(src + e);
-        if (op.active(u, val)) {
+        if (op.active(u, val, rq)) {
             int32_t v;
             op.edge((uint32_t)e, val, a, v);
             a.edges++;
@@ -517,15 +530,18 @@ __device__ __forceinline__ void lb_expand(const uint32_t *__restrict__ row_off, 
     while (t0 < (uint32_t)hi) {
         int i0 = s_i0;
         int cnt = min(kBlock, n_items - i0);
+        bool rq = false;
+        int32_t u = 0;
         if ((int)threadIdx.x < cnt) {
             int i = i0 + threadIdx.x;
-            int32_t u = ldcg(items + i);
+            u = ldcg(items + i);
             s_goff[threadIdx.x] = goff(i);
             s_rb[threadIdx.x] = __ldg(row_off + u);
             int32_t val = 0;
-            op.active(u, val);
+            op.active(u, val, rq);
             s_val[threadIdx.x] = val;
         }
+        push(rq, u, a);
         if (threadIdx.x == 0) s_goff[cnt] = (i0 + cnt < n_items) ? goff(i0 + cnt) : T;
         __syncthreads();
         uint32_t t1 = min((uint32_t)hi, min(t0 + (uint32_t)(kBlock * kLbEdgesPerThread), s_goff[cnt]));
@@ -641,7 +657,8 @@ __global__ void __launch_bounds__(kBlock) fixpoint_kernel(Params p) {
                     // carry the values of last round's changed vertices into next
                     for (int64_t v = tid; v < n; v += nth) {
                         int32_t val;
-                        if (op.active((int32_t)v, val)) {
+                        bool rq;
+                        if (op.active((int32_t)v, val, rq)) {
                             op.own((int32_t)v, val);
                             a.verts++;
                         }
