@@ -26,7 +26,9 @@
  *     device memory of the current device; the library tells them apart
  *     with cudaPointerGetAttributes.  Inputs are read during the call only
  *     and never retained.  Outputs are caller-owned int32[n], written once,
- *     in bulk, only on success (the paper's aggregated transfer, Sec. 3.5).
+ *     in bulk, only on success (one transfer per attribute array, as the
+ *     paper's data-transfer aggregation prescribes for attributes read back
+ *     on the host).
  *   - Every call returns an fg_status; nothing throws across the ABI.  On
  *     error, fg_last_error() gives a message for the calling thread and the
  *     outputs are untouched.
