@@ -184,6 +184,35 @@ fg_status fg_run(const fg_graph *g, fg_algo algo, int32_t src, int32_t *out, fg_
 fg_status fg_sweep(const fg_graph *g, fg_mode mode, const int32_t *cur, int32_t *next,
                    void *stream, int64_t *updates, float *kernel_ms);
 
+/*
+ * fg_sssp_csr_noalloc -- shortest paths without any device allocation.  The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc, e.g. code whose device memory is all owned by another
+ * allocator (a framework's caching pool that has reserved the budget), or a
+ * latency-critical loop where an allocation may synchronise the device or
+ * fail.  It computes what fg_sssp computes with FG_VERTEX_SYNC, directly from
+ * a caller-owned CSR:
+ *   n <= FG_NOALLOC_MAX_VERTICES vertices (larger n: FG_ERR_INVALID_ARG);
+ *   row_off[n+1] int64, col[m] int32, w[m] int32 (>= 0) or NULL for unit
+ *   weights, dist_out[n] int32 -- all device memory of the current device;
+ *   stream: cudaStream_t or NULL for the legacy default stream.
+ * Its scratch (a second distance buffer, two activity-stamp arrays and the
+ * control block) is one fixed array of about 12 MiB in the library's device
+ * image; every GPU that loads the library holds it until the process exits.
+ * The first call on a device looks up that array's device address (once per
+ * device, with that device current), so make the first call before any
+ * stream capture.  Every call on a device shares the one array and starts by
+ * clearing its control block: calls that overlap on the GPU (another stream,
+ * another host thread) race and must not be issued.  dist_out doubles as the
+ * first distance buffer, so on error its contents are unspecified.  Blocks
+ * until the result is written.  Errors: FG_ERR_INVALID_ARG (sizes, NULL,
+ * host pointers, invalid CSR or negative weight), FG_ERR_OVERFLOW,
+ * FG_ERR_TIMEOUT, FG_ERR_CUDA.
+ */
+#define FG_NOALLOC_MAX_VERTICES 1048576
+fg_status fg_sssp_csr_noalloc(int32_t n, int64_t m, const int64_t *row_off, const int32_t *col,
+                              const int32_t *w, int32_t src, int32_t *dist_out, void *stream);
+
 /* Number of kernels this library has launched in this process so far (all
    threads and devices); lets a caller count the device work of a region. */
 uint64_t fg_kernel_launches(void);

@@ -83,6 +83,8 @@ _SIGNATURES = {
                               ctypes.POINTER(fg_options), ctypes.POINTER(fg_stats)]),
     "fg_sweep": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_int64),
                                 ctypes.POINTER(ctypes.c_float)]),
+    "fg_sssp_csr_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _VP, _VP, _VP, ctypes.c_int32,
+                                           _VP, _VP]),
     "fg_kernel_launches": (ctypes.c_uint64, []),
     "fg_last_error": (ctypes.c_char_p, []),
     "fg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -218,6 +220,24 @@ def fg_sweep(g, mode, cur, nxt, stream=None):
     ms = ctypes.c_float(0)
     st = load().fg_sweep(g, int(mode), _ptr(cur), _ptr(nxt), stream, ctypes.byref(upd), ctypes.byref(ms))
     return st, upd.value, ms.value
+
+
+FG_NOALLOC_MAX_VERTICES = 1048576
+
+
+def fg_sssp_csr_noalloc(n, row_off, col, w, src, dist_out, stream=None):
+    """SSSP from a caller-owned device CSR without any device allocation (see include/fg.h).
+
+    For callers that cannot allocate device memory; all arrays must be CUDA
+    tensors.  Returns the status code."""
+    _check_dtype(row_off, "int64")
+    _check_dtype(col, "int32")
+    _check_dtype(w, "int32")
+    _check_dtype(dist_out, "int32")
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    return load().fg_sssp_csr_noalloc(int(n), _len(col), _ptr(row_off), _ptr(col), _ptr(w), int(src),
+                                      _ptr(dist_out), stream)
 
 
 def fg_kernel_launches() -> int:
