@@ -250,6 +250,19 @@ def dist_setup(args):
     return ws, rank, local
 
 
+def aggregate(units_local: int, seconds_local: float, pg=None, device=None):
+    """Whole-job throughput of independent replicas: total units over all ranks
+    divided by the slowest rank's time (max over ranks).  Returns (units, seconds)."""
+    if pg is None:
+        return units_local, seconds_local
+    import torch
+    t = torch.tensor([seconds_local], dtype=torch.float64, device=device)
+    u = torch.tensor([units_local], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    pg.all_reduce(u, op=pg.ReduceOp.SUM)
+    return int(u.item()), float(t.item())
+
+
 def run_ours(args):
     import torch
     import paper_1903_01665_gb300 as fg
@@ -292,11 +305,9 @@ def run_ours(args):
     launches = fg.fg_kernel_launches() - l0
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    if pg:
-        t = torch.tensor([ms], device=device)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * units / (ms * 1e-3) / 1e9
+    units_all, sec = aggregate(units, ms * 1e-3, pg, device)
+    ms = sec * 1e3
+    value = units_all / sec / 1e9
 
     # ---- roofline of the dominant kernel (largest share of device time)
     per_kernel = {}
@@ -338,11 +349,8 @@ def run_ours(args):
             u2 += r.step(e2e=True)
         barrier()
         dt = time.perf_counter() - t0
-        if pg:
-            t = torch.tensor([dt], device=device)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": round(ws * u2 / dt / 1e9, 4), "unit": "GTEPS",
+        u2, dt = aggregate(u2, dt, pg, device)
+        e2e = {"value": round(u2 / dt / 1e9, 4), "unit": "GTEPS",
                "h2d_bytes_per_step": 3 * 4 * r.g.m,
                "d2h_bytes_per_step": 4 * r.g.n * len(r.queries), "steps": k2}
 
