@@ -58,7 +58,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for src in sources():
             obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
             objs.append(obj)
-            cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
+            extra = os.environ.get("FG_NVCC_FLAGS", "").split()
+            cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
             procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
         failed = []
         for cmd, p in procs:

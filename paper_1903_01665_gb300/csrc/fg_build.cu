@@ -227,6 +227,14 @@ __global__ void k_bucket_counts(int32_t n, const uint32_t *__restrict__ ro, uint
     if (lane_id() == 0) atomicMax(max_deg, mx);
 }
 
+__global__ void k_vertex_class(int32_t n, const uint32_t *__restrict__ ro, uint8_t *cls) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t d = ro[v + 1] - ro[v];
+        cls[v] = d == 0 ? 0 : d < (uint32_t)kLowMax ? 1 : d < (uint32_t)kMidMax ? 2 : 3;
+    }
+}
+
 __global__ void k_bucket_write(int32_t n, const uint32_t *__restrict__ ro, const uint32_t *p_low,
                                const uint32_t *p_mid, const uint32_t *p_chunks, const uint32_t *p_nz,
                                const uint32_t *p_zero, int32_t *low, int32_t *mid, int2 *high, int32_t *nz,
@@ -268,6 +276,12 @@ struct Builder {
             status = (e == cudaErrorMemoryAllocation) ? FG_ERR_OUT_OF_MEMORY : FG_ERR_CUDA;
             msg = std::string("device allocation failed: ") + cudaGetErrorString(e);
             cudaGetLastError();
+            return nullptr;
+        }
+        if (g->n_allocs >= (int)(sizeof(g->allocs) / sizeof(g->allocs[0]))) {
+            cudaFreeAsync(p, st);
+            status = FG_ERR_CUDA;
+            msg = "internal error: too many graph arrays";
             return nullptr;
         }
         g->allocs[g->n_allocs++] = p;
@@ -342,7 +356,10 @@ void make_buckets(Builder &b, View &v) {
     int2 *high = b.alloc_graph<int2>(v.n_high_chunks);
     int32_t *nz = b.alloc_graph<int32_t>(v.n_nz);
     int32_t *zero = b.alloc_graph<int32_t>(v.n_zero);
+    uint8_t *vclass = b.alloc_graph<uint8_t>(n);
     if (b.status != FG_OK) return;
+    k_vertex_class<<<grid_for(n), kBlock, 0, b.st>>>(n, v.row_off, vclass);
+    count_launch();
     k_bucket_write<<<grid_for(n), kBlock, 0, b.st>>>(n, v.row_off, p_low, p_mid, p_chunks, p_nz, p_zero, low,
                                                      mid, high, nz, zero);
     count_launch();
@@ -352,6 +369,7 @@ void make_buckets(Builder &b, View &v) {
     v.high = high;
     v.nz = nz;
     v.zero = zero;
+    v.vclass = vclass;
     cudaFreeAsync(f, b.st);
     cudaFreeAsync(p, b.st);
     cudaFreeAsync(mx, b.st);

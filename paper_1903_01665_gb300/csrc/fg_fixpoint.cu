@@ -53,13 +53,17 @@ __device__ __forceinline__ T block_sum(T x) {
 //                      lower u's own value here (CC pointer jumping); it then
 //                      sets rq if u must be re-queued for the next generation.
 //   own(u, val)     -- once per expanded vertex (sync: carry cur[u] into next)
-//   edge(e, val, a, v) -- relax edge e from a source with value val; returns
-//                      true if target v must be appended to the worklist.
+//   cand(val, e, c, a) -- the candidate value of edge e from a source value
+//                      val (false: dropped, e.g. >= INT32_MAX)
+//   probe(v)        -- the target's current value, to compare against
+//   commit(v, c, pv, a) -- apply a candidate; true if v must be appended to
+//                      the worklist.
+// Splitting a relaxation into cand / probe / commit lets the expansions
+// issue the loads of several edges before using any of them.
 
 // Synchronous SSSP / CC: Jacobi round r reads cur, lowers next.
 template <int ALGO>
 struct SyncOp {
-    const int32_t *__restrict__ col;
     const int32_t *__restrict__ w;
     const int32_t *cur;
     int32_t *next;
@@ -72,26 +76,26 @@ struct SyncOp {
         val = ldcg(cur + u);
         return true;
     }
-    __device__ __forceinline__ void own(int32_t u, int32_t val) const {
-        if (ldcg(next + u) > val) atomicMin(next + u, val);
-    }
-    __device__ __forceinline__ bool edge(uint32_t e, int32_t val, Acc &a, int32_t &v) const {
-        v = __ldg(col + e);
-        int32_t cand;
+    __device__ __forceinline__ void own(int32_t u, int32_t val) const { red_min(next + u, val); }
+    __device__ __forceinline__ bool cand(int32_t val, uint32_t e, int32_t &c, Acc &a) const {
         if (ALGO == kSSSP) {
-            uint32_t c = (uint32_t)val + (uint32_t)__ldg(w + e);
-            if (c >= (uint32_t)kInf) { a.overflow = 1; return false; }
-            cand = (int32_t)c;
+            uint32_t x = (uint32_t)val + (uint32_t)__ldg(w + e);
+            if (x >= (uint32_t)kInf) { a.overflow = 1; return false; }
+            c = (int32_t)x;
         } else {
-            cand = val;
+            c = val;
         }
-        if (cand < ldcg(cur + v)) {
-            int32_t old = atomicMin(next + v, cand);
-            if (old > cand) {
-                stcg(snext + v, r + 1);
-                a.changed++;
-                a.updates++;
-            }
+        return true;
+    }
+    __device__ __forceinline__ int32_t probe(int32_t v) const { return ldcg(cur + v); }
+    // v changes this round iff some candidate is below its previous-round
+    // value, so any such candidate may mark it: the MIN needs no return value.
+    __device__ __forceinline__ bool commit(int32_t v, int32_t c, int32_t pv, Acc &a) const {
+        if (c < pv) {
+            red_min(next + v, c);
+            stcg(snext + v, r + 1);
+            a.changed++;
+            a.updates++;
         }
         return false;
     }
@@ -99,7 +103,6 @@ struct SyncOp {
 
 // Level-synchronous BFS (Alg. 3): in place, filter dist == lev.
 struct BfsSyncOp {
-    const int32_t *__restrict__ col;
     int32_t *L;
     int32_t lev;
 
@@ -108,10 +111,14 @@ struct BfsSyncOp {
         return ldcg(L + u) == lev;
     }
     __device__ __forceinline__ void own(int32_t, int32_t) const {}
-    __device__ __forceinline__ bool edge(uint32_t e, int32_t, Acc &a, int32_t &v) const {
-        v = __ldg(col + e);
-        if (ldcg(L + v) > lev + 1) {
-            stcg(L + v, lev + 1);
+    __device__ __forceinline__ bool cand(int32_t, uint32_t, int32_t &c, Acc &) const {
+        c = lev + 1;
+        return true;
+    }
+    __device__ __forceinline__ int32_t probe(int32_t v) const { return ldcg(L + v); }
+    __device__ __forceinline__ bool commit(int32_t v, int32_t c, int32_t pv, Acc &a) const {
+        if (pv > c) {
+            stcg(L + v, c);
             a.changed++;
             a.updates++;
         }
@@ -122,7 +129,6 @@ struct BfsSyncOp {
 // Asynchronous SSSP / CC: in place, push on decrease, dedup by generation stamp.
 template <int ALGO>
 struct AsyncOp {
-    const int32_t *__restrict__ col;
     const int32_t *__restrict__ w;
     int32_t *D;
     int32_t *stamp;
@@ -149,22 +155,25 @@ struct AsyncOp {
         return true;
     }
     __device__ __forceinline__ void own(int32_t, int32_t) const {}
-    __device__ __forceinline__ bool edge(uint32_t e, int32_t val, Acc &a, int32_t &v) const {
-        v = __ldg(col + e);
-        int32_t cand;
+    __device__ __forceinline__ bool cand(int32_t val, uint32_t e, int32_t &c, Acc &a) const {
         if (ALGO == kSSSP) {
-            uint32_t c = (uint32_t)val + (uint32_t)__ldg(w + e);
-            if (c >= (uint32_t)kInf) { a.overflow = 1; return false; }
-            cand = (int32_t)c;
+            uint32_t x = (uint32_t)val + (uint32_t)__ldg(w + e);
+            if (x >= (uint32_t)kInf) { a.overflow = 1; return false; }
+            c = (int32_t)x;
         } else {
-            cand = val;
+            c = val;
         }
-        if (cand < ldcg(D + v)) {
-            int32_t old = atomicMin(D + v, cand);
-            if (old > cand) {
-                a.updates++;
-                return atomicExch(stamp + v, gen + 1) != gen + 1;
-            }
+        return true;
+    }
+    __device__ __forceinline__ int32_t probe(int32_t v) const { return ldcg(D + v); }
+    // A candidate below the value just read lowers v or loses to an even
+    // lower one; either way v has changed in this generation and is queued
+    // (once, by the stamp) for the next.
+    __device__ __forceinline__ bool commit(int32_t v, int32_t c, int32_t pv, Acc &a) const {
+        if (c < pv) {
+            red_min(D + v, c);
+            a.updates++;
+            return atomicExch(stamp + v, gen + 1) != gen + 1;
         }
         return false;
     }
@@ -172,7 +181,6 @@ struct AsyncOp {
 
 // Asynchronous BFS: frontier queue; a vertex is claimed once by CAS from INF.
 struct BfsAsyncOp {
-    const int32_t *__restrict__ col;
     int32_t *L;
     int32_t gen;
 
@@ -181,10 +189,14 @@ struct BfsAsyncOp {
         return true;
     }
     __device__ __forceinline__ void own(int32_t, int32_t) const {}
-    __device__ __forceinline__ bool edge(uint32_t e, int32_t, Acc &a, int32_t &v) const {
-        v = __ldg(col + e);
-        if (ldcg(L + v) != kInf) return false;
-        if (atomicCAS(L + v, kInf, gen + 1) == kInf) {
+    __device__ __forceinline__ bool cand(int32_t, uint32_t, int32_t &c, Acc &) const {
+        c = gen + 1;
+        return true;
+    }
+    __device__ __forceinline__ int32_t probe(int32_t v) const { return ldcg(L + v); }
+    __device__ __forceinline__ bool commit(int32_t v, int32_t c, int32_t pv, Acc &a) const {
+        if (pv != kInf) return false;
+        if (atomicCAS(L + v, kInf, c) == kInf) {
             a.updates++;
             return true;
         }
@@ -194,7 +206,6 @@ struct BfsAsyncOp {
 
 // One full sweep with every vertex active (roofline measurement).
 struct SweepOp {
-    const int32_t *__restrict__ col;
     const int32_t *__restrict__ w;
     const int32_t *cur;
     int32_t *next;
@@ -204,14 +215,16 @@ struct SweepOp {
         return val != kInf;
     }
     __device__ __forceinline__ void own(int32_t, int32_t) const {}
-    __device__ __forceinline__ bool edge(uint32_t e, int32_t val, Acc &a, int32_t &v) const {
-        v = __ldg(col + e);
-        uint32_t c = (uint32_t)val + (uint32_t)__ldg(w + e);
-        if (c >= (uint32_t)kInf) { a.overflow = 1; return false; }
-        int32_t cand = (int32_t)c;
-        if (cand < ldcg(next + v)) {
-            int32_t old = atomicMin(next + v, cand);
-            if (old > cand) a.updates++;
+    __device__ __forceinline__ bool cand(int32_t val, uint32_t e, int32_t &c, Acc &a) const {
+        uint32_t x = (uint32_t)val + (uint32_t)__ldg(w + e);
+        if (x >= (uint32_t)kInf) { a.overflow = 1; return false; }
+        c = (int32_t)x;
+        return true;
+    }
+    __device__ __forceinline__ int32_t probe(int32_t v) const { return ldcg(next + v); }
+    __device__ __forceinline__ bool commit(int32_t v, int32_t c, int32_t pv, Acc &a) const {
+        if (c < pv) {
+            if (atomicMin(next + v, c) > c) a.updates++;
         }
         return false;
     }
@@ -220,29 +233,78 @@ struct SweepOp {
 // ================================================================ appenders
 struct NoPush {
     __device__ __forceinline__ void operator()(bool, int32_t, Acc &) const {}
+    __device__ __forceinline__ void flush() const {}
 };
+
+// Per-warp staging buffer of worklist appends in shared memory: appends go
+// to the warp's buffer (ballot + prefix, no atomics) and reach the global
+// list in blocks, one atomicAdd on the list's size per block, so that
+// thousands of warps do not serialise on one counter.
+constexpr int kPushBuf = 256;
+struct WarpBuf {
+    int32_t item[kPushBuf];
+    int count;
+};
+
+__device__ __forceinline__ void warp_flush(WarpBuf *b, int cnt, int32_t *list, int *size, int32_t cap, Ctrl *c) {
+    __syncwarp();
+    int base = 0;
+    if (lane_id() == 0) base = atomicAdd(size, cnt);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int i = (int)lane_id(); i < cnt; i += 32) {
+        int pos = base + i;
+        if (pos < cap) list[pos] = b->item[i];
+        else atomicOr(&c->status, kStWorklist);
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void buffered_append(bool want, int32_t v, WarpBuf *b, int32_t *list, int *size,
+                                                int32_t cap, Ctrl *c) {
+    unsigned bal = __ballot_sync(0xffffffffu, want);
+    if (bal == 0) return;
+    int n = __popc(bal);
+    int cnt = b->count;
+    if (cnt + n > kPushBuf) {
+        warp_flush(b, cnt, list, size, cap, c);
+        cnt = 0;
+    }
+    if (want) b->item[cnt + __popc(bal & lanemask_lt())] = v;
+    __syncwarp();
+    if (lane_id() == 0) b->count = cnt + n;
+    __syncwarp();
+}
+
+__device__ __forceinline__ void buffered_flush(WarpBuf *b, int32_t *list, int *size, int32_t cap, Ctrl *c) {
+    int cnt = b->count;
+    if (cnt > 0) warp_flush(b, cnt, list, size, cap, c);
+    __syncwarp();
+    if (lane_id() == 0) b->count = 0;
+    __syncwarp();
+}
 
 // vertex-async: append to the class list of the target's out-degree
 struct ClassPush {
     const uint32_t *__restrict__ row_off;
+    const uint8_t *__restrict__ vclass;   // 0 no out-edge, 1 low, 2 mid, 3 high
     int32_t *low, *mid;
     int2 *high;
     int *size;          // [3]
     int32_t cap_low, cap_mid, cap_high;
+    WarpBuf *buf_low, *buf_mid;           // this warp's staging buffers
     Ctrl *c;
 
     __device__ __forceinline__ void operator()(bool want, int32_t v, Acc &a) const {
         int cls = -1;
-        uint32_t b = 0, d = 0;
         if (want) {
-            b = __ldg(row_off + v);
-            d = __ldg(row_off + v + 1) - b;
-            cls = d == 0 ? -1 : d < (uint32_t)kLowMax ? kWlLow : d < (uint32_t)kMidMax ? kWlMid : kWlHigh;
+            cls = (int)__ldg(vclass + v) - 1;
             if (cls >= 0) a.pushes++;
         }
-        warp_append(0xffffffffu, cls == kWlLow, v, low, &size[kWlLow], cap_low, c);
-        warp_append(0xffffffffu, cls == kWlMid, v, mid, &size[kWlMid], cap_mid, c);
+        if (__ballot_sync(0xffffffffu, cls >= 0) == 0) return;
+        buffered_append(cls == kWlLow, v, buf_low, low, &size[kWlLow], cap_low, c);
+        buffered_append(cls == kWlMid, v, buf_mid, mid, &size[kWlMid], cap_mid, c);
         if (cls == kWlHigh) {
+            uint32_t b = __ldg(row_off + v), d = __ldg(row_off + v + 1) - b;
             int nck = (int)((d + kChunk - 1) / kChunk);
             int base = atomicAdd(&size[kWlHigh], nck);
             if (base + nck <= cap_high) {
@@ -252,25 +314,172 @@ struct ClassPush {
             }
         }
     }
+    __device__ __forceinline__ void flush() const {
+        buffered_flush(buf_low, low, &size[kWlLow], cap_low, c);
+        buffered_flush(buf_mid, mid, &size[kWlMid], cap_mid, c);
+    }
 };
 
 // edge-async: one list of vertices with >= 1 out-edge
 struct ListPush {
-    const uint32_t *__restrict__ row_off;
+    const uint8_t *__restrict__ vclass;
     int32_t *list;
     int *size;
     int32_t cap;
+    WarpBuf *buf;
     Ctrl *c;
 
     __device__ __forceinline__ void operator()(bool want, int32_t v, Acc &a) const {
         bool ok = false;
         if (want) {
-            ok = __ldg(row_off + v + 1) > __ldg(row_off + v);
+            ok = __ldg(vclass + v) != 0;
             if (ok) a.pushes++;
         }
-        warp_append(0xffffffffu, ok, v, list, size, cap, c);
+        buffered_append(ok, v, buf, list, size, cap, c);
     }
+    __device__ __forceinline__ void flush() const { buffered_flush(buf, list, size, cap, c); }
 };
+
+// ================================================================ batched relaxation
+constexpr int kU = 4;   // edges per thread per loop iteration
+
+// Relax up to kU edges per thread: every load of the batch is issued before
+// any result is used.  All lanes of the warp call it (the appends are
+// warp-collective); lanes with in[j] == false take no part in edge j.
+template <class OP, class PUSH, int N>
+__device__ __forceinline__ void relax_batch(const int32_t *__restrict__ col, const OP &op, const PUSH &push,
+                                            const uint32_t (&e)[N], const int32_t (&val)[N],
+                                            const bool (&in)[N], Acc &a) {
+    int32_t v[N], c[N], pv[N];
+    bool ok[N];
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+        v[j] = 0;
+        c[j] = 0;
+        ok[j] = in[j];
+        if (ok[j]) {
+            v[j] = __ldg(col + e[j]);
+            ok[j] = op.cand(val[j], e[j], c[j], a);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < N; j++) pv[j] = ok[j] ? op.probe(v[j]) : 0;
+    bool want[N];
+#pragma unroll
+    for (int j = 0; j < N; j++) want[j] = ok[j] && op.commit(v[j], c[j], pv[j], a);
+#pragma unroll
+    for (int j = 0; j < N; j++) push(want[j], v[j], a);
+}
+
+// Edges of up to 32 rows, given per lane as (row start, degree < 32, value),
+// redistributed over the warp: a warp-wide prefix sum of the degrees, and each
+// lane finds the owner row of its edge by a 5-step shuffle search, so that the
+// edge loads of a batch are contiguous.
+template <class OP, class PUSH>
+__device__ __forceinline__ void relax_rows_of_warp(const int32_t *__restrict__ col, const OP &op, const PUSH &push,
+                                                   uint32_t rb, uint32_t d, int32_t vv, Acc &a) {
+    const unsigned lane = lane_id();
+    uint32_t incl = warp_inclusive_scan(d);
+    uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    uint32_t excl = incl - d;
+    if (lane == 0) a.edges += total;
+    for (uint32_t k0 = 0; k0 < total; k0 += 32 * kU) {
+        uint32_t e[kU];
+        int32_t val[kU];
+        bool in[kU];
+#pragma unroll
+        for (int j = 0; j < kU; j++) {
+            uint32_t k = k0 + 32 * j + lane;
+            int owner = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                uint32_t pv = __shfl_sync(0xffffffffu, incl, owner + step - 1);
+                if (pv <= k) owner += step;
+            }
+            uint32_t ob = __shfl_sync(0xffffffffu, rb, owner);
+            uint32_t oe = __shfl_sync(0xffffffffu, excl, owner);
+            val[j] = __shfl_sync(0xffffffffu, vv, owner);
+            e[j] = ob + (k - oe);
+            in[j] = k < total;
+        }
+        relax_batch(col, op, push, e, val, in, a);
+    }
+}
+
+// Synchronous low-degree path: the warp scans 128 consecutive vertex ids per
+// step with 128-bit loads of the activity word (round stamp, or BFS level),
+// compacts the active vertices with 1..31 out-edges into shared memory, and
+// relaxes their edges 32 rows at a time.  Mid and high vertices are expanded
+// from their bucket lists; vertices without out-edges have nothing to expand.
+template <class OP>
+__device__ __forceinline__ void expand_low_dense(const uint32_t *__restrict__ row_off, const int32_t *__restrict__ col,
+                                                 const int32_t *actw, int32_t act_val, int32_t n, const OP &op,
+                                                 Acc &a) {
+    __shared__ uint32_t s_rb[kWarps][128];
+    __shared__ uint32_t s_d[kWarps][128];
+    __shared__ int32_t s_v[kWarps][128];
+    const unsigned lane = lane_id();
+    const int wid = threadIdx.x >> 5;
+    const int64_t gw = (blockIdx.x * (int64_t)kBlock + threadIdx.x) >> 5;
+    const int64_t nw = (int64_t)gridDim.x * kWarps;
+    for (int64_t w0 = gw * 128; w0 < n; w0 += nw * 128) {
+        const int64_t v0 = w0 + 4 * lane;
+        int32_t st[4];
+        if (v0 + 3 < n) {
+            int4 t = __ldcg(reinterpret_cast<const int4 *>(actw + v0));
+            st[0] = t.x; st[1] = t.y; st[2] = t.z; st[3] = t.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; j++) st[j] = (v0 + j < n) ? ldcg(actw + v0 + j) : act_val - 1;
+        }
+        bool act[4];
+        uint32_t rb[4], d[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            act[j] = st[j] == act_val;
+            rb[j] = 0;
+            d[j] = 0;
+            if (act[j]) {
+                rb[j] = __ldg(row_off + v0 + j);
+                d[j] = __ldg(row_off + v0 + j + 1) - rb[j];
+                act[j] = d[j] >= 1 && d[j] < (uint32_t)kLowMax;
+            }
+        }
+        unsigned cnt_lane = act[0] + act[1] + act[2] + act[3];
+        unsigned any = __ballot_sync(0xffffffffu, cnt_lane != 0);
+        if (!any) continue;
+        unsigned incl = warp_inclusive_scan(cnt_lane);
+        unsigned tot = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned slot = incl - cnt_lane;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if (act[j]) {
+                int32_t val;
+                bool rq;
+                op.active((int32_t)(v0 + j), val, rq);
+                op.own((int32_t)(v0 + j), val);
+                s_rb[wid][slot] = rb[j];
+                s_d[wid][slot] = d[j];
+                s_v[wid][slot] = val;
+                slot++;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) a.verts += tot;
+        for (unsigned g0 = 0; g0 < tot; g0 += 32) {
+            unsigned k = g0 + lane;
+            uint32_t r0 = 0, dd = 0;
+            int32_t vv = 0;
+            if (k < tot) {
+                r0 = s_rb[wid][k];
+                dd = s_d[wid][k];
+                vv = s_v[wid][k];
+            }
+            relax_rows_of_warp(col, op, NoPush{}, r0, dd, vv, a);
+        }
+        __syncwarp();
+    }
+}
 
 // ================================================================ expansions
 // Bucketed vertex expansion: high chunks by whole CTAs, mid vertices by warps,
@@ -278,9 +487,10 @@ struct ListPush {
 // (a warp-wide prefix sum of the degrees; each lane finds the owner of its
 // edge by a 5-step shuffle search), so edge loads are contiguous.
 template <class OP, class PUSH>
-__device__ __forceinline__ void expand_vertices(const uint32_t *__restrict__ row_off, const int32_t *low,
-                                                int n_low, const int32_t *mid, int n_mid, const int2 *high,
-                                                int n_high, const OP &op, const PUSH &push, Acc &a) {
+__device__ __forceinline__ void expand_vertices(const uint32_t *__restrict__ row_off, const int32_t *__restrict__ col,
+                                                const int32_t *low, int n_low, const int32_t *mid, int n_mid,
+                                                const int2 *high, int n_high, const OP &op, const PUSH &push,
+                                                Acc &a) {
     __shared__ int32_t s_val;
     __shared__ int s_act, s_rq;
     const unsigned lane = lane_id();
@@ -305,15 +515,20 @@ __device__ __forceinline__ void expand_vertices(const uint32_t *__restrict__ row
         __syncthreads();
         push(threadIdx.x == 0 && s_rq, ch.x, a);
         if (s_act) {
-            int32_t val = s_val;
+            int32_t vv = s_val;
             uint32_t e0 = (uint32_t)ch.y, e1 = min(e0 + (uint32_t)kChunk, re);
             if (threadIdx.x == 0) a.edges += e1 - e0;
-            for (uint32_t base = e0; base < e1; base += kBlock) {
-                uint32_t e = base + threadIdx.x;
-                int32_t v = 0;
-                bool want = false;
-                if (e < e1) want = op.edge(e, val, a, v);
-                push(want, v, a);
+            for (uint32_t base = e0; base < e1; base += kBlock * kU) {
+                uint32_t e[kU];
+                int32_t val[kU];
+                bool in[kU];
+#pragma unroll
+                for (int j = 0; j < kU; j++) {
+                    e[j] = base + j * kBlock + threadIdx.x;
+                    in[j] = e[j] < e1;
+                    val[j] = vv;
+                }
+                relax_batch(col, op, push, e, val, in, a);
             }
         }
         __syncthreads();
@@ -323,106 +538,99 @@ __device__ __forceinline__ void expand_vertices(const uint32_t *__restrict__ row
     // mid-degree vertices: one warp each
     for (int i = gw; i < n_mid; i += nw) {
         int32_t u = ldcg(mid + i);
-        int32_t val = 0;
+        int32_t vv = 0;
         int act = 0;
         bool rq = false;
         if (lane == 0) {
-            act = op.active(u, val, rq);
-            if (act) op.own(u, val);
+            act = op.active(u, vv, rq);
+            if (act) op.own(u, vv);
         }
         push(lane == 0 && rq, u, a);
         act = __shfl_sync(0xffffffffu, act, 0);
         if (!act) continue;
-        val = __shfl_sync(0xffffffffu, val, 0);
-        uint32_t b = __ldg(row_off + u), e = __ldg(row_off + u + 1);
+        vv = __shfl_sync(0xffffffffu, vv, 0);
+        uint32_t b = __ldg(row_off + u), en = __ldg(row_off + u + 1);
         if (lane == 0) {
             a.verts++;
-            a.edges += e - b;
+            a.edges += en - b;
         }
-        for (uint32_t base = b; base < e; base += 32) {
-            uint32_t k = base + lane;
-            int32_t v = 0;
-            bool want = false;
-            if (k < e) want = op.edge(k, val, a, v);
-            push(want, v, a);
+        for (uint32_t base = b; base < en; base += 32 * kU) {
+            uint32_t e[kU];
+            int32_t val[kU];
+            bool in[kU];
+#pragma unroll
+            for (int j = 0; j < kU; j++) {
+                e[j] = base + 32 * j + lane;
+                in[j] = e[j] < en;
+                val[j] = vv;
+            }
+            relax_batch(col, op, push, e, val, in, a);
         }
     }
     // low-degree vertices: a thread each, edges redistributed over the warp
     for (int base = gw * 32; base < n_low; base += nw * 32) {
         int i = base + (int)lane;
-        int32_t val = 0, u = 0;
+        int32_t vv = 0, u = 0;
         uint32_t rb = 0, d = 0;
         bool rq = false;
         if (i < n_low) {
             u = ldcg(low + i);
-            if (op.active(u, val, rq)) {
-                op.own(u, val);
+            if (op.active(u, vv, rq)) {
+                op.own(u, vv);
                 rb = __ldg(row_off + u);
                 d = __ldg(row_off + u + 1) - rb;
                 a.verts++;
             }
         }
         push(rq, u, a);
-        uint32_t incl = warp_inclusive_scan(d);
-        uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        uint32_t excl = incl - d;
-        if (lane == 0) a.edges += total;
-        for (uint32_t k0 = 0; k0 < total; k0 += 32) {
-            uint32_t k = k0 + lane;
-            int owner = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                uint32_t pv = __shfl_sync(0xffffffffu, incl, owner + step - 1);
-                if (pv <= k) owner += step;
-            }
-            uint32_t ob = __shfl_sync(0xffffffffu, rb, owner);
-            uint32_t oe = __shfl_sync(0xffffffffu, excl, owner);
-            int32_t ov = __shfl_sync(0xffffffffu, val, owner);
-            int32_t v = 0;
-            bool want = false;
-            if (k < total) want = op.edge(ob + (k - oe), ov, a, v);
-            push(want, v, a);
-        }
+        relax_rows_of_warp(col, op, push, rb, d, vv, a);
     }
 }
 
-// Edge-parallel sweep over the source-sorted COO with 128-bit loads of src
-// (four edges per load); the activity test of a source is reused across
-// consecutive edges of the same source.
+// Edge-parallel sweep over the source-sorted COO: each thread takes four
+// consecutive edges with 128-bit loads of src (and of col and w through the
+// op's cand), and the activity test of a source is reused across consecutive
+// edges of the same source.
 template <class OP>
-__device__ __forceinline__ void expand_edges(const int32_t *__restrict__ src, int64_t m, const OP &op,
-                                             Acc &a) {
+__device__ __forceinline__ void expand_edges(const int32_t *__restrict__ src, const int32_t *__restrict__ col,
+                                             int64_t m, const OP &op, Acc &a) {
+    static_assert(kU == 4, "one int4 of sources per thread");
     const int64_t tid = blockIdx.x * (int64_t)kBlock + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * kBlock;
     const int64_t m4 = m >> 2;
     const int4 *src4 = reinterpret_cast<const int4 *>(src);
     for (int64_t q = tid; q < m4; q += nth) {
-        int4 s = __ldg(src4 + q);
-        int32_t us[4] = {s.x, s.y, s.z, s.w};
+        int4 s4 = __ldg(src4 + q);
+        int32_t us[4] = {s4.x, s4.y, s4.z, s4.w};
+        uint32_t e[4];
+        int32_t val[4];
+        bool in[4];
         int32_t prev = -1, pval = 0;
         bool pact = false;
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            int32_t u = us[j];
-            if (u != prev) {
+            if (us[j] != prev) {
                 bool rq;
-                pact = op.active(u, pval, rq);
-                prev = u;
+                pact = op.active(us[j], pval, rq);
+                prev = us[j];
             }
-            if (pact) {
-                int32_t v;
-                op.edge((uint32_t)(4 * q + j), pval, a, v);
-                a.edges++;
-            }
+            e[j] = (uint32_t)(4 * q + j);
+            val[j] = pval;
+            in[j] = pact;
+            a.edges += pact;
         }
+        relax_batch(col, op, NoPush{}, e, val, in, a);
     }
-    for (int64_t e = 4 * m4 + tid; e < m; e += nth) {
-        int32_t val;
+    for (int64_t x = 4 * m4 + tid; x < m; x += nth) {
+        int32_t vv;
         bool rq;
-        int32_t u = __ldg(src + e);
-        if (op.active(u, val, rq)) {
-            int32_t v;
-            op.edge((uint32_t)e, val, a, v);
+        int32_t u = __ldg(src + x);
+        if (op.active(u, vv, rq)) {
+            int32_t v = __ldg(col + x), c, pv;
+            if (op.cand(vv, (uint32_t)x, c, a)) {
+                pv = op.probe(v);
+                op.commit(v, c, pv, a);
+            }
             a.edges++;
         }
     }
@@ -465,16 +673,15 @@ __device__ __forceinline__ void lb_prefix(const uint32_t *__restrict__ row_off, 
 }
 
 constexpr int kMaxGrid = 152 * 8;   // persistent CTAs (lb prefix table size)
-constexpr int kLbEdgesPerThread = 4;
 
 // Phase 2 (after the barrier): the edge space [0, T) is split evenly over the
 // CTAs; each CTA walks its range in tiles, staging up to kBlock items'
 // offsets, row starts and values in shared memory, and every thread finds the
 // owner of its edges by binary search in shared memory.
 template <class OP, class PUSH>
-__device__ __forceinline__ void lb_expand(const uint32_t *__restrict__ row_off, const int32_t *items, int n_items,
-                                          const uint32_t *lb_off, const uint32_t *lb_blk, const OP &op,
-                                          const PUSH &push, Acc &a) {
+__device__ __forceinline__ void lb_expand(const uint32_t *__restrict__ row_off, const int32_t *__restrict__ col,
+                                          const int32_t *items, int n_items, const uint32_t *lb_off,
+                                          const uint32_t *lb_blk, const OP &op, const PUSH &push, Acc &a) {
     __shared__ uint32_t sP[kMaxGrid + 1];
     __shared__ uint32_t s_goff[kBlock + 1];
     __shared__ uint32_t s_rb[kBlock];
@@ -544,24 +751,28 @@ __device__ __forceinline__ void lb_expand(const uint32_t *__restrict__ row_off, 
         push(rq, u, a);
         if (threadIdx.x == 0) s_goff[cnt] = (i0 + cnt < n_items) ? goff(i0 + cnt) : T;
         __syncthreads();
-        uint32_t t1 = min((uint32_t)hi, min(t0 + (uint32_t)(kBlock * kLbEdgesPerThread), s_goff[cnt]));
+        uint32_t t1 = min((uint32_t)hi, min(t0 + (uint32_t)(kBlock * kU), s_goff[cnt]));
+        uint32_t e[kU];
+        int32_t val[kU];
+        bool in[kU];
 #pragma unroll
-        for (int j = 0; j < kLbEdgesPerThread; j++) {
+        for (int j = 0; j < kU; j++) {
             uint32_t x = t0 + j * kBlock + threadIdx.x;
-            bool in = x < t1;
-            int32_t v = 0;
-            bool want = false;
-            if (in) {
+            in[j] = x < t1;
+            e[j] = 0;
+            val[j] = 0;
+            if (in[j]) {
                 int l = 0, r = cnt - 1;
                 while (l < r) {
                     int mdl = (l + r + 1) >> 1;
                     if (s_goff[mdl] <= x) l = mdl; else r = mdl - 1;
                 }
-                want = op.edge(s_rb[l] + (x - s_goff[l]), s_val[l], a, v);
+                e[j] = s_rb[l] + (x - s_goff[l]);
+                val[j] = s_val[l];
                 a.edges++;
             }
-            push(want, v, a);
         }
+        relax_batch(col, op, push, e, val, in, a);
         if (threadIdx.x == 0) {
             // next tile starts at edge t1; find its item among the staged ones
             int l = 0, r = cnt;   // s_goff[cnt] may equal t1 (then item i0 + cnt)
@@ -576,12 +787,16 @@ __device__ __forceinline__ void lb_expand(const uint32_t *__restrict__ row_off, 
         t0 = s_t1;
         __syncthreads();
     }
-    if (threadIdx.x == 0) a.verts += 0;
 }
 
 // ================================================================ the kernel
+// Resident CTAs per SM the register budget is sized for: the synchronous
+// modes gain from more warps in flight; the worklist modes do not.
+template <int MODE>
+constexpr int min_blocks() { return (MODE == kVertexSync || MODE == kEdgeSync) ? 6 : 4; }
+
 template <int ALGO, int MODE>
-__global__ void __launch_bounds__(kBlock) fixpoint_kernel(Params p) {
+__global__ void __launch_bounds__(kBlock, min_blocks<MODE>()) fixpoint_kernel(Params p) {
     constexpr bool SYNC = (MODE == kVertexSync || MODE == kEdgeSync);
     Ctrl *c = p.ctrl;
     const View &g = p.g;
@@ -637,25 +852,40 @@ __global__ void __launch_bounds__(kBlock) fixpoint_kernel(Params p) {
             if (tid == 0) c->changed[(r + 1) % 3] = 0;
             rounds = r;
             if (ALGO == kBFS) {
-                BfsSyncOp op{g.col, p.A, r - 1};
-                if (MODE == kVertexSync)
-                    expand_vertices(g.row_off, g.low, g.n_low, g.mid, g.n_mid, g.high, g.n_high_chunks, op,
+                BfsSyncOp op{p.A, r - 1};
+                if (MODE == kVertexSync) {
+                    expand_vertices(g.row_off, g.col, g.low, 0, g.mid, g.n_mid, g.high, g.n_high_chunks, op,
                                     NoPush{}, a);
-                else
-                    expand_edges(g.src, g.m, op, a);
+                    expand_low_dense(g.row_off, g.col, p.A, r - 1, n, op, a);
+                } else {
+                    expand_edges(g.src, g.col, g.m, op, a);
+                }
             } else {
                 const int32_t *cur = (r & 1) ? p.A : p.B;
                 int32_t *next = (r & 1) ? p.B : p.A;
                 const int32_t *scur = (r & 1) ? p.S1 : p.S0;
                 int32_t *snext = (r & 1) ? p.S0 : p.S1;
-                SyncOp<ALGO> op{g.col, g.w, cur, next, scur, snext, r};
+                SyncOp<ALGO> op{g.w, cur, next, scur, snext, r};
                 if (MODE == kVertexSync) {
-                    expand_vertices(g.row_off, g.low, g.n_low, g.mid, g.n_mid, g.high, g.n_high_chunks, op,
+                    expand_vertices(g.row_off, g.col, g.low, 0, g.mid, g.n_mid, g.high, g.n_high_chunks, op,
                                     NoPush{}, a);
+                    expand_low_dense(g.row_off, g.col, scur, r, n, op, a);
                 } else {
-                    expand_edges(g.src, g.m, op, a);
+                    expand_edges(g.src, g.col, g.m, op, a);
                     // carry the values of last round's changed vertices into next
-                    for (int64_t v = tid; v < n; v += nth) {
+                    const int64_t n4 = n >> 2;
+                    for (int64_t q = tid; q < n4; q += nth) {
+                        int4 t = __ldcg(reinterpret_cast<const int4 *>(scur) + q);
+                        int32_t st4[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+                        for (int j = 0; j < 4; j++) {
+                            if (st4[j] == r) {
+                                op.own((int32_t)(4 * q + j), ldcg(cur + 4 * q + j));
+                                a.verts++;
+                            }
+                        }
+                    }
+                    for (int64_t v = 4 * n4 + tid; v < n; v += nth) {
                         int32_t val;
                         bool rq;
                         if (op.active((int32_t)v, val, rq)) {
@@ -714,6 +944,13 @@ __global__ void __launch_bounds__(kBlock) fixpoint_kernel(Params p) {
             }
         }
     } else if (!SYNC && ok) {
+        __shared__ WarpBuf s_buf[kWarps][2];
+        if (lane_id() == 0) {
+            s_buf[threadIdx.x >> 5][0].count = 0;
+            s_buf[threadIdx.x >> 5][1].count = 0;
+        }
+        __syncwarp();
+        WarpBuf *wb = s_buf[threadIdx.x >> 5];
         for (int gen = 0;; gen++) {
             const int in_slot = gen % 3, out_slot = (gen + 1) % 3;
             const bool initial_cc = (ALGO == kCC && gen == 0);
@@ -740,31 +977,33 @@ __global__ void __launch_bounds__(kBlock) fixpoint_kernel(Params p) {
                 const int32_t *low = initial_cc ? g.low : p.wl[pi][kWlLow];
                 const int32_t *mid = initial_cc ? g.mid : p.wl[pi][kWlMid];
                 const int2 *high = initial_cc ? g.high : reinterpret_cast<const int2 *>(p.wl[pi][kWlHigh]);
-                ClassPush push{g.row_off, p.wl[po][kWlLow], p.wl[po][kWlMid],
+                ClassPush push{g.row_off, g.vclass, p.wl[po][kWlLow], p.wl[po][kWlMid],
                                reinterpret_cast<int2 *>(p.wl[po][kWlHigh]), osize,
-                               p.wl_cap[kWlLow], p.wl_cap[kWlMid], p.wl_cap[kWlHigh] / 2, c};
+                               p.wl_cap[kWlLow], p.wl_cap[kWlMid], p.wl_cap[kWlHigh] / 2, &wb[0], &wb[1], c};
                 if (ALGO == kBFS) {
-                    BfsAsyncOp op{g.col, p.A, gen};
-                    expand_vertices(g.row_off, low, n_in[kWlLow], mid, n_in[kWlMid], high, n_in[kWlHigh], op,
-                                    push, a);
+                    BfsAsyncOp op{p.A, gen};
+                    expand_vertices(g.row_off, g.col, low, n_in[kWlLow], mid, n_in[kWlMid], high, n_in[kWlHigh],
+                                    op, push, a);
                 } else {
-                    AsyncOp<ALGO> op{g.col, g.w, p.A, p.S0, gen};
-                    expand_vertices(g.row_off, low, n_in[kWlLow], mid, n_in[kWlMid], high, n_in[kWlHigh], op,
-                                    push, a);
+                    AsyncOp<ALGO> op{g.w, p.A, p.S0, gen};
+                    expand_vertices(g.row_off, g.col, low, n_in[kWlLow], mid, n_in[kWlMid], high, n_in[kWlHigh],
+                                    op, push, a);
                 }
+                push.flush();
             } else {
                 const int32_t *items = initial_cc ? g.nz : p.wl[pi][0];
                 lb_prefix(g.row_off, items, n_in[0], p.lb_off, p.lb_blk);
                 if (!grid_sync(c, p.timeout_ns)) break;
-                ListPush push{g.row_off, p.wl[po][0], &osize[0], p.wl_cap[0], c};
+                ListPush push{g.vclass, p.wl[po][0], &osize[0], p.wl_cap[0], &wb[0], c};
                 a.verts += 0;
                 if (ALGO == kBFS) {
-                    BfsAsyncOp op{g.col, p.A, gen};
-                    lb_expand(g.row_off, items, n_in[0], p.lb_off, p.lb_blk, op, push, a);
+                    BfsAsyncOp op{p.A, gen};
+                    lb_expand(g.row_off, g.col, items, n_in[0], p.lb_off, p.lb_blk, op, push, a);
                 } else {
-                    AsyncOp<ALGO> op{g.col, g.w, p.A, p.S0, gen};
-                    lb_expand(g.row_off, items, n_in[0], p.lb_off, p.lb_blk, op, push, a);
+                    AsyncOp<ALGO> op{g.w, p.A, p.S0, gen};
+                    lb_expand(g.row_off, g.col, items, n_in[0], p.lb_off, p.lb_blk, op, push, a);
                 }
+                push.flush();
                 if (tid == 0) a.verts += (unsigned long long)n_in[0];
             }
             if (!grid_sync(c, p.timeout_ns)) break;
@@ -790,11 +1029,12 @@ __global__ void __launch_bounds__(kBlock) fixpoint_kernel(Params p) {
 template <int MODE>
 __global__ void __launch_bounds__(kBlock) sweep_kernel(View g, const int32_t *cur, int32_t *next, Ctrl *c) {
     Acc a;
-    SweepOp op{g.col, g.w, cur, next};
+    SweepOp op{g.w, cur, next};
     if (MODE == kVertexSync)
-        expand_vertices(g.row_off, g.low, g.n_low, g.mid, g.n_mid, g.high, g.n_high_chunks, op, NoPush{}, a);
+        expand_vertices(g.row_off, g.col, g.low, g.n_low, g.mid, g.n_mid, g.high, g.n_high_chunks, op, NoPush{},
+                        a);
     else
-        expand_edges(g.src, g.m, op, a);
+        expand_edges(g.src, g.col, g.m, op, a);
     unsigned long long eu = block_sum(a.updates);
     int of = block_sum(a.overflow);
     if (threadIdx.x == 0) {

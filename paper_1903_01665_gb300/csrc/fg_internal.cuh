@@ -40,6 +40,7 @@ struct View {
     const int2 *high = nullptr;         // {vertex, first edge} per 2048-edge chunk of >= 1024
     const int32_t *nz = nullptr;        // all vertices with >= 1 out-edge, ascending
     const int32_t *zero = nullptr;      // vertices with no out-edge, ascending
+    const uint8_t *vclass = nullptr;    // per vertex: 0 no out-edge, 1 low, 2 mid, 3 high
     int32_t n_low = 0, n_mid = 0, n_high = 0, n_high_chunks = 0, n_nz = 0, n_zero = 0;
     int32_t max_deg = 0;
 };
@@ -51,7 +52,7 @@ struct fg_graph {
     fg::View g;      // directed
     fg::View s;      // symmetrised
     fg_graph_info_t info{};
-    void *allocs[24] = {};
+    void *allocs[32] = {};
     int n_allocs = 0;
     // lazily computed diameter estimate for fg_select_mode
     mutable std::mutex mu;
@@ -127,6 +128,10 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // during the kernel, so L1 copies could be stale.
 __device__ __forceinline__ int32_t ldcg(const int32_t *p) { return __ldcg(p); }
 __device__ __forceinline__ void stcg(int32_t *p, int32_t v) { __stcg(p, v); }
+// atomic MIN whose result is not needed (a reduction: no round trip)
+__device__ __forceinline__ void red_min(int32_t *p, int32_t v) {
+    asm volatile("red.relaxed.gpu.global.min.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 // ---------------------------------------------------------------- grid barrier
 // Sense-by-generation barrier over all CTAs of a cooperative launch.  The
