@@ -87,35 +87,27 @@ def queries_for(workload: str, srcs):
 def algorithmic_bytes(algo: int, mode: int, st: dict, info: dict) -> float:
     """Bytes the variant must move for one query, from its device counters.
 
-    R rounds, Va expanded vertices, Ea relaxed edges, U successful MIN
-    updates, P worklist appends, n vertices, nz vertices with out-edges, m
-    edges (symmetrised graph for CC).  4-byte ids, values and offsets.
+    S activity words scanned (sync modes: vertex stamps or levels, and for
+    edge-sync the edge sources streamed), Va expanded vertices, Ea relaxed
+    edges, U accepted candidates, P worklist appends, n vertices.  Ids,
+    values and offsets are 4 bytes; per edge: col (+ w for SSSP) + the
+    target's value.
     """
-    R, Va, Ea, U, P = st["rounds"], st["vertices_processed"], st["edges_relaxed"], st["updates"], st["pushes"]
+    S, Va, Ea, U, P = (st["scanned"], st["vertices_processed"], st["edges_relaxed"], st["updates"],
+                       st["pushes"])
     n = info["n"]
-    if algo == 2:
-        m = info["m_sym"]
-        nz = n - info["n_isolated"]
-    else:
-        m = info["m"]
-        nz = n - info["n_zero_out"]
-    per_edge = {0: 12, 1: 8, 2: 8}[algo]          # col (+ w for SSSP) + target value
-    if mode == 0:   # vertex-sync: stamp test per listed vertex per round
+    per_edge = {0: 12, 1: 8, 2: 8}[algo]
+    if mode in (0, 2):           # sync: scans + expansion (2 offsets, value, carry) + MIN and stamp
         if algo == 1:
-            b = R * 4 * nz + Va * 8 + Ea * per_edge + U * 4
+            b = 4 * S + Va * 8 + Ea * per_edge + U * 4
         else:
-            b = R * 4 * nz + Va * 16 + Ea * per_edge + U * 12
-    elif mode == 2:  # edge-sync: src stream + source test per round
-        if algo == 1:
-            b = R * (4 * m + 4 * nz) + Ea * per_edge + U * 4
-        else:
-            b = R * (4 * m + 4 * nz + 4 * n) + Va * 8 + Ea * per_edge + U * 12
-    else:            # async: per item (item, offsets, value), per edge, per update, per push
+            b = 4 * S + Va * 16 + Ea * per_edge + U * 12
+    else:                        # async: per item (item, offsets, value), per edge, per update, per push
         item = 12 if algo == 1 else 16
         if mode == 3:
-            item += 16                              # degree prefix: item, offsets, prefix write
-        upd = 8 if algo == 1 else 16
-        b = Va * item + Ea * per_edge + U * upd + P * 12
+            item += 16           # degree prefix: item, offsets, prefix write
+        upd = 8 if algo == 1 else 12
+        b = Va * item + Ea * per_edge + U * upd + P * 8
     if algo == 2:
         b += st["jump_passes"] * n * 8
     return float(b)

@@ -147,6 +147,11 @@ typedef struct {
                                    barrier, so every other CTA's bounded wait runs out and
                                    the call returns FG_ERR_TIMEOUT (the context stays
                                    usable).  0 in normal use. */
+    uint64_t *round_trace;      /* optional device buffer: CTA 0 writes %globaltimer (ns) at
+                                   every grid barrier of the query (init, each round, and each
+                                   mid-round or pointer-jumping barrier), at most
+                                   round_trace_cap entries; NULL = no tracing */
+    int32_t round_trace_cap;
 } fg_options;
 
 typedef struct {
@@ -159,8 +164,12 @@ typedef struct {
     int64_t edges_relaxed;      /* edges whose source was active, summed over rounds */
     int64_t updates;            /* successful MIN updates */
     int64_t pushes;             /* worklist appends (async modes) */
+    int64_t scanned;            /* activity words read by the sync modes' scans (vertex ids,
+                                   or edge sources streamed by edge-sync), summed over rounds */
     float kernel_ms;            /* device time of the fixpoint kernel (CUDA events on
                                    the query's stream) */
+    int32_t barriers;           /* grid barriers the kernel passed (= trace entries written,
+                                   up to the cap) */
 } fg_stats;
 
 /*

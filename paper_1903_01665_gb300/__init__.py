@@ -44,14 +44,16 @@ FG_INF = 2**31 - 1
 class fg_options(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("max_rounds", ctypes.c_int32),
                 ("wait_timeout_ms", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("inject_missing_arrival", ctypes.c_int32)]
+                ("inject_missing_arrival", ctypes.c_int32), ("round_trace", ctypes.c_void_p),
+                ("round_trace_cap", ctypes.c_int32)]
 
 
 class fg_stats(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("rounds", ctypes.c_int32), ("jump_passes", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32), ("vertices_processed", ctypes.c_int64),
                 ("edges_relaxed", ctypes.c_int64), ("updates", ctypes.c_int64),
-                ("pushes", ctypes.c_int64), ("kernel_ms", ctypes.c_float)]
+                ("pushes", ctypes.c_int64), ("scanned", ctypes.c_int64), ("kernel_ms", ctypes.c_float),
+                ("barriers", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -200,13 +202,14 @@ def fg_select_mode(g, algo):
 
 
 def fg_run(g, algo, src, out, mode, stream=None, max_rounds=0, wait_timeout_ms=0, blocks_per_sm=0,
-           inject_missing_arrival=0):
+           inject_missing_arrival=0, round_trace=None):
     """Returns (status, fg_stats).  stream: a torch.cuda.Stream, a raw handle, or None."""
     _check_dtype(out, "int32")
     if stream is not None and hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
     opt = fg_options(stream, int(max_rounds), int(wait_timeout_ms), int(blocks_per_sm),
-                     int(inject_missing_arrival))
+                     int(inject_missing_arrival), _ptr(round_trace),
+                     int(round_trace.shape[0]) if round_trace is not None else 0)
     stats = fg_stats()
     st = load().fg_run(g, int(algo), int(src), _ptr(out), int(mode), ctypes.byref(opt), ctypes.byref(stats))
     return st, stats

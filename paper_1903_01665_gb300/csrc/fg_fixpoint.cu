@@ -27,7 +27,7 @@ namespace fg {
 namespace {
 
 struct Acc {
-    unsigned long long edges = 0, verts = 0, updates = 0, pushes = 0;
+    unsigned long long edges = 0, verts = 0, updates = 0, pushes = 0, scanned = 0;
     int changed = 0;
     int overflow = 0;
 };
@@ -77,6 +77,7 @@ struct SyncOp {
         return true;
     }
     __device__ __forceinline__ void own(int32_t u, int32_t val) const { red_min(next + u, val); }
+    __device__ __forceinline__ int32_t refresh(int32_t, int32_t val) const { return val; }
     __device__ __forceinline__ bool cand(int32_t val, uint32_t e, int32_t &c, Acc &a) const {
         if (ALGO == kSSSP) {
             uint32_t x = (uint32_t)val + (uint32_t)__ldg(w + e);
@@ -111,6 +112,7 @@ struct BfsSyncOp {
         return ldcg(L + u) == lev;
     }
     __device__ __forceinline__ void own(int32_t, int32_t) const {}
+    __device__ __forceinline__ int32_t refresh(int32_t, int32_t val) const { return val; }
     __device__ __forceinline__ bool cand(int32_t, uint32_t, int32_t &c, Acc &) const {
         c = lev + 1;
         return true;
@@ -155,6 +157,8 @@ struct AsyncOp {
         return true;
     }
     __device__ __forceinline__ void own(int32_t, int32_t) const {}
+    // in place: the latest value, read just before the vertex is expanded
+    __device__ __forceinline__ int32_t refresh(int32_t u, int32_t val) const { return min(val, ldcg(D + u)); }
     __device__ __forceinline__ bool cand(int32_t val, uint32_t e, int32_t &c, Acc &a) const {
         if (ALGO == kSSSP) {
             uint32_t x = (uint32_t)val + (uint32_t)__ldg(w + e);
@@ -189,6 +193,7 @@ struct BfsAsyncOp {
         return true;
     }
     __device__ __forceinline__ void own(int32_t, int32_t) const {}
+    __device__ __forceinline__ int32_t refresh(int32_t, int32_t val) const { return val; }
     __device__ __forceinline__ bool cand(int32_t, uint32_t, int32_t &c, Acc &) const {
         c = gen + 1;
         return true;
@@ -215,6 +220,7 @@ struct SweepOp {
         return val != kInf;
     }
     __device__ __forceinline__ void own(int32_t, int32_t) const {}
+    __device__ __forceinline__ int32_t refresh(int32_t, int32_t val) const { return val; }
     __device__ __forceinline__ bool cand(int32_t val, uint32_t e, int32_t &c, Acc &a) const {
         uint32_t x = (uint32_t)val + (uint32_t)__ldg(w + e);
         if (x >= (uint32_t)kInf) { a.overflow = 1; return false; }
@@ -424,6 +430,7 @@ __device__ __forceinline__ void expand_low_dense(const uint32_t *__restrict__ ro
     const int64_t nw = (int64_t)gridDim.x * kWarps;
     for (int64_t w0 = gw * 128; w0 < n; w0 += nw * 128) {
         const int64_t v0 = w0 + 4 * lane;
+        if (lane == 0) a.scanned += min((int64_t)128, (int64_t)n - w0);
         int32_t st[4];
         if (v0 + 3 < n) {
             int4 t = __ldcg(reinterpret_cast<const int4 *>(actw + v0));
@@ -482,49 +489,66 @@ __device__ __forceinline__ void expand_low_dense(const uint32_t *__restrict__ ro
 }
 
 // ================================================================ expansions
+// Block-wide compaction helper: every thread offers at most one index; the
+// offered indices are gathered in shared memory (order not kept).
+__device__ __forceinline__ int block_compact(bool offer, int32_t idx, int32_t *s_list, int *s_n) {
+    if (threadIdx.x == 0) *s_n = 0;
+    __syncthreads();
+    unsigned bal = __ballot_sync(0xffffffffu, offer);
+    int base = 0;
+    if (lane_id() == 0 && bal) base = atomicAdd(s_n, __popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (offer) s_list[base + __popc(bal & lanemask_lt())] = idx;
+    __syncthreads();
+    return *s_n;
+}
+
 // Bucketed vertex expansion: high chunks by whole CTAs, mid vertices by warps,
-// low vertices by threads with the warp's edges redistributed over its lanes
-// (a warp-wide prefix sum of the degrees; each lane finds the owner of its
-// edge by a 5-step shuffle search), so edge loads are contiguous.
+// low vertices by threads with the warp's edges redistributed over its lanes.
+// Activity is tested for many items at once (256 chunks per CTA, 32 mid
+// vertices per warp) so that inactive items cost one parallel load.
 template <class OP, class PUSH>
 __device__ __forceinline__ void expand_vertices(const uint32_t *__restrict__ row_off, const int32_t *__restrict__ col,
                                                 const int32_t *low, int n_low, const int32_t *mid, int n_mid,
                                                 const int2 *high, int n_high, const OP &op, const PUSH &push,
                                                 Acc &a) {
-    __shared__ int32_t s_val;
-    __shared__ int s_act, s_rq;
+    __shared__ int32_t s_list[kBlock];
+    __shared__ int32_t s_cval[kBlock];
+    __shared__ int s_n;
     const unsigned lane = lane_id();
-    // high-degree chunks: one CTA per 2048-edge chunk
-    for (int ci = blockIdx.x; ci < n_high; ci += gridDim.x) {
-        int2 ch;
-        ch.x = ldcg(&high[ci].x);
-        ch.y = ldcg(&high[ci].y);
-        uint32_t rb = __ldg(row_off + ch.x), re = __ldg(row_off + ch.x + 1);
-        if (threadIdx.x == 0) {
-            int32_t val = 0;
-            bool rq = false;
-            bool act = op.active(ch.x, val, rq);
-            if (act && (uint32_t)ch.y == rb) {
-                op.own(ch.x, val);
+    // high-degree chunks: dealt to the CTAs round-robin, one CTA per chunk
+    const int64_t G = gridDim.x;
+    for (int64_t base = blockIdx.x; base < n_high; base += G * kBlock) {
+        const int64_t ci = base + (int64_t)threadIdx.x * G;
+        bool act = false, rq = false;
+        int32_t cval = 0, cv = 0;
+        if (ci < n_high) {
+            cv = ldcg(&high[ci].x);
+            const int32_t cb = ldcg(&high[ci].y);
+            act = op.active(cv, cval, rq);
+            if (act && (uint32_t)cb == __ldg(row_off + cv)) {
+                op.own(cv, cval);
                 a.verts++;
             }
-            s_act = act;
-            s_val = val;
-            s_rq = rq;
         }
-        __syncthreads();
-        push(threadIdx.x == 0 && s_rq, ch.x, a);
-        if (s_act) {
-            int32_t vv = s_val;
-            uint32_t e0 = (uint32_t)ch.y, e1 = min(e0 + (uint32_t)kChunk, re);
+        push(rq, cv, a);
+        s_cval[threadIdx.x] = cval;
+        const int na = block_compact(act, (int32_t)threadIdx.x, s_list, &s_n);
+        for (int i = 0; i < na; i++) {
+            const int t = s_list[i];
+            const int64_t cj = base + (int64_t)t * G;
+            const int32_t vtx = ldcg(&high[cj].x);
+            const uint32_t e0 = (uint32_t)ldcg(&high[cj].y);
+            const uint32_t e1 = min(e0 + (uint32_t)kChunk, __ldg(row_off + vtx + 1));
+            const int32_t vv = op.refresh(vtx, s_cval[t]);
             if (threadIdx.x == 0) a.edges += e1 - e0;
-            for (uint32_t base = e0; base < e1; base += kBlock * kU) {
+            for (uint32_t eb = e0; eb < e1; eb += kBlock * kU) {
                 uint32_t e[kU];
                 int32_t val[kU];
                 bool in[kU];
 #pragma unroll
                 for (int j = 0; j < kU; j++) {
-                    e[j] = base + j * kBlock + threadIdx.x;
+                    e[j] = eb + j * kBlock + threadIdx.x;
                     in[j] = e[j] < e1;
                     val[j] = vv;
                 }
@@ -535,36 +559,39 @@ __device__ __forceinline__ void expand_vertices(const uint32_t *__restrict__ row
     }
     const int gw = (int)((blockIdx.x * (unsigned)kBlock + threadIdx.x) >> 5);
     const int nw = (int)(gridDim.x * (unsigned)kWarps);
-    // mid-degree vertices: one warp each
-    for (int i = gw; i < n_mid; i += nw) {
-        int32_t u = ldcg(mid + i);
-        int32_t vv = 0;
-        int act = 0;
-        bool rq = false;
-        if (lane == 0) {
+    // mid-degree vertices: a warp tests 32 at once, then expands the active
+    // ones one after the other with all its lanes
+    for (int base = gw; base < n_mid; base += nw * 32) {
+        const int i = base + (int)lane * nw;
+        int32_t u = 0, vv = 0;
+        bool act = false, rq = false;
+        if (i < n_mid) {
+            u = ldcg(mid + i);
             act = op.active(u, vv, rq);
             if (act) op.own(u, vv);
         }
-        push(lane == 0 && rq, u, a);
-        act = __shfl_sync(0xffffffffu, act, 0);
-        if (!act) continue;
-        vv = __shfl_sync(0xffffffffu, vv, 0);
-        uint32_t b = __ldg(row_off + u), en = __ldg(row_off + u + 1);
-        if (lane == 0) {
-            a.verts++;
-            a.edges += en - b;
-        }
-        for (uint32_t base = b; base < en; base += 32 * kU) {
-            uint32_t e[kU];
-            int32_t val[kU];
-            bool in[kU];
+        push(rq, u, a);
+        unsigned bal = __ballot_sync(0xffffffffu, act);
+        if (lane == 0) a.verts += __popc(bal);
+        while (bal) {
+            const int l = __ffs(bal) - 1;
+            bal &= bal - 1;
+            const int32_t uu = __shfl_sync(0xffffffffu, u, l);
+            const int32_t uval = op.refresh(uu, __shfl_sync(0xffffffffu, vv, l));
+            const uint32_t b = __ldg(row_off + uu), en = __ldg(row_off + uu + 1);
+            if (lane == 0) a.edges += en - b;
+            for (uint32_t eb = b; eb < en; eb += 32 * kU) {
+                uint32_t e[kU];
+                int32_t val[kU];
+                bool in[kU];
 #pragma unroll
-            for (int j = 0; j < kU; j++) {
-                e[j] = base + 32 * j + lane;
-                in[j] = e[j] < en;
-                val[j] = vv;
+                for (int j = 0; j < kU; j++) {
+                    e[j] = eb + 32 * j + lane;
+                    in[j] = e[j] < en;
+                    val[j] = uval;
+                }
+                relax_batch(col, op, push, e, val, in, a);
             }
-            relax_batch(col, op, push, e, val, in, a);
         }
     }
     // low-degree vertices: a thread each, edges redistributed over the warp
@@ -588,9 +615,11 @@ __device__ __forceinline__ void expand_vertices(const uint32_t *__restrict__ row
 }
 
 // Edge-parallel sweep over the source-sorted COO: each thread takes four
-// consecutive edges with 128-bit loads of src (and of col and w through the
-// op's cand), and the activity test of a source is reused across consecutive
-// edges of the same source.
+// consecutive edges with a 128-bit load of src, and the activity test of a
+// source is reused across consecutive edges of the same source.  The thread
+// that holds an active source's first edge (the previous edge has another
+// source) also carries the source's value (op.own), so the synchronous
+// edge mode needs no separate pass over the vertices.
 template <class OP>
 __device__ __forceinline__ void expand_edges(const int32_t *__restrict__ src, const int32_t *__restrict__ col,
                                              int64_t m, const OP &op, Acc &a) {
@@ -599,19 +628,38 @@ __device__ __forceinline__ void expand_edges(const int32_t *__restrict__ src, co
     const int64_t nth = (int64_t)gridDim.x * kBlock;
     const int64_t m4 = m >> 2;
     const int4 *src4 = reinterpret_cast<const int4 *>(src);
-    for (int64_t q = tid; q < m4; q += nth) {
-        int4 s4 = __ldg(src4 + q);
-        int32_t us[4] = {s4.x, s4.y, s4.z, s4.w};
+    const unsigned lane = lane_id();
+    if (tid == 0) a.scanned += (uint64_t)m;    // every edge's source is read once per round
+    for (int64_t q0 = tid - lane; q0 < m4; q0 += nth) {   // warp-uniform trip count
+        const int64_t q = q0 + lane;
+        int32_t us[4] = {-1, -1, -1, -1};
+        if (q < m4) {
+            int4 s4 = __ldg(src4 + q);
+            us[0] = s4.x; us[1] = s4.y; us[2] = s4.z; us[3] = s4.w;
+        }
+        // source of the edge before this thread's first edge
+        int32_t before = __shfl_up_sync(0xffffffffu, us[3], 1);
+        if (lane == 0) before = (q > 0 && q < m4) ? __ldg(src + 4 * q - 1) : -1;
         uint32_t e[4];
         int32_t val[4];
         bool in[4];
-        int32_t prev = -1, pval = 0;
+        int32_t prev = before, pval = 0;
         bool pact = false;
+        if (before >= 0 && q < m4) {
+            bool rq;
+            pact = op.active(before, pval, rq);
+        }
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            if (us[j] != prev) {
+            if (us[j] < 0) {
+                pact = false;
+            } else if (us[j] != prev) {
                 bool rq;
                 pact = op.active(us[j], pval, rq);
+                if (pact) {
+                    op.own(us[j], pval);
+                    a.verts++;
+                }
                 prev = us[j];
             }
             e[j] = (uint32_t)(4 * q + j);
@@ -626,6 +674,10 @@ __device__ __forceinline__ void expand_edges(const int32_t *__restrict__ src, co
         bool rq;
         int32_t u = __ldg(src + x);
         if (op.active(u, vv, rq)) {
+            if (x == 0 || __ldg(src + x - 1) != u) {
+                op.own(u, vv);
+                a.verts++;
+            }
             int32_t v = __ldg(col + x), c, pv;
             if (op.cand(vv, (uint32_t)x, c, a)) {
                 pv = op.probe(v);
@@ -789,11 +841,142 @@ __device__ __forceinline__ void lb_expand(const uint32_t *__restrict__ row_off, 
     }
 }
 
+// ================================================================ sparse edge-sync rounds
+// A round of the synchronous edge mode normally streams every edge's source.
+// When the previous round changed few vertices the round is "sparse": a
+// flag pass first marks the 1024-edge chunks whose sources include an active
+// vertex (from the activity words of 256-vertex groups), and only those
+// chunks are streamed.  The choice is made identically by every CTA.
+
+// Flag pass: one warp per 256-vertex group; if any vertex of the group is
+// active (activity word == act_val), flag the edge chunks holding the
+// group's out-edges with `round`.
+__device__ __forceinline__ void flag_edge_chunks(const uint32_t *__restrict__ row_off, const int32_t *actw,
+                                                 int32_t act_val, int32_t n, int32_t *eflag, int32_t round,
+                                                 Acc &a) {
+    const unsigned lane = lane_id();
+    const int64_t gw = (blockIdx.x * (int64_t)kBlock + threadIdx.x) >> 5;
+    const int64_t nw = (int64_t)gridDim.x * kWarps;
+    const int64_t ngr = ((int64_t)n + kVGroup - 1) >> kVGroupLog;
+    for (int64_t gi = gw; gi < ngr; gi += nw) {
+        const int64_t vlo = gi << kVGroupLog, vhi = min((int64_t)n, vlo + kVGroup);
+        bool any = false;
+#pragma unroll
+        for (int h = 0; h < kVGroup / 128; h++) {
+            const int64_t v0 = vlo + 128 * h + 4 * lane;
+            if (v0 + 3 < vhi) {
+                int4 t = __ldcg(reinterpret_cast<const int4 *>(actw + v0));
+                any |= (t.x == act_val) | (t.y == act_val) | (t.z == act_val) | (t.w == act_val);
+            } else {
+                for (int j = 0; j < 4; j++)
+                    if (v0 + j < vhi) any |= ldcg(actw + v0 + j) == act_val;
+            }
+        }
+        if (lane == 0) a.scanned += vhi - vlo;
+        if (!__any_sync(0xffffffffu, any)) continue;
+        const uint32_t eb = __ldg(row_off + vlo), ee = __ldg(row_off + vhi);
+        if (ee > eb)
+            for (uint32_t k = (eb >> kEChunkLog) + lane; k <= (ee - 1) >> kEChunkLog; k += 32) stcg(eflag + k, round);
+    }
+}
+
+// Stream pass of a sparse round: the 1024-edge chunks are dealt to the CTAs
+// round-robin; a CTA reads the flags of up to 256 of its chunks at once,
+// keeps the flagged ones and streams each with one 128-bit load of src per
+// thread (first-edge carry as in expand_edges).
+template <class OP>
+__device__ __forceinline__ void expand_flagged_chunks(const int32_t *__restrict__ src, const int32_t *__restrict__ col,
+                                                      int64_t m, const int32_t *eflag, int32_t round, const OP &op,
+                                                      Acc &a) {
+    __shared__ int32_t s_klist[kBlock];
+    __shared__ int s_kn;
+    const int64_t nec = (m + kEChunk - 1) >> kEChunkLog;
+    const int64_t m4 = m >> 2;
+    const int4 *src4 = reinterpret_cast<const int4 *>(src);
+    const int64_t G = gridDim.x;
+    const unsigned lane = lane_id();
+    for (int64_t base = blockIdx.x; base < nec; base += G * kBlock) {
+        const int64_t k = base + (int64_t)threadIdx.x * G;
+        const bool act = k < nec && ldcg(eflag + k) == round;
+        const int na = block_compact(act, (int32_t)k, s_klist, &s_kn);
+        for (int i = 0; i < na; i++) {
+            const int64_t kk = s_klist[i];
+            const int64_t e0 = kk << kEChunkLog, e1 = min(m, e0 + kEChunk);
+            if (threadIdx.x == 0) a.scanned += e1 - e0;
+            const int64_t q = (e0 >> 2) + threadIdx.x;
+            const bool qin = q < min(m4, (e1 + 3) >> 2) && q < m4;
+            int32_t us[4] = {-1, -1, -1, -1};
+            if (qin) {
+                int4 s4 = __ldg(src4 + q);
+                us[0] = s4.x; us[1] = s4.y; us[2] = s4.z; us[3] = s4.w;
+            }
+            int32_t before = __shfl_up_sync(0xffffffffu, us[3], 1);
+            if (lane == 0) before = (qin && q > 0) ? __ldg(src + 4 * q - 1) : -1;
+            uint32_t e[4];
+            int32_t val[4];
+            bool in[4];
+            int32_t prev = before, pval = 0;
+            bool pact = false;
+            if (before >= 0 && qin) {
+                bool rq;
+                pact = op.active(before, pval, rq);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                if (us[j] < 0) {
+                    pact = false;
+                } else if (us[j] != prev) {
+                    bool rq;
+                    pact = op.active(us[j], pval, rq);
+                    if (pact) {
+                        op.own(us[j], pval);
+                        a.verts++;
+                    }
+                    prev = us[j];
+                }
+                e[j] = (uint32_t)(4 * q + j);
+                val[j] = pval;
+                in[j] = pact;
+                a.edges += pact;
+            }
+            relax_batch(col, op, NoPush{}, e, val, in, a);
+            // the last chunk may end with up to three edges past the 128-bit part
+            const int64_t x = max(e0, 4 * m4) + threadIdx.x;
+            if (x < e1) {
+                int32_t vv;
+                bool rq;
+                int32_t u = __ldg(src + x);
+                if (op.active(u, vv, rq)) {
+                    if (x == 0 || __ldg(src + x - 1) != u) {
+                        op.own(u, vv);
+                        a.verts++;
+                    }
+                    int32_t v = __ldg(col + x), cc, pv;
+                    if (op.cand(vv, (uint32_t)x, cc, a)) {
+                        pv = op.probe(v);
+                        op.commit(v, cc, pv, a);
+                    }
+                    a.edges++;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ================================================================ the kernel
 // Resident CTAs per SM the register budget is sized for: the synchronous
 // modes gain from more warps in flight; the worklist modes do not.
+#ifndef FG_SYNC_MIN_BLOCKS
+#define FG_SYNC_MIN_BLOCKS 6
+#endif
+#ifndef FG_ASYNC_MIN_BLOCKS
+#define FG_ASYNC_MIN_BLOCKS 4
+#endif
 template <int MODE>
-constexpr int min_blocks() { return (MODE == kVertexSync || MODE == kEdgeSync) ? 6 : 4; }
+constexpr int min_blocks() {
+    return (MODE == kVertexSync || MODE == kEdgeSync) ? FG_SYNC_MIN_BLOCKS : FG_ASYNC_MIN_BLOCKS;
+}
 
 template <int ALGO, int MODE>
 __global__ void __launch_bounds__(kBlock, min_blocks<MODE>()) fixpoint_kernel(Params p) {
@@ -805,6 +988,16 @@ __global__ void __launch_bounds__(kBlock, min_blocks<MODE>()) fixpoint_kernel(Pa
     const int64_t nth = (int64_t)gridDim.x * kBlock;
     Acc a;
     int rounds = 0;
+    int n_barriers = 0;
+    // every grid barrier of the query; CTA 0 optionally timestamps each
+    auto sync_ = [&]() -> bool {
+        bool r = grid_sync(c, p.timeout_ns);
+        if (tid == 0) {
+            if (p.trace && n_barriers < p.trace_cap) p.trace[n_barriers] = global_ns();
+            n_barriers++;
+        }
+        return r;
+    };
 
     // ---- init: values, stamps, initial worklist (a2)
     for (int64_t v = tid; v < n; v += nth) {
@@ -817,6 +1010,9 @@ __global__ void __launch_bounds__(kBlock, min_blocks<MODE>()) fixpoint_kernel(Pa
         }
         if (!SYNC && ALGO != kBFS) p.S0[v] = 0;
     }
+    if (MODE == kEdgeSync)
+        for (int64_t k = tid; k < ((g.m + kEChunk - 1) >> kEChunkLog); k += nth) p.eflag[k] = 0;
+
     if (!SYNC && ALGO != kCC && tid == 0) {
         int32_t s = p.source;
         uint32_t b = g.row_off[s], d = g.row_off[s + 1] - b;
@@ -840,10 +1036,16 @@ __global__ void __launch_bounds__(kBlock, min_blocks<MODE>()) fixpoint_kernel(Pa
     }
     // failure-detection test: CTA 0 never arrives, the others' waits run out
     if (p.inject_missing_arrival && blockIdx.x == 0) return;
-    bool ok = grid_sync(c, p.timeout_ns);
+    bool ok = sync_();
 
     if (SYNC && ok) {
         int pass_ctr = 0;
+        // edge-sync: a round is sparse if the previous one accepted fewer
+        // candidates than n/8 (round 1: only the source is active, except CC)
+        auto sparse_round = [&](int r) -> bool {
+            if (r == 1) return ALGO != kCC;
+            return (int64_t)__ldcg(&c->changed[(r - 1) % 3]) * 8 < (int64_t)n;
+        };
         for (int r = 1;; r++) {
             if (r > p.max_rounds) {
                 if (tid == 0) atomicOr(&c->status, kStRoundCap);
@@ -857,6 +1059,10 @@ __global__ void __launch_bounds__(kBlock, min_blocks<MODE>()) fixpoint_kernel(Pa
                     expand_vertices(g.row_off, g.col, g.low, 0, g.mid, g.n_mid, g.high, g.n_high_chunks, op,
                                     NoPush{}, a);
                     expand_low_dense(g.row_off, g.col, p.A, r - 1, n, op, a);
+                } else if (sparse_round(r)) {
+                    flag_edge_chunks(g.row_off, p.A, r - 1, n, p.eflag, r, a);
+                    if (!sync_()) break;
+                    expand_flagged_chunks(g.src, g.col, g.m, p.eflag, r, op, a);
                 } else {
                     expand_edges(g.src, g.col, g.m, op, a);
                 }
@@ -870,40 +1076,24 @@ __global__ void __launch_bounds__(kBlock, min_blocks<MODE>()) fixpoint_kernel(Pa
                     expand_vertices(g.row_off, g.col, g.low, 0, g.mid, g.n_mid, g.high, g.n_high_chunks, op,
                                     NoPush{}, a);
                     expand_low_dense(g.row_off, g.col, scur, r, n, op, a);
+                } else if (sparse_round(r)) {
+                    flag_edge_chunks(g.row_off, scur, r, n, p.eflag, r, a);
+                    if (!sync_()) break;
+                    expand_flagged_chunks(g.src, g.col, g.m, p.eflag, r, op, a);
                 } else {
                     expand_edges(g.src, g.col, g.m, op, a);
-                    // carry the values of last round's changed vertices into next
-                    const int64_t n4 = n >> 2;
-                    for (int64_t q = tid; q < n4; q += nth) {
-                        int4 t = __ldcg(reinterpret_cast<const int4 *>(scur) + q);
-                        int32_t st4[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-                        for (int j = 0; j < 4; j++) {
-                            if (st4[j] == r) {
-                                op.own((int32_t)(4 * q + j), ldcg(cur + 4 * q + j));
-                                a.verts++;
-                            }
-                        }
-                    }
-                    for (int64_t v = 4 * n4 + tid; v < n; v += nth) {
-                        int32_t val;
-                        bool rq;
-                        if (op.active((int32_t)v, val, rq)) {
-                            op.own((int32_t)v, val);
-                            a.verts++;
-                        }
-                    }
                 }
             }
             int ch = block_sum(a.changed);
             a.changed = 0;
             if (threadIdx.x == 0 && ch) atomicAdd(&c->changed[r % 3], ch);
-            if (!grid_sync(c, p.timeout_ns)) break;
+            if (!sync_()) break;
             if (__ldcg(&c->changed[r % 3]) == 0) {
                 if (tid == 0) c->result_in_b = (ALGO != kBFS) && (r & 1);
-                if (ALGO == kSSSP && MODE == kVertexSync) {
-                    // A vertex without out-edges belongs to no bucket, so its
-                    // last improvement sits in one buffer only: take the min.
+                if (ALGO == kSSSP) {
+                    // A vertex without out-edges is never expanded, so no
+                    // carry copies its last improvement into the other
+                    // buffer: take the min of the two.
                     int32_t *res = (r & 1) ? p.B : p.A;
                     const int32_t *oth = (r & 1) ? p.A : p.B;
                     for (int64_t i = tid; i < g.n_zero; i += nth) {
@@ -936,7 +1126,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks<MODE>()) fixpoint_kernel(Pa
                     }
                     jc = block_sum(jc);
                     if (threadIdx.x == 0 && jc) atomicAdd(&c->jchanged[slot], jc);
-                    if (!grid_sync(c, p.timeout_ns)) { jok = false; break; }
+                    if (!sync_()) { jok = false; break; }
                     if (tid == 0) c->jump_passes++;
                     if (__ldcg(&c->jchanged[slot]) == 0) break;
                 }
@@ -993,7 +1183,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks<MODE>()) fixpoint_kernel(Pa
             } else {
                 const int32_t *items = initial_cc ? g.nz : p.wl[pi][0];
                 lb_prefix(g.row_off, items, n_in[0], p.lb_off, p.lb_blk);
-                if (!grid_sync(c, p.timeout_ns)) break;
+                if (!sync_()) break;
                 ListPush push{g.vclass, p.wl[po][0], &osize[0], p.wl_cap[0], &wb[0], c};
                 a.verts += 0;
                 if (ALGO == kBFS) {
@@ -1006,22 +1196,26 @@ __global__ void __launch_bounds__(kBlock, min_blocks<MODE>()) fixpoint_kernel(Pa
                 push.flush();
                 if (tid == 0) a.verts += (unsigned long long)n_in[0];
             }
-            if (!grid_sync(c, p.timeout_ns)) break;
+            if (!sync_()) break;
         }
     }
 
     // ---- statistics
     unsigned long long ev = block_sum(a.verts), ee = block_sum(a.edges), eu = block_sum(a.updates),
-                       ep = block_sum(a.pushes);
+                       ep = block_sum(a.pushes), es = block_sum(a.scanned);
     int of = block_sum(a.overflow);
     if (threadIdx.x == 0) {
         if (ev) atomicAdd(&c->st_vertices, ev);
         if (ee) atomicAdd(&c->st_edges, ee);
         if (eu) atomicAdd(&c->st_updates, eu);
         if (ep) atomicAdd(&c->st_pushes, ep);
+        if (es) atomicAdd(&c->st_scanned, es);
         if (of) atomicOr(&c->status, kStOverflow);
     }
-    if (tid == 0) c->rounds = rounds;
+    if (tid == 0) {
+        c->rounds = rounds;
+        c->barriers = n_barriers;
+    }
 }
 
 // One all-active sweep: vertex variant over the buckets, edge variant over
@@ -1127,6 +1321,8 @@ fg_status run_query(const fg_graph *G, Algo algo, Mode mode, int32_t source, int
     size_t need = Workspace::need(1, sizeof(Ctrl)) + Workspace::need(n, 4);
     int64_t cap[3] = {0, 0, 0};
     if (sync && algo != kBFS) need += 3 * Workspace::need(n, 4);
+    const int64_t nec = (g.m + kEChunk - 1) >> kEChunkLog;
+    if (mode == kEdgeSync) need += Workspace::need(nec, 4);
     if (!sync) {
         if (algo != kBFS) need += Workspace::need(n, 4);
         if (mode == kVertexAsync) {
@@ -1153,6 +1349,7 @@ fg_status run_query(const fg_graph *G, Algo algo, Mode mode, int32_t source, int
         p.S0 = ws.take<int32_t>(n);
         p.S1 = ws.take<int32_t>(n);
     }
+    if (mode == kEdgeSync) p.eflag = ws.take<int32_t>(nec);
     if (!sync) {
         if (algo != kBFS) p.S0 = ws.take<int32_t>(n);
         for (int par = 0; par < 2; par++)
@@ -1168,6 +1365,14 @@ fg_status run_query(const fg_graph *G, Algo algo, Mode mode, int32_t source, int
     int tmo = (opt && opt->wait_timeout_ms > 0) ? opt->wait_timeout_ms : 1000;
     p.timeout_ns = (unsigned long long)tmo * 1000000ull;
     p.inject_missing_arrival = (opt && opt->inject_missing_arrival) ? 1 : 0;
+    if (opt && opt->round_trace && opt->round_trace_cap > 0) {
+        if (!is_device_pointer(opt->round_trace)) {
+            cudaFreeAsync(ws.base, st);
+            return fail(FG_ERR_INVALID_ARG, "round_trace must be device memory");
+        }
+        p.trace = reinterpret_cast<unsigned long long *>(opt->round_trace);
+        p.trace_cap = opt->round_trace_cap;
+    }
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEventCreate(&ev0);
@@ -1243,6 +1448,8 @@ fg_status run_query(const fg_graph *G, Algo algo, Mode mode, int32_t source, int
         stats->edges_relaxed = (int64_t)hc.st_edges;
         stats->updates = (int64_t)hc.st_updates;
         stats->pushes = (int64_t)hc.st_pushes;
+        stats->scanned = (int64_t)hc.st_scanned;
+        stats->barriers = hc.barriers;
         stats->kernel_ms = ms;
     }
     if (status != FG_OK) return fail(status, msg);

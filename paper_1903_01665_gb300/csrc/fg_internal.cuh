@@ -19,6 +19,8 @@ constexpr int kLowMax = 32;            // low bucket: 1 .. 31 out-edges (thread 
 constexpr int kMidMax = 1024;          // mid bucket: 32 .. 1023 (warp per vertex)
 constexpr int kChunk = 2048;           // high bucket: >= 1024, split in 2048-edge chunks (CTA each)
 constexpr int32_t kInf = FG_INF;
+constexpr int kVGroupLog = 8, kVGroup = 1 << kVGroupLog;    // edge-sync: vertices per activity group
+constexpr int kEChunkLog = 10, kEChunk = 1 << kEChunkLog;   // edge-sync: edges per streamed chunk
 
 // device status bits (Ctrl::status)
 constexpr int kStTimeout = 1;          // a grid barrier wait ran out
@@ -73,7 +75,8 @@ struct Ctrl {
     int changed[3];             // per-round change counters, rotating slots
     int jchanged[3];            // per-pass pointer-jumping change counters
     int wl_size[3][4];          // async: worklist sizes per generation slot and class
-    unsigned long long st_vertices, st_edges, st_updates, st_pushes;
+    unsigned long long st_vertices, st_edges, st_updates, st_pushes, st_scanned;
+    int barriers;
 };
 
 enum Algo { kSSSP = 0, kBFS = 1, kCC = 2 };
@@ -92,10 +95,13 @@ struct Params {
     int32_t wl_cap[3] = {};     // capacity per class (in int32 slots)
     uint32_t *lb_off = nullptr; // edge-async: per-item local offsets
     uint32_t *lb_blk = nullptr; // edge-async: per-CTA totals
+    int32_t *eflag = nullptr;   // edge-sync sparse rounds: round stamp per 1024-edge chunk
     int32_t source = 0;
     int32_t max_rounds = 0;
     unsigned long long timeout_ns = 0;
     int32_t inject_missing_arrival = 0;
+    unsigned long long *trace = nullptr;   // optional per-barrier timestamps (CTA 0)
+    int32_t trace_cap = 0;
     Ctrl *ctrl = nullptr;
 };
 
