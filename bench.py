@@ -43,7 +43,11 @@ ALGO_NAMES = ["sssp", "bfs", "cc"]
 # DRAM bytes per launch from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by kernel; valid only while the kernel source
 # is unchanged (sha256 of csrc/fg_fixpoint.cu at capture time).
-NCU_TRAFFIC: dict = {}
+NCU_TRAFFIC: dict = {
+    # profiles/sssp_edge_sync_rmat22.md: one launch, first bench source, R-MAT 22
+    "fixpoint_kernel<sssp,edge_sync>": {"bytes_per_launch": 6907746560 + 466209280,
+                                        "src_sha": "b504cc75616bdffc"},
+}
 
 
 def fixpoint_source_sha() -> str:
