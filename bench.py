@@ -436,8 +436,35 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_case(args):
+    """Profiling driver: one query type on one seeded graph, run twice (the
+    second run is the one to capture), stats printed; no benchmark line."""
+    import torch
+    import paper_1903_01665_gb300 as fg
+    algo_name, mode_name = args.case.split(":")
+    algo = ALGO_NAMES.index(algo_name)
+    mode = MODE_NAMES.index(mode_name)
+    if args.case_graph == "rmat":
+        g = gg.rmat(args.case_scale)
+    else:
+        g = gg.grid(args.case_scale)
+    s = int(gg.sources(g, 1)[0])
+    st, h = fg.fg_graph_create_coo(g.n, torch.from_numpy(g.src).cuda(), torch.from_numpy(g.dst).cuda(),
+                                   torch.from_numpy(g.w).cuda())
+    fg.check(st)
+    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    for i in range(2):
+        st, stats = fg.fg_run(h, algo, s, out, mode)
+        fg.check(st)
+        print(i, json.dumps(stats.as_dict()), flush=True)
+    fg.check(fg.fg_graph_destroy(h))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default=None, help="profiling driver, e.g. sssp:edge_sync")
+    ap.add_argument("--case-graph", default="rmat", choices=["rmat", "grid"])
+    ap.add_argument("--case-scale", type=int, default=20, help="R-MAT scale or grid side")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -448,7 +475,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.impl == "reference":
+    if args.case:
+        run_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
