@@ -1,1234 +1,32 @@
-// The fixpoint relaxation sweep (Sec. 2, Alg. 1-3) in the four variants of
-// Sec. 3.1-3.3, as persistent cooperative kernels: one launch runs init,
-// every round and the convergence test on the device.  Rounds are separated
-// by a grid barrier whose waits are bounded in time.
-//
-//   vertex-sync  : Alg. 1 -- every round scans the degree-bucketed vertex
-//                  lists (topology-driven) and expands the vertices that
-//                  changed in the previous round; reads cur, atomic MIN into
-//                  next (double-buffered, Jacobi), barrier, swap.
-//   edge-sync    : Alg. 2 -- every round streams all edges (src,dst,w) with
-//                  128-bit loads and relaxes those whose source changed.
-//   vertex-async : data-driven (Sec. 3.3) -- worklists of vertices by degree
-//                  class, in-place atomic MIN, changed targets appended with
-//                  warp-aggregated atomics, until the worklist is empty.
-//   edge-async   : the worklist's out-edges, load-balanced edge-parallel by a
-//                  prefix sum of the items' degrees, in place.
-//
-// BFS uses Alg. 3's level filter (dist == lev, plain store of lev+1); CC is
-// min-label propagation on the symmetrised graph plus pointer jumping
-// (label[v] = label[label[v]]).
+// Single-query entry of the fixpoint sweep: one persistent cooperative
+// kernel per query, the whole grid as one team; plus the all-active sweep
+// used for roofline measurements and the overflow test.
 #include <algorithm>
 
-#include "fg_internal.cuh"
+#include "fg_device.cuh"
 
 namespace fg {
 
 namespace {
 
-struct Acc {
-    unsigned long long edges = 0, verts = 0, updates = 0, pushes = 0, scanned = 0;
-    int changed = 0;
-    int overflow = 0;
-};
-
-template <typename T>
-__device__ __forceinline__ T block_sum(T x) {
-    __shared__ T sh[kWarps];
-    x = warp_sum(x);
-    if (lane_id() == 0) sh[threadIdx.x >> 5] = x;
-    __syncthreads();
-    T r = 0;
-    if (threadIdx.x < 32) {
-        r = lane_id() < (unsigned)kWarps ? sh[lane_id()] : (T)0;
-        r = warp_sum(r);
-    }
-    __syncthreads();
-    return r;
-}
-
-// ================================================================ edge ops
-// Each op provides:
-//   active(u, val, rq) -- is u expanded this round; its value.  An op may
-//                      lower u's own value here (CC pointer jumping); it then
-//                      sets rq if u must be re-queued for the next generation.
-//   own(u, val)     -- once per expanded vertex (sync: carry cur[u] into next)
-//   cand(val, e, c, a) -- the candidate value of edge e from a source value
-//                      val (false: dropped, e.g. >= INT32_MAX)
-//   probe(v)        -- the target's current value, to compare against
-//   commit(v, c, pv, a) -- apply a candidate; true if v must be appended to
-//                      the worklist.
-// Splitting a relaxation into cand / probe / commit lets the expansions
-// issue the loads of several edges before using any of them.
-
-// Synchronous SSSP / CC: Jacobi round r reads cur, lowers next.
-template <int ALGO>
-struct SyncOp {
-    const int32_t *__restrict__ w;
-    const int32_t *cur;
-    int32_t *next;
-    const int32_t *scur;
-    int32_t *snext;
-    int32_t r;
-
-    __device__ __forceinline__ bool active(int32_t u, int32_t &val, bool &) const {
-        if (ldcg(scur + u) != r) return false;
-        val = ldcg(cur + u);
-        return true;
-    }
-    __device__ __forceinline__ void own(int32_t u, int32_t val) const { red_min(next + u, val); }
-    __device__ __forceinline__ int32_t refresh(int32_t, int32_t val) const { return val; }
-    __device__ __forceinline__ bool cand(int32_t val, uint32_t e, int32_t &c, Acc &a) const {
-        if (ALGO == kSSSP) {
-            uint32_t x = (uint32_t)val + (uint32_t)__ldg(w + e);
-            if (x >= (uint32_t)kInf) { a.overflow = 1; return false; }
-            c = (int32_t)x;
-        } else {
-            c = val;
-        }
-        return true;
-    }
-    __device__ __forceinline__ int32_t probe(int32_t v) const { return ldcg(cur + v); }
-    // v changes this round iff some candidate is below its previous-round
-    // value, so any such candidate may mark it: the MIN needs no return value.
-    __device__ __forceinline__ bool commit(int32_t v, int32_t c, int32_t pv, Acc &a) const {
-        if (c < pv) {
-            red_min(next + v, c);
-            stcg(snext + v, r + 1);
-            a.changed++;
-            a.updates++;
-        }
-        return false;
-    }
-};
-
-// Level-synchronous BFS (Alg. 3): in place, filter dist == lev.
-struct BfsSyncOp {
-    int32_t *L;
-    int32_t lev;
-
-    __device__ __forceinline__ bool active(int32_t u, int32_t &val, bool &) const {
-        val = lev;
-        return ldcg(L + u) == lev;
-    }
-    __device__ __forceinline__ void own(int32_t, int32_t) const {}
-    __device__ __forceinline__ int32_t refresh(int32_t, int32_t val) const { return val; }
-    __device__ __forceinline__ bool cand(int32_t, uint32_t, int32_t &c, Acc &) const {
-        c = lev + 1;
-        return true;
-    }
-    __device__ __forceinline__ int32_t probe(int32_t v) const { return ldcg(L + v); }
-    __device__ __forceinline__ bool commit(int32_t v, int32_t c, int32_t pv, Acc &a) const {
-        if (pv > c) {
-            stcg(L + v, c);
-            a.changed++;
-            a.updates++;
-        }
-        return false;
-    }
-};
-
-// Asynchronous SSSP / CC: in place, push on decrease, dedup by generation stamp.
-template <int ALGO>
-struct AsyncOp {
-    const int32_t *__restrict__ w;
-    int32_t *D;
-    int32_t *stamp;
-    int32_t gen;
-
-    __device__ __forceinline__ bool active(int32_t u, int32_t &val, bool &rq) const {
-        val = ldcg(D + u);
-        if (ALGO == kCC) {
-            // pointer jumping: follow label[label[...]] while it decreases
-            int32_t l = val;
-#pragma unroll 1
-            for (int k = 0; k < 8; k++) {
-                int32_t ll = ldcg(D + l);
-                if (ll >= l) break;
-                l = ll;
-            }
-            if (l < val) {
-                // u's other edges may be relaxed elsewhere with the old label,
-                // so u is queued again to pass the new one to all neighbours
-                if (atomicMin(D + u, l) > l) rq = atomicExch(stamp + u, gen + 1) != gen + 1;
-                val = l;
-            }
-        }
-        return true;
-    }
-    __device__ __forceinline__ void own(int32_t, int32_t) const {}
-    // in place: the latest value, read just before the vertex is expanded
-    __device__ __forceinline__ int32_t refresh(int32_t u, int32_t val) const { return min(val, ldcg(D + u)); }
-    __device__ __forceinline__ bool cand(int32_t val, uint32_t e, int32_t &c, Acc &a) const {
-        if (ALGO == kSSSP) {
-            uint32_t x = (uint32_t)val + (uint32_t)__ldg(w + e);
-            if (x >= (uint32_t)kInf) { a.overflow = 1; return false; }
-            c = (int32_t)x;
-        } else {
-            c = val;
-        }
-        return true;
-    }
-    __device__ __forceinline__ int32_t probe(int32_t v) const { return ldcg(D + v); }
-    // A candidate below the value just read lowers v or loses to an even
-    // lower one; either way v has changed in this generation and is queued
-    // (once, by the stamp) for the next.
-    __device__ __forceinline__ bool commit(int32_t v, int32_t c, int32_t pv, Acc &a) const {
-        if (c < pv) {
-            red_min(D + v, c);
-            a.updates++;
-            return atomicExch(stamp + v, gen + 1) != gen + 1;
-        }
-        return false;
-    }
-};
-
-// Asynchronous BFS: frontier queue; a vertex is claimed once by CAS from INF.
-struct BfsAsyncOp {
-    int32_t *L;
-    int32_t gen;
-
-    __device__ __forceinline__ bool active(int32_t, int32_t &val, bool &) const {
-        val = gen;
-        return true;
-    }
-    __device__ __forceinline__ void own(int32_t, int32_t) const {}
-    __device__ __forceinline__ int32_t refresh(int32_t, int32_t val) const { return val; }
-    __device__ __forceinline__ bool cand(int32_t, uint32_t, int32_t &c, Acc &) const {
-        c = gen + 1;
-        return true;
-    }
-    __device__ __forceinline__ int32_t probe(int32_t v) const { return ldcg(L + v); }
-    __device__ __forceinline__ bool commit(int32_t v, int32_t c, int32_t pv, Acc &a) const {
-        if (pv != kInf) return false;
-        if (atomicCAS(L + v, kInf, c) == kInf) {
-            a.updates++;
-            return true;
-        }
-        return false;
-    }
-};
-
-// One full sweep with every vertex active (roofline measurement).
-struct SweepOp {
-    const int32_t *__restrict__ w;
-    const int32_t *cur;
-    int32_t *next;
-
-    __device__ __forceinline__ bool active(int32_t u, int32_t &val, bool &) const {
-        val = ldcg(cur + u);
-        return val != kInf;
-    }
-    __device__ __forceinline__ void own(int32_t, int32_t) const {}
-    __device__ __forceinline__ int32_t refresh(int32_t, int32_t val) const { return val; }
-    __device__ __forceinline__ bool cand(int32_t val, uint32_t e, int32_t &c, Acc &a) const {
-        uint32_t x = (uint32_t)val + (uint32_t)__ldg(w + e);
-        if (x >= (uint32_t)kInf) { a.overflow = 1; return false; }
-        c = (int32_t)x;
-        return true;
-    }
-    __device__ __forceinline__ int32_t probe(int32_t v) const { return ldcg(next + v); }
-    __device__ __forceinline__ bool commit(int32_t v, int32_t c, int32_t pv, Acc &a) const {
-        if (c < pv) {
-            if (atomicMin(next + v, c) > c) a.updates++;
-        }
-        return false;
-    }
-};
-
-// ================================================================ appenders
-struct NoPush {
-    __device__ __forceinline__ void operator()(bool, int32_t, Acc &) const {}
-    __device__ __forceinline__ void flush() const {}
-};
-
-// Per-warp staging buffer of worklist appends in shared memory: appends go
-// to the warp's buffer (ballot + prefix, no atomics) and reach the global
-// list in blocks, one atomicAdd on the list's size per block, so that
-// thousands of warps do not serialise on one counter.
-constexpr int kPushBuf = 256;
-struct WarpBuf {
-    int32_t item[kPushBuf];
-    int count;
-};
-
-__device__ __forceinline__ void warp_flush(WarpBuf *b, int cnt, int32_t *list, int *size, int32_t cap, Ctrl *c) {
-    __syncwarp();
-    int base = 0;
-    if (lane_id() == 0) base = atomicAdd(size, cnt);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    for (int i = (int)lane_id(); i < cnt; i += 32) {
-        int pos = base + i;
-        if (pos < cap) list[pos] = b->item[i];
-        else atomicOr(&c->status, kStWorklist);
-    }
-    __syncwarp();
-}
-
-__device__ __forceinline__ void buffered_append(bool want, int32_t v, WarpBuf *b, int32_t *list, int *size,
-                                                int32_t cap, Ctrl *c) {
-    unsigned bal = __ballot_sync(0xffffffffu, want);
-    if (bal == 0) return;
-    int n = __popc(bal);
-    int cnt = b->count;
-    if (cnt + n > kPushBuf) {
-        warp_flush(b, cnt, list, size, cap, c);
-        cnt = 0;
-    }
-    if (want) b->item[cnt + __popc(bal & lanemask_lt())] = v;
-    __syncwarp();
-    if (lane_id() == 0) b->count = cnt + n;
-    __syncwarp();
-}
-
-__device__ __forceinline__ void buffered_flush(WarpBuf *b, int32_t *list, int *size, int32_t cap, Ctrl *c) {
-    int cnt = b->count;
-    if (cnt > 0) warp_flush(b, cnt, list, size, cap, c);
-    __syncwarp();
-    if (lane_id() == 0) b->count = 0;
-    __syncwarp();
-}
-
-// vertex-async: append to the class list of the target's out-degree
-struct ClassPush {
-    const uint32_t *__restrict__ row_off;
-    const uint8_t *__restrict__ vclass;   // 0 no out-edge, 1 low, 2 mid, 3 high
-    int32_t *low, *mid;
-    int2 *high;
-    int *size;          // [3]
-    int32_t cap_low, cap_mid, cap_high;
-    WarpBuf *buf_low, *buf_mid;           // this warp's staging buffers
-    Ctrl *c;
-
-    __device__ __forceinline__ void operator()(bool want, int32_t v, Acc &a) const {
-        int cls = -1;
-        if (want) {
-            cls = (int)__ldg(vclass + v) - 1;
-            if (cls >= 0) a.pushes++;
-        }
-        if (__ballot_sync(0xffffffffu, cls >= 0) == 0) return;
-        buffered_append(cls == kWlLow, v, buf_low, low, &size[kWlLow], cap_low, c);
-        buffered_append(cls == kWlMid, v, buf_mid, mid, &size[kWlMid], cap_mid, c);
-        if (cls == kWlHigh) {
-            uint32_t b = __ldg(row_off + v), d = __ldg(row_off + v + 1) - b;
-            int nck = (int)((d + kChunk - 1) / kChunk);
-            int base = atomicAdd(&size[kWlHigh], nck);
-            if (base + nck <= cap_high) {
-                for (int k = 0; k < nck; k++) high[base + k] = make_int2(v, (int32_t)(b + (uint32_t)k * kChunk));
-            } else {
-                atomicOr(&c->status, kStWorklist);
-            }
-        }
-    }
-    __device__ __forceinline__ void flush() const {
-        buffered_flush(buf_low, low, &size[kWlLow], cap_low, c);
-        buffered_flush(buf_mid, mid, &size[kWlMid], cap_mid, c);
-    }
-};
-
-// edge-async: one list of vertices with >= 1 out-edge
-struct ListPush {
-    const uint8_t *__restrict__ vclass;
-    int32_t *list;
-    int *size;
-    int32_t cap;
-    WarpBuf *buf;
-    Ctrl *c;
-
-    __device__ __forceinline__ void operator()(bool want, int32_t v, Acc &a) const {
-        bool ok = false;
-        if (want) {
-            ok = __ldg(vclass + v) != 0;
-            if (ok) a.pushes++;
-        }
-        buffered_append(ok, v, buf, list, size, cap, c);
-    }
-    __device__ __forceinline__ void flush() const { buffered_flush(buf, list, size, cap, c); }
-};
-
-// ================================================================ batched relaxation
-constexpr int kU = 4;   // edges per thread per loop iteration
-
-// Relax up to kU edges per thread: every load of the batch is issued before
-// any result is used.  All lanes of the warp call it (the appends are
-// warp-collective); lanes with in[j] == false take no part in edge j.
-template <class OP, class PUSH, int N>
-__device__ __forceinline__ void relax_batch(const int32_t *__restrict__ col, const OP &op, const PUSH &push,
-                                            const uint32_t (&e)[N], const int32_t (&val)[N],
-                                            const bool (&in)[N], Acc &a) {
-    int32_t v[N], c[N], pv[N];
-    bool ok[N];
-#pragma unroll
-    for (int j = 0; j < N; j++) {
-        v[j] = 0;
-        c[j] = 0;
-        ok[j] = in[j];
-        if (ok[j]) {
-            v[j] = __ldg(col + e[j]);
-            ok[j] = op.cand(val[j], e[j], c[j], a);
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < N; j++) pv[j] = ok[j] ? op.probe(v[j]) : 0;
-    bool want[N];
-#pragma unroll
-    for (int j = 0; j < N; j++) want[j] = ok[j] && op.commit(v[j], c[j], pv[j], a);
-#pragma unroll
-    for (int j = 0; j < N; j++) push(want[j], v[j], a);
-}
-
-// Edges of up to 32 rows, given per lane as (row start, degree < 32, value),
-// redistributed over the warp: a warp-wide prefix sum of the degrees, and each
-// lane finds the owner row of its edge by a 5-step shuffle search, so that the
-// edge loads of a batch are contiguous.
-template <class OP, class PUSH>
-__device__ __forceinline__ void relax_rows_of_warp(const int32_t *__restrict__ col, const OP &op, const PUSH &push,
-                                                   uint32_t rb, uint32_t d, int32_t vv, Acc &a) {
-    const unsigned lane = lane_id();
-    uint32_t incl = warp_inclusive_scan(d);
-    uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    uint32_t excl = incl - d;
-    if (lane == 0) a.edges += total;
-    for (uint32_t k0 = 0; k0 < total; k0 += 32 * kU) {
-        uint32_t e[kU];
-        int32_t val[kU];
-        bool in[kU];
-#pragma unroll
-        for (int j = 0; j < kU; j++) {
-            uint32_t k = k0 + 32 * j + lane;
-            int owner = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                uint32_t pv = __shfl_sync(0xffffffffu, incl, owner + step - 1);
-                if (pv <= k) owner += step;
-            }
-            uint32_t ob = __shfl_sync(0xffffffffu, rb, owner);
-            uint32_t oe = __shfl_sync(0xffffffffu, excl, owner);
-            val[j] = __shfl_sync(0xffffffffu, vv, owner);
-            e[j] = ob + (k - oe);
-            in[j] = k < total;
-        }
-        relax_batch(col, op, push, e, val, in, a);
-    }
-}
-
-// Synchronous low-degree path: the warp scans 128 consecutive vertex ids per
-// step with 128-bit loads of the activity word (round stamp, or BFS level),
-// compacts the active vertices with 1..31 out-edges into shared memory, and
-// relaxes their edges 32 rows at a time.  Mid and high vertices are expanded
-// from their bucket lists; vertices without out-edges have nothing to expand.
-template <class OP>
-__device__ __forceinline__ void expand_low_dense(const uint32_t *__restrict__ row_off, const int32_t *__restrict__ col,
-                                                 const int32_t *actw, int32_t act_val, int32_t n, const OP &op,
-                                                 Acc &a) {
-    __shared__ uint32_t s_rb[kWarps][128];
-    __shared__ uint32_t s_d[kWarps][128];
-    __shared__ int32_t s_v[kWarps][128];
-    const unsigned lane = lane_id();
-    const int wid = threadIdx.x >> 5;
-    const int64_t gw = (blockIdx.x * (int64_t)kBlock + threadIdx.x) >> 5;
-    const int64_t nw = (int64_t)gridDim.x * kWarps;
-    for (int64_t w0 = gw * 128; w0 < n; w0 += nw * 128) {
-        const int64_t v0 = w0 + 4 * lane;
-        if (lane == 0) a.scanned += min((int64_t)128, (int64_t)n - w0);
-        int32_t st[4];
-        if (v0 + 3 < n) {
-            int4 t = __ldcg(reinterpret_cast<const int4 *>(actw + v0));
-            st[0] = t.x; st[1] = t.y; st[2] = t.z; st[3] = t.w;
-        } else {
-#pragma unroll
-            for (int j = 0; j < 4; j++) st[j] = (v0 + j < n) ? ldcg(actw + v0 + j) : act_val - 1;
-        }
-        bool act[4];
-        uint32_t rb[4], d[4];
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            act[j] = st[j] == act_val;
-            rb[j] = 0;
-            d[j] = 0;
-            if (act[j]) {
-                rb[j] = __ldg(row_off + v0 + j);
-                d[j] = __ldg(row_off + v0 + j + 1) - rb[j];
-                act[j] = d[j] >= 1 && d[j] < (uint32_t)kLowMax;
-            }
-        }
-        unsigned cnt_lane = act[0] + act[1] + act[2] + act[3];
-        unsigned any = __ballot_sync(0xffffffffu, cnt_lane != 0);
-        if (!any) continue;
-        unsigned incl = warp_inclusive_scan(cnt_lane);
-        unsigned tot = __shfl_sync(0xffffffffu, incl, 31);
-        unsigned slot = incl - cnt_lane;
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            if (act[j]) {
-                int32_t val;
-                bool rq;
-                op.active((int32_t)(v0 + j), val, rq);
-                op.own((int32_t)(v0 + j), val);
-                s_rb[wid][slot] = rb[j];
-                s_d[wid][slot] = d[j];
-                s_v[wid][slot] = val;
-                slot++;
-            }
-        }
-        __syncwarp();
-        if (lane == 0) a.verts += tot;
-        for (unsigned g0 = 0; g0 < tot; g0 += 32) {
-            unsigned k = g0 + lane;
-            uint32_t r0 = 0, dd = 0;
-            int32_t vv = 0;
-            if (k < tot) {
-                r0 = s_rb[wid][k];
-                dd = s_d[wid][k];
-                vv = s_v[wid][k];
-            }
-            relax_rows_of_warp(col, op, NoPush{}, r0, dd, vv, a);
-        }
-        __syncwarp();
-    }
-}
-
-// ================================================================ expansions
-// Block-wide compaction helper: every thread offers at most one index; the
-// offered indices are gathered in shared memory (order not kept).
-__device__ __forceinline__ int block_compact(bool offer, int32_t idx, int32_t *s_list, int *s_n) {
-    if (threadIdx.x == 0) *s_n = 0;
-    __syncthreads();
-    unsigned bal = __ballot_sync(0xffffffffu, offer);
-    int base = 0;
-    if (lane_id() == 0 && bal) base = atomicAdd(s_n, __popc(bal));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (offer) s_list[base + __popc(bal & lanemask_lt())] = idx;
-    __syncthreads();
-    return *s_n;
-}
-
-// Bucketed vertex expansion: high chunks by whole CTAs, mid vertices by warps,
-// low vertices by threads with the warp's edges redistributed over its lanes.
-// Activity is tested for many items at once (256 chunks per CTA, 32 mid
-// vertices per warp) so that inactive items cost one parallel load.
-template <class OP, class PUSH>
-__device__ __forceinline__ void expand_vertices(const uint32_t *__restrict__ row_off, const int32_t *__restrict__ col,
-                                                const int32_t *low, int n_low, const int32_t *mid, int n_mid,
-                                                const int2 *high, int n_high, const OP &op, const PUSH &push,
-                                                Acc &a) {
-    __shared__ int32_t s_list[kBlock];
-    __shared__ int32_t s_cval[kBlock];
-    __shared__ int s_n;
-    const unsigned lane = lane_id();
-    // high-degree chunks: dealt to the CTAs round-robin, one CTA per chunk
-    const int64_t G = gridDim.x;
-    for (int64_t base = blockIdx.x; base < n_high; base += G * kBlock) {
-        const int64_t ci = base + (int64_t)threadIdx.x * G;
-        bool act = false, rq = false;
-        int32_t cval = 0, cv = 0;
-        if (ci < n_high) {
-            cv = ldcg(&high[ci].x);
-            const int32_t cb = ldcg(&high[ci].y);
-            act = op.active(cv, cval, rq);
-            if (act && (uint32_t)cb == __ldg(row_off + cv)) {
-                op.own(cv, cval);
-                a.verts++;
-            }
-        }
-        push(rq, cv, a);
-        s_cval[threadIdx.x] = cval;
-        const int na = block_compact(act, (int32_t)threadIdx.x, s_list, &s_n);
-        for (int i = 0; i < na; i++) {
-            const int t = s_list[i];
-            const int64_t cj = base + (int64_t)t * G;
-            const int32_t vtx = ldcg(&high[cj].x);
-            const uint32_t e0 = (uint32_t)ldcg(&high[cj].y);
-            const uint32_t e1 = min(e0 + (uint32_t)kChunk, __ldg(row_off + vtx + 1));
-            const int32_t vv = op.refresh(vtx, s_cval[t]);
-            if (threadIdx.x == 0) a.edges += e1 - e0;
-            for (uint32_t eb = e0; eb < e1; eb += kBlock * kU) {
-                uint32_t e[kU];
-                int32_t val[kU];
-                bool in[kU];
-#pragma unroll
-                for (int j = 0; j < kU; j++) {
-                    e[j] = eb + j * kBlock + threadIdx.x;
-                    in[j] = e[j] < e1;
-                    val[j] = vv;
-                }
-                relax_batch(col, op, push, e, val, in, a);
-            }
-        }
-        __syncthreads();
-    }
-    const int gw = (int)((blockIdx.x * (unsigned)kBlock + threadIdx.x) >> 5);
-    const int nw = (int)(gridDim.x * (unsigned)kWarps);
-    // mid-degree vertices: a warp tests 32 at once, then expands the active
-    // ones one after the other with all its lanes
-    for (int base = gw; base < n_mid; base += nw * 32) {
-        const int i = base + (int)lane * nw;
-        int32_t u = 0, vv = 0;
-        bool act = false, rq = false;
-        if (i < n_mid) {
-            u = ldcg(mid + i);
-            act = op.active(u, vv, rq);
-            if (act) op.own(u, vv);
-        }
-        push(rq, u, a);
-        unsigned bal = __ballot_sync(0xffffffffu, act);
-        if (lane == 0) a.verts += __popc(bal);
-        while (bal) {
-            const int l = __ffs(bal) - 1;
-            bal &= bal - 1;
-            const int32_t uu = __shfl_sync(0xffffffffu, u, l);
-            const int32_t uval = op.refresh(uu, __shfl_sync(0xffffffffu, vv, l));
-            const uint32_t b = __ldg(row_off + uu), en = __ldg(row_off + uu + 1);
-            if (lane == 0) a.edges += en - b;
-            for (uint32_t eb = b; eb < en; eb += 32 * kU) {
-                uint32_t e[kU];
-                int32_t val[kU];
-                bool in[kU];
-#pragma unroll
-                for (int j = 0; j < kU; j++) {
-                    e[j] = eb + 32 * j + lane;
-                    in[j] = e[j] < en;
-                    val[j] = uval;
-                }
-                relax_batch(col, op, push, e, val, in, a);
-            }
-        }
-    }
-    // low-degree vertices: a thread each, edges redistributed over the warp
-    for (int base = gw * 32; base < n_low; base += nw * 32) {
-        int i = base + (int)lane;
-        int32_t vv = 0, u = 0;
-        uint32_t rb = 0, d = 0;
-        bool rq = false;
-        if (i < n_low) {
-            u = ldcg(low + i);
-            if (op.active(u, vv, rq)) {
-                op.own(u, vv);
-                rb = __ldg(row_off + u);
-                d = __ldg(row_off + u + 1) - rb;
-                a.verts++;
-            }
-        }
-        push(rq, u, a);
-        relax_rows_of_warp(col, op, push, rb, d, vv, a);
-    }
-}
-
-// Edge-parallel sweep over the source-sorted COO: each thread takes four
-// consecutive edges with a 128-bit load of src, and the activity test of a
-// source is reused across consecutive edges of the same source.  The thread
-// that holds an active source's first edge (the previous edge has another
-// source) also carries the source's value (op.own), so the synchronous
-// edge mode needs no separate pass over the vertices.
-template <class OP>
-__device__ __forceinline__ void expand_edges(const int32_t *__restrict__ src, const int32_t *__restrict__ col,
-                                             int64_t m, const OP &op, Acc &a) {
-    static_assert(kU == 4, "one int4 of sources per thread");
-    const int64_t tid = blockIdx.x * (int64_t)kBlock + threadIdx.x;
-    const int64_t nth = (int64_t)gridDim.x * kBlock;
-    const int64_t m4 = m >> 2;
-    const int4 *src4 = reinterpret_cast<const int4 *>(src);
-    const unsigned lane = lane_id();
-    if (tid == 0) a.scanned += (uint64_t)m;    // every edge's source is read once per round
-    for (int64_t q0 = tid - lane; q0 < m4; q0 += nth) {   // warp-uniform trip count
-        const int64_t q = q0 + lane;
-        int32_t us[4] = {-1, -1, -1, -1};
-        if (q < m4) {
-            int4 s4 = __ldg(src4 + q);
-            us[0] = s4.x; us[1] = s4.y; us[2] = s4.z; us[3] = s4.w;
-        }
-        // source of the edge before this thread's first edge
-        int32_t before = __shfl_up_sync(0xffffffffu, us[3], 1);
-        if (lane == 0) before = (q > 0 && q < m4) ? __ldg(src + 4 * q - 1) : -1;
-        uint32_t e[4];
-        int32_t val[4];
-        bool in[4];
-        int32_t prev = before, pval = 0;
-        bool pact = false;
-        if (before >= 0 && q < m4) {
-            bool rq;
-            pact = op.active(before, pval, rq);
-        }
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            if (us[j] < 0) {
-                pact = false;
-            } else if (us[j] != prev) {
-                bool rq;
-                pact = op.active(us[j], pval, rq);
-                if (pact) {
-                    op.own(us[j], pval);
-                    a.verts++;
-                }
-                prev = us[j];
-            }
-            e[j] = (uint32_t)(4 * q + j);
-            val[j] = pval;
-            in[j] = pact;
-            a.edges += pact;
-        }
-        relax_batch(col, op, NoPush{}, e, val, in, a);
-    }
-    for (int64_t x = 4 * m4 + tid; x < m; x += nth) {
-        int32_t vv;
-        bool rq;
-        int32_t u = __ldg(src + x);
-        if (op.active(u, vv, rq)) {
-            if (x == 0 || __ldg(src + x - 1) != u) {
-                op.own(u, vv);
-                a.verts++;
-            }
-            int32_t v = __ldg(col + x), c, pv;
-            if (op.cand(vv, (uint32_t)x, c, a)) {
-                pv = op.probe(v);
-                op.commit(v, c, pv, a);
-            }
-            a.edges++;
-        }
-    }
-}
-
-// Load-balanced expansion of a vertex worklist to its out-edges (edge-async).
-// Phase 1 (before the caller's grid barrier): each CTA takes a contiguous
-// slice of the worklist and writes the exclusive prefix sum of its items'
-// degrees (lb_off) and its slice total (lb_blk).
-__device__ __forceinline__ void lb_prefix(const uint32_t *__restrict__ row_off, const int32_t *items, int n_items,
-                                          uint32_t *lb_off, uint32_t *lb_blk) {
-    __shared__ uint32_t s_tot;
-    __shared__ uint32_t warp_tot[kWarps];
-    int S = (n_items + gridDim.x - 1) / gridDim.x;
-    int lo = min(n_items, (int)blockIdx.x * S), hi = min(n_items, lo + S);
-    uint32_t run = 0;
-    for (int t0 = lo; t0 < hi; t0 += kBlock) {
-        int i = t0 + threadIdx.x;
-        uint32_t d = 0;
-        if (i < hi) {
-            int32_t u = ldcg(items + i);
-            d = __ldg(row_off + u + 1) - __ldg(row_off + u);
-        }
-        uint32_t inc = warp_inclusive_scan(d);
-        int wid = threadIdx.x >> 5;
-        if (lane_id() == 31) warp_tot[wid] = inc;
-        __syncthreads();
-        if (wid == 0) {
-            uint32_t t = lane_id() < (unsigned)kWarps ? warp_tot[lane_id()] : 0u;
-            uint32_t ti = warp_inclusive_scan(t);
-            if (lane_id() < (unsigned)kWarps) warp_tot[lane_id()] = ti - t;
-            if (lane_id() == kWarps - 1) s_tot = ti;
-        }
-        __syncthreads();
-        if (i < hi) lb_off[i] = run + warp_tot[wid] + inc - d;
-        run += s_tot;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) lb_blk[blockIdx.x] = run;
-}
-
-constexpr int kMaxGrid = 152 * 8;   // persistent CTAs (lb prefix table size)
-
-// Phase 2 (after the barrier): the edge space [0, T) is split evenly over the
-// CTAs; each CTA walks its range in tiles, staging up to kBlock items'
-// offsets, row starts and values in shared memory, and every thread finds the
-// owner of its edges by binary search in shared memory.
-template <class OP, class PUSH>
-__device__ __forceinline__ void lb_expand(const uint32_t *__restrict__ row_off, const int32_t *__restrict__ col,
-                                          const int32_t *items, int n_items, const uint32_t *lb_off,
-                                          const uint32_t *lb_blk, const OP &op, const PUSH &push, Acc &a) {
-    __shared__ uint32_t sP[kMaxGrid + 1];
-    __shared__ uint32_t s_goff[kBlock + 1];
-    __shared__ uint32_t s_rb[kBlock];
-    __shared__ int32_t s_val[kBlock];
-    __shared__ int s_i0;
-    __shared__ uint32_t s_t1;
-    const int G = gridDim.x;
-    // exclusive scan of the slice totals, redundantly in every CTA
-    {
-        __shared__ uint32_t warp_tot[kWarps];
-        __shared__ uint32_t carry;
-        if (threadIdx.x == 0) carry = 0;
-        __syncthreads();
-        for (int t0 = 0; t0 < G; t0 += kBlock) {
-            int i = t0 + threadIdx.x;
-            uint32_t x = i < G ? ldcg((const int32_t *)lb_blk + i) : 0u;
-            uint32_t inc = warp_inclusive_scan(x);
-            int wid = threadIdx.x >> 5;
-            if (lane_id() == 31) warp_tot[wid] = inc;
-            __syncthreads();
-            if (wid == 0) {
-                uint32_t t = lane_id() < (unsigned)kWarps ? warp_tot[lane_id()] : 0u;
-                uint32_t ti = warp_inclusive_scan(t);
-                if (lane_id() < (unsigned)kWarps) warp_tot[lane_id()] = ti - t;
-            }
-            __syncthreads();
-            if (i < G) sP[i] = carry + warp_tot[wid] + inc - x;
-            __syncthreads();
-            if (threadIdx.x == kBlock - 1) carry += warp_tot[wid] + inc;
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) sP[G] = carry;
-        __syncthreads();
-    }
-    const uint32_t T = sP[G];
-    if (T == 0) return;
-    const int S = (n_items + G - 1) / G;
-    const uint64_t lo = (uint64_t)T * blockIdx.x / G, hi = (uint64_t)T * (blockIdx.x + 1) / G;
-    if (lo >= hi) return;
-    // global offset of item i
-    auto goff = [&](int i) -> uint32_t { return sP[i / S] + (uint32_t)ldcg((const int32_t *)lb_off + i); };
-    if (threadIdx.x == 0) {
-        // item containing edge lo: last item with goff <= lo
-        int l = 0, r = n_items - 1;
-        while (l < r) {
-            int mdl = (l + r + 1) >> 1;
-            if (goff(mdl) <= (uint32_t)lo) l = mdl; else r = mdl - 1;
-        }
-        s_i0 = l;
-    }
-    __syncthreads();
-    uint32_t t0 = (uint32_t)lo;
-    while (t0 < (uint32_t)hi) {
-        int i0 = s_i0;
-        int cnt = min(kBlock, n_items - i0);
-        bool rq = false;
-        int32_t u = 0;
-        if ((int)threadIdx.x < cnt) {
-            int i = i0 + threadIdx.x;
-            u = ldcg(items + i);
-            s_goff[threadIdx.x] = goff(i);
-            s_rb[threadIdx.x] = __ldg(row_off + u);
-            int32_t val = 0;
-            op.active(u, val, rq);
-            s_val[threadIdx.x] = val;
-        }
-        push(rq, u, a);
-        if (threadIdx.x == 0) s_goff[cnt] = (i0 + cnt < n_items) ? goff(i0 + cnt) : T;
-        __syncthreads();
-        uint32_t t1 = min((uint32_t)hi, min(t0 + (uint32_t)(kBlock * kU), s_goff[cnt]));
-        uint32_t e[kU];
-        int32_t val[kU];
-        bool in[kU];
-#pragma unroll
-        for (int j = 0; j < kU; j++) {
-            uint32_t x = t0 + j * kBlock + threadIdx.x;
-            in[j] = x < t1;
-            e[j] = 0;
-            val[j] = 0;
-            if (in[j]) {
-                int l = 0, r = cnt - 1;
-                while (l < r) {
-                    int mdl = (l + r + 1) >> 1;
-                    if (s_goff[mdl] <= x) l = mdl; else r = mdl - 1;
-                }
-                e[j] = s_rb[l] + (x - s_goff[l]);
-                val[j] = s_val[l];
-                a.edges++;
-            }
-        }
-        relax_batch(col, op, push, e, val, in, a);
-        if (threadIdx.x == 0) {
-            // next tile starts at edge t1; find its item among the staged ones
-            int l = 0, r = cnt;   // s_goff[cnt] may equal t1 (then item i0 + cnt)
-            while (l < r) {
-                int mdl = (l + r + 1) >> 1;
-                if (s_goff[mdl] <= t1) l = mdl; else r = mdl - 1;
-            }
-            s_i0 = i0 + l;
-            s_t1 = t1;
-        }
-        __syncthreads();
-        t0 = s_t1;
-        __syncthreads();
-    }
-}
-
-// ================================================================ sparse edge-sync rounds
-// A round of the synchronous edge mode normally streams every edge's source.
-// When the previous round changed few vertices the round is "sparse": a
-// flag pass first marks the 1024-edge chunks whose sources include an active
-// vertex (from the activity words of 256-vertex groups), and only those
-// chunks are streamed.  The choice is made identically by every CTA.
-
-// Flag pass: one warp per 256-vertex group; if any vertex of the group is
-// active (activity word == act_val), flag the edge chunks holding the
-// group's out-edges with `round`.
-__device__ __forceinline__ void flag_edge_chunks(const uint32_t *__restrict__ row_off, const int32_t *actw,
-                                                 int32_t act_val, int32_t n, int32_t *eflag, int32_t round,
-                                                 Acc &a) {
-    const unsigned lane = lane_id();
-    const int64_t gw = (blockIdx.x * (int64_t)kBlock + threadIdx.x) >> 5;
-    const int64_t nw = (int64_t)gridDim.x * kWarps;
-    const int64_t ngr = ((int64_t)n + kVGroup - 1) >> kVGroupLog;
-    for (int64_t gi = gw; gi < ngr; gi += nw) {
-        const int64_t vlo = gi << kVGroupLog, vhi = min((int64_t)n, vlo + kVGroup);
-        bool any = false;
-#pragma unroll
-        for (int h = 0; h < kVGroup / 128; h++) {
-            const int64_t v0 = vlo + 128 * h + 4 * lane;
-            if (v0 + 3 < vhi) {
-                int4 t = __ldcg(reinterpret_cast<const int4 *>(actw + v0));
-                any |= (t.x == act_val) | (t.y == act_val) | (t.z == act_val) | (t.w == act_val);
-            } else {
-                for (int j = 0; j < 4; j++)
-                    if (v0 + j < vhi) any |= ldcg(actw + v0 + j) == act_val;
-            }
-        }
-        if (lane == 0) a.scanned += vhi - vlo;
-        if (!__any_sync(0xffffffffu, any)) continue;
-        const uint32_t eb = __ldg(row_off + vlo), ee = __ldg(row_off + vhi);
-        if (ee > eb)
-            for (uint32_t k = (eb >> kEChunkLog) + lane; k <= (ee - 1) >> kEChunkLog; k += 32) stcg(eflag + k, round);
-    }
-}
-
-// Stream pass of a sparse round: the 1024-edge chunks are dealt to the CTAs
-// round-robin; a CTA reads the flags of up to 256 of its chunks at once,
-// keeps the flagged ones and streams each with one 128-bit load of src per
-// thread (first-edge carry as in expand_edges).
-template <class OP>
-__device__ __forceinline__ void expand_flagged_chunks(const int32_t *__restrict__ src, const int32_t *__restrict__ col,
-                                                      int64_t m, const int32_t *eflag, int32_t round, const OP &op,
-                                                      Acc &a) {
-    __shared__ int32_t s_klist[kBlock];
-    __shared__ int s_kn;
-    const int64_t nec = (m + kEChunk - 1) >> kEChunkLog;
-    const int64_t m4 = m >> 2;
-    const int4 *src4 = reinterpret_cast<const int4 *>(src);
-    const int64_t G = gridDim.x;
-    const unsigned lane = lane_id();
-    for (int64_t base = blockIdx.x; base < nec; base += G * kBlock) {
-        const int64_t k = base + (int64_t)threadIdx.x * G;
-        const bool act = k < nec && ldcg(eflag + k) == round;
-        const int na = block_compact(act, (int32_t)k, s_klist, &s_kn);
-        for (int i = 0; i < na; i++) {
-            const int64_t kk = s_klist[i];
-            const int64_t e0 = kk << kEChunkLog, e1 = min(m, e0 + kEChunk);
-            if (threadIdx.x == 0) a.scanned += e1 - e0;
-            const int64_t q = (e0 >> 2) + threadIdx.x;
-            const bool qin = q < min(m4, (e1 + 3) >> 2) && q < m4;
-            int32_t us[4] = {-1, -1, -1, -1};
-            if (qin) {
-                int4 s4 = __ldg(src4 + q);
-                us[0] = s4.x; us[1] = s4.y; us[2] = s4.z; us[3] = s4.w;
-            }
-            int32_t before = __shfl_up_sync(0xffffffffu, us[3], 1);
-            if (lane == 0) before = (qin && q > 0) ? __ldg(src + 4 * q - 1) : -1;
-            uint32_t e[4];
-            int32_t val[4];
-            bool in[4];
-            int32_t prev = before, pval = 0;
-            bool pact = false;
-            if (before >= 0 && qin) {
-                bool rq;
-                pact = op.active(before, pval, rq);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                if (us[j] < 0) {
-                    pact = false;
-                } else if (us[j] != prev) {
-                    bool rq;
-                    pact = op.active(us[j], pval, rq);
-                    if (pact) {
-                        op.own(us[j], pval);
-                        a.verts++;
-                    }
-                    prev = us[j];
-                }
-                e[j] = (uint32_t)(4 * q + j);
-                val[j] = pval;
-                in[j] = pact;
-                a.edges += pact;
-            }
-            relax_batch(col, op, NoPush{}, e, val, in, a);
-            // the last chunk may end with up to three edges past the 128-bit part
-            const int64_t x = max(e0, 4 * m4) + threadIdx.x;
-            if (x < e1) {
-                int32_t vv;
-                bool rq;
-                int32_t u = __ldg(src + x);
-                if (op.active(u, vv, rq)) {
-                    if (x == 0 || __ldg(src + x - 1) != u) {
-                        op.own(u, vv);
-                        a.verts++;
-                    }
-                    int32_t v = __ldg(col + x), cc, pv;
-                    if (op.cand(vv, (uint32_t)x, cc, a)) {
-                        pv = op.probe(v);
-                        op.commit(v, cc, pv, a);
-                    }
-                    a.edges++;
-                }
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// ================================================================ the kernel
-// Resident CTAs per SM the register budget is sized for: the synchronous
-// modes gain from more warps in flight; the worklist modes do not.
-#ifndef FG_SYNC_MIN_BLOCKS
-#define FG_SYNC_MIN_BLOCKS 6
-#endif
-#ifndef FG_ASYNC_MIN_BLOCKS
-#define FG_ASYNC_MIN_BLOCKS 4
-#endif
-template <int MODE>
-constexpr int min_blocks() {
-    return (MODE == kVertexSync || MODE == kEdgeSync) ? FG_SYNC_MIN_BLOCKS : FG_ASYNC_MIN_BLOCKS;
-}
-
 template <int ALGO, int MODE>
 __global__ void __launch_bounds__(kBlock, min_blocks<MODE>()) fixpoint_kernel(Params p) {
-    constexpr bool SYNC = (MODE == kVertexSync || MODE == kEdgeSync);
-    Ctrl *c = p.ctrl;
-    const View &g = p.g;
-    const int32_t n = g.n;
-    const int64_t tid = blockIdx.x * (int64_t)kBlock + threadIdx.x;
-    const int64_t nth = (int64_t)gridDim.x * kBlock;
-    Acc a;
-    int rounds = 0;
-    int n_barriers = 0;
-    // every grid barrier of the query; CTA 0 optionally timestamps each
-    auto sync_ = [&]() -> bool {
-        bool r = grid_sync(c, p.timeout_ns);
-        if (tid == 0) {
-            if (p.trace && n_barriers < p.trace_cap) p.trace[n_barriers] = global_ns();
-            n_barriers++;
-        }
-        return r;
-    };
-
-    // ---- init: values, stamps, initial worklist (a2)
-    for (int64_t v = tid; v < n; v += nth) {
-        int32_t x = (ALGO == kCC) ? (int32_t)v : (v == p.source ? 0 : kInf);
-        p.A[v] = x;
-        if (SYNC && ALGO != kBFS) {
-            p.B[v] = x;
-            p.S1[v] = (ALGO == kCC || v == p.source) ? 1 : 0;   // active in round 1
-            p.S0[v] = 0;
-        }
-        if (!SYNC && ALGO != kBFS) p.S0[v] = 0;
-    }
-    if (MODE == kEdgeSync)
-        for (int64_t k = tid; k < ((g.m + kEChunk - 1) >> kEChunkLog); k += nth) p.eflag[k] = 0;
-
-    if (!SYNC && ALGO != kCC && tid == 0) {
-        int32_t s = p.source;
-        uint32_t b = g.row_off[s], d = g.row_off[s + 1] - b;
-        if (d > 0) {
-            if (MODE == kEdgeAsync) {
-                p.wl[0][0][0] = s;
-                c->wl_size[0][0] = 1;
-            } else if (d < (uint32_t)kLowMax) {
-                p.wl[0][kWlLow][0] = s;
-                c->wl_size[0][kWlLow] = 1;
-            } else if (d < (uint32_t)kMidMax) {
-                p.wl[0][kWlMid][0] = s;
-                c->wl_size[0][kWlMid] = 1;
-            } else {
-                int nck = (int)((d + kChunk - 1) / kChunk);
-                int2 *h = reinterpret_cast<int2 *>(p.wl[0][kWlHigh]);
-                for (int k = 0; k < nck; k++) h[k] = make_int2(s, (int32_t)(b + (uint32_t)k * kChunk));
-                c->wl_size[0][kWlHigh] = nck;
-            }
-        }
-    }
-    // failure-detection test: CTA 0 never arrives, the others' waits run out
-    if (p.inject_missing_arrival && blockIdx.x == 0) return;
-    bool ok = sync_();
-
-    if (SYNC && ok) {
-        int pass_ctr = 0;
-        // edge-sync: a round is sparse if the previous one accepted fewer
-        // candidates than n/8 (round 1: only the source is active, except CC)
-        auto sparse_round = [&](int r) -> bool {
-            if (r == 1) return ALGO != kCC;
-            return (int64_t)__ldcg(&c->changed[(r - 1) % 3]) * 8 < (int64_t)n;
-        };
-        for (int r = 1;; r++) {
-            if (r > p.max_rounds) {
-                if (tid == 0) atomicOr(&c->status, kStRoundCap);
-                break;
-            }
-            if (tid == 0) c->changed[(r + 1) % 3] = 0;
-            rounds = r;
-            if (ALGO == kBFS) {
-                BfsSyncOp op{p.A, r - 1};
-                if (MODE == kVertexSync) {
-                    expand_vertices(g.row_off, g.col, g.low, 0, g.mid, g.n_mid, g.high, g.n_high_chunks, op,
-                                    NoPush{}, a);
-                    expand_low_dense(g.row_off, g.col, p.A, r - 1, n, op, a);
-                } else if (sparse_round(r)) {
-                    flag_edge_chunks(g.row_off, p.A, r - 1, n, p.eflag, r, a);
-                    if (!sync_()) break;
-                    expand_flagged_chunks(g.src, g.col, g.m, p.eflag, r, op, a);
-                } else {
-                    expand_edges(g.src, g.col, g.m, op, a);
-                }
-            } else {
-                const int32_t *cur = (r & 1) ? p.A : p.B;
-                int32_t *next = (r & 1) ? p.B : p.A;
-                const int32_t *scur = (r & 1) ? p.S1 : p.S0;
-                int32_t *snext = (r & 1) ? p.S0 : p.S1;
-                SyncOp<ALGO> op{g.w, cur, next, scur, snext, r};
-                if (MODE == kVertexSync) {
-                    expand_vertices(g.row_off, g.col, g.low, 0, g.mid, g.n_mid, g.high, g.n_high_chunks, op,
-                                    NoPush{}, a);
-                    expand_low_dense(g.row_off, g.col, scur, r, n, op, a);
-                } else if (sparse_round(r)) {
-                    flag_edge_chunks(g.row_off, scur, r, n, p.eflag, r, a);
-                    if (!sync_()) break;
-                    expand_flagged_chunks(g.src, g.col, g.m, p.eflag, r, op, a);
-                } else {
-                    expand_edges(g.src, g.col, g.m, op, a);
-                }
-            }
-            int ch = block_sum(a.changed);
-            a.changed = 0;
-            if (threadIdx.x == 0 && ch) atomicAdd(&c->changed[r % 3], ch);
-            if (!sync_()) break;
-            if (__ldcg(&c->changed[r % 3]) == 0) {
-                if (tid == 0) c->result_in_b = (ALGO != kBFS) && (r & 1);
-                if (ALGO == kSSSP) {
-                    // A vertex without out-edges is never expanded, so no
-                    // carry copies its last improvement into the other
-                    // buffer: take the min of the two.
-                    int32_t *res = (r & 1) ? p.B : p.A;
-                    const int32_t *oth = (r & 1) ? p.A : p.B;
-                    for (int64_t i = tid; i < g.n_zero; i += nth) {
-                        int32_t v = __ldg(g.zero + i);
-                        int32_t x = ldcg(oth + v);
-                        if (x < ldcg(res + v)) stcg(res + v, x);
-                    }
-                }
-                break;
-            }
-            if (ALGO == kCC) {
-                // pointer jumping on next until a pass changes nothing
-                int32_t *next = (r & 1) ? p.B : p.A;
-                int32_t *snext = (r & 1) ? p.S0 : p.S1;
-                bool jok = true;
-                for (int pass = 0; pass < 16; pass++) {
-                    int slot = pass_ctr % 3;
-                    if (tid == 0) c->jchanged[(pass_ctr + 1) % 3] = 0;
-                    pass_ctr++;
-                    int jc = 0;
-                    for (int64_t v = tid; v < n; v += nth) {
-                        int32_t l = ldcg(next + v);
-                        if (l == (int32_t)v) continue;
-                        int32_t ll = ldcg(next + l);
-                        if (ll < l) {
-                            atomicMin(next + v, ll);
-                            stcg(snext + v, r + 1);
-                            jc++;
-                        }
-                    }
-                    jc = block_sum(jc);
-                    if (threadIdx.x == 0 && jc) atomicAdd(&c->jchanged[slot], jc);
-                    if (!sync_()) { jok = false; break; }
-                    if (tid == 0) c->jump_passes++;
-                    if (__ldcg(&c->jchanged[slot]) == 0) break;
-                }
-                if (!jok) break;
-            }
-        }
-    } else if (!SYNC && ok) {
-        __shared__ WarpBuf s_buf[kWarps][2];
-        if (lane_id() == 0) {
-            s_buf[threadIdx.x >> 5][0].count = 0;
-            s_buf[threadIdx.x >> 5][1].count = 0;
-        }
-        __syncwarp();
-        WarpBuf *wb = s_buf[threadIdx.x >> 5];
-        for (int gen = 0;; gen++) {
-            const int in_slot = gen % 3, out_slot = (gen + 1) % 3;
-            const bool initial_cc = (ALGO == kCC && gen == 0);
-            int n_in[3];
-            for (int k = 0; k < 3; k++) n_in[k] = __ldcg(&c->wl_size[in_slot][k]);
-            if (initial_cc) {
-                if (MODE == kEdgeAsync) {
-                    n_in[0] = g.n_nz; n_in[1] = n_in[2] = 0;
-                } else {
-                    n_in[kWlLow] = g.n_low; n_in[kWlMid] = g.n_mid; n_in[kWlHigh] = g.n_high_chunks;
-                }
-            }
-            if (n_in[0] + n_in[1] + n_in[2] == 0) break;
-            if (gen >= p.max_rounds) {
-                if (tid == 0) atomicOr(&c->status, kStRoundCap);
-                break;
-            }
-            rounds = gen + 1;
-            if (tid == 0)
-                for (int k = 0; k < 3; k++) c->wl_size[(gen + 2) % 3][k] = 0;
-            const int pi = gen & 1, po = pi ^ 1;
-            int *osize = c->wl_size[out_slot];
-            if (MODE == kVertexAsync) {
-                const int32_t *low = initial_cc ? g.low : p.wl[pi][kWlLow];
-                const int32_t *mid = initial_cc ? g.mid : p.wl[pi][kWlMid];
-                const int2 *high = initial_cc ? g.high : reinterpret_cast<const int2 *>(p.wl[pi][kWlHigh]);
-                ClassPush push{g.row_off, g.vclass, p.wl[po][kWlLow], p.wl[po][kWlMid],
-                               reinterpret_cast<int2 *>(p.wl[po][kWlHigh]), osize,
-                               p.wl_cap[kWlLow], p.wl_cap[kWlMid], p.wl_cap[kWlHigh] / 2, &wb[0], &wb[1], c};
-                if (ALGO == kBFS) {
-                    BfsAsyncOp op{p.A, gen};
-                    expand_vertices(g.row_off, g.col, low, n_in[kWlLow], mid, n_in[kWlMid], high, n_in[kWlHigh],
-                                    op, push, a);
-                } else {
-                    AsyncOp<ALGO> op{g.w, p.A, p.S0, gen};
-                    expand_vertices(g.row_off, g.col, low, n_in[kWlLow], mid, n_in[kWlMid], high, n_in[kWlHigh],
-                                    op, push, a);
-                }
-                push.flush();
-            } else {
-                const int32_t *items = initial_cc ? g.nz : p.wl[pi][0];
-                lb_prefix(g.row_off, items, n_in[0], p.lb_off, p.lb_blk);
-                if (!sync_()) break;
-                ListPush push{g.vclass, p.wl[po][0], &osize[0], p.wl_cap[0], &wb[0], c};
-                a.verts += 0;
-                if (ALGO == kBFS) {
-                    BfsAsyncOp op{p.A, gen};
-                    lb_expand(g.row_off, g.col, items, n_in[0], p.lb_off, p.lb_blk, op, push, a);
-                } else {
-                    AsyncOp<ALGO> op{g.w, p.A, p.S0, gen};
-                    lb_expand(g.row_off, g.col, items, n_in[0], p.lb_off, p.lb_blk, op, push, a);
-                }
-                push.flush();
-                if (tid == 0) a.verts += (unsigned long long)n_in[0];
-            }
-            if (!sync_()) break;
-        }
-    }
-
-    // ---- statistics
-    unsigned long long ev = block_sum(a.verts), ee = block_sum(a.edges), eu = block_sum(a.updates),
-                       ep = block_sum(a.pushes), es = block_sum(a.scanned);
-    int of = block_sum(a.overflow);
-    if (threadIdx.x == 0) {
-        if (ev) atomicAdd(&c->st_vertices, ev);
-        if (ee) atomicAdd(&c->st_edges, ee);
-        if (eu) atomicAdd(&c->st_updates, eu);
-        if (ep) atomicAdd(&c->st_pushes, ep);
-        if (es) atomicAdd(&c->st_scanned, es);
-        if (of) atomicOr(&c->status, kStOverflow);
-    }
-    if (tid == 0) {
-        c->rounds = rounds;
-        c->barriers = n_barriers;
-    }
+    const Team t{(int)blockIdx.x, (int)gridDim.x, &p.ctrl->bar_count};
+    fixpoint_body<ALGO, MODE>(p, t);
 }
 
 // One all-active sweep: vertex variant over the buckets, edge variant over
 // the COO.  Ordinary launch (no grid barrier).
 template <int MODE>
 __global__ void __launch_bounds__(kBlock) sweep_kernel(View g, const int32_t *cur, int32_t *next, Ctrl *c) {
+    const Team t{(int)blockIdx.x, (int)gridDim.x, nullptr};
     Acc a;
     SweepOp op{g.w, cur, next};
     if (MODE == kVertexSync)
-        expand_vertices(g.row_off, g.col, g.low, g.n_low, g.mid, g.n_mid, g.high, g.n_high_chunks, op, NoPush{},
+        expand_vertices(t, g.row_off, g.col, g.low, g.n_low, g.mid, g.n_mid, g.high, g.n_high_chunks, op, NoPush{},
                         a);
     else
-        expand_edges(g.src, g.col, g.m, op, a);
+        expand_edges(t, g.src, g.col, g.m, op, a);
     unsigned long long eu = block_sum(a.updates);
     int of = block_sum(a.overflow);
     if (threadIdx.x == 0) {

@@ -139,26 +139,46 @@ __device__ __forceinline__ void red_min(int32_t *p, int32_t v) {
     asm volatile("red.relaxed.gpu.global.min.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// ---------------------------------------------------------------- grid barrier
-// Sense-by-generation barrier over all CTAs of a cooperative launch.  The
-// wait is bounded by timeout_ns; on expiry the CTA records kStTimeout and
-// returns false.  It also returns false once any error bit is set, so every
-// CTA leaves the kernel at its next barrier.
-__device__ __forceinline__ bool grid_sync(Ctrl *c, unsigned long long timeout_ns) {
+// ---------------------------------------------------------------- team barrier
+// A team is the set of CTAs that run one query together: the whole grid of a
+// single-query launch, or a slice of a batched launch (down to one CTA).
+// rank/size replace blockIdx.x/gridDim.x in the work distribution; bar
+// points at the team's {arrivals, generation} pair (unused for one CTA).
+struct Team {
+    int rank;
+    int size;
+    unsigned *bar;
+};
+
+constexpr int kStFatal = kStTimeout | kStRoundCap | kStWorklist;
+
+// Sense-by-generation barrier over the CTAs of a team (all co-resident: the
+// launch is cooperative).  The wait is bounded by timeout_ns; on expiry the
+// CTA records kStTimeout in the query's status and returns false.  It also
+// returns false once any fatal error bit is set, so every CTA of the team
+// leaves the query at its next barrier.  A one-CTA team needs only
+// __syncthreads.
+__device__ __forceinline__ bool team_sync(const Team &t, Ctrl *c, unsigned long long timeout_ns) {
     __shared__ int s_ok;
     __syncthreads();
+    if (t.size == 1) {
+        if (threadIdx.x == 0) s_ok = !(ld_acquire_i(&c->status) & kStFatal);
+        __syncthreads();
+        return s_ok != 0;
+    }
     if (threadIdx.x == 0) {
         int ok = 1;
         __threadfence();
-        unsigned gen = ld_acquire(&c->bar_gen);
-        unsigned arrived = atom_add_acq_rel(&c->bar_count, 1u) + 1u;
-        if (arrived == gridDim.x) {
-            c->bar_count = 0;
-            st_release(&c->bar_gen, gen + 1u);
+        unsigned *count = t.bar, *genp = t.bar + 1;
+        unsigned gen = ld_acquire(genp);
+        unsigned arrived = atom_add_acq_rel(count, 1u) + 1u;
+        if (arrived == (unsigned)t.size) {
+            *count = 0;
+            st_release(genp, gen + 1u);
         } else {
             unsigned long long t0 = global_ns();
             unsigned spins = 0;
-            while (ld_acquire(&c->bar_gen) == gen) {
+            while (ld_acquire(genp) == gen) {
                 if (++spins > 64) {
                     __nanosleep(32);
                     if (global_ns() - t0 > timeout_ns) {
@@ -170,11 +190,17 @@ __device__ __forceinline__ bool grid_sync(Ctrl *c, unsigned long long timeout_ns
             }
         }
         __threadfence();
-        if (ld_acquire_i(&c->status) & (kStTimeout | kStRoundCap | kStWorklist)) ok = 0;
+        if (ld_acquire_i(&c->status) & kStFatal) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// The whole grid of a cooperative launch as one team.
+__device__ __forceinline__ bool grid_sync(Ctrl *c, unsigned long long timeout_ns) {
+    const Team t{(int)blockIdx.x, (int)gridDim.x, &c->bar_count};
+    return team_sync(t, c, timeout_ns);
 }
 
 // ---------------------------------------------------------------- warp helpers
