@@ -226,6 +226,54 @@ fg_status fg_sssp_csr_noalloc(int32_t n, int64_t m, const int64_t *row_off, cons
    threads and devices); lets a caller count the device work of a region. */
 uint64_t fg_kernel_launches(void);
 
+/*
+ * Batches: many queries over many resident graphs in one launch per
+ * (algorithm, mode) kind present, the kinds running concurrently -- the
+ * runtime form of the paper's barrier-free kernels on separate streams
+ * (Sec. 3.2) and independent parallel sections (Sec. 3.4).  Each launch is
+ * a persistent kernel split into teams of CTAs (team size from the query's
+ * edge count, CTA share from its estimated work); teams pull queries from
+ * size-class queues and run each fixpoint with a team-local barrier.
+ * Results are identical to fg_run's.
+ */
+typedef struct {
+    const fg_graph *g;          /* graph on the current device */
+    int32_t algo;               /* fg_algo */
+    int32_t src;                /* source vertex (ignored for CC) */
+    int32_t *out;               /* int32[n] result, host or device memory */
+    int32_t mode;               /* fg_mode; FG_AUTO = fg_select_mode's choice */
+} fg_query;
+
+typedef struct {
+    void *stream;               /* cudaStream_t; NULL = legacy default stream */
+    int32_t use_cuda_graph;     /* nonzero: capture the launches in a CUDA graph, launch it */
+    int32_t wait_timeout_ms;    /* bound on any device-side wait; 0 = 1000 ms */
+} fg_batch_options;
+
+typedef struct {
+    float kernel_ms;            /* device time of the batch (events around all launches) */
+    int32_t launches;           /* persistent kernels launched (kinds present) */
+    int32_t teams;              /* teams over all launches */
+    int32_t ctas;               /* CTAs over all launches */
+} fg_batch_stats;
+
+/*
+ * Runs nq queries.  status_out[nq] and stats_out[nq] (each may be NULL)
+ * receive every query's outcome and counters (kernel_ms is per batch, in
+ * bstats).  Returns FG_OK if every query succeeded, else the first failing
+ * query's status; the outputs of successful queries are written either way.
+ */
+fg_status fg_run_batch(const fg_query *queries, int32_t nq, const fg_batch_options *opt,
+                       fg_status *status_out, fg_stats *stats_out, fg_batch_stats *bstats);
+
+/*
+ * Autotuner: times the four modes on this graph (one query each from src,
+ * ignored for CC), writes their device times in ms to times_ms[4] (may be
+ * NULL) and the fastest mode to *best, and caches it on the handle:
+ * fg_select_mode (and FG_AUTO) return the cached choice from then on.
+ */
+fg_status fg_autotune(const fg_graph *g, fg_algo algo, int32_t src, fg_mode *best, float *times_ms);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *fg_last_error(void);
 /* Name of a status code. */

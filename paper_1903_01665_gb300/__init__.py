@@ -70,6 +70,24 @@ class fg_graph_info_t(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class fg_query(ctypes.Structure):
+    _fields_ = [("g", ctypes.c_void_p), ("algo", ctypes.c_int32), ("src", ctypes.c_int32),
+                ("out", ctypes.c_void_p), ("mode", ctypes.c_int32)]
+
+
+class fg_batch_options(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p), ("use_cuda_graph", ctypes.c_int32),
+                ("wait_timeout_ms", ctypes.c_int32)]
+
+
+class fg_batch_stats(ctypes.Structure):
+    _fields_ = [("kernel_ms", ctypes.c_float), ("launches", ctypes.c_int32), ("teams", ctypes.c_int32),
+                ("ctas", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 _VP = ctypes.c_void_p
 _SIGNATURES = {
@@ -87,6 +105,11 @@ _SIGNATURES = {
                                 ctypes.POINTER(ctypes.c_float)]),
     "fg_sssp_csr_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _VP, _VP, _VP, ctypes.c_int32,
                                            _VP, _VP]),
+    "fg_run_batch": (ctypes.c_int, [ctypes.POINTER(fg_query), ctypes.c_int32, ctypes.POINTER(fg_batch_options),
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(fg_stats),
+                                    ctypes.POINTER(fg_batch_stats)]),
+    "fg_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_float)]),
     "fg_kernel_launches": (ctypes.c_uint64, []),
     "fg_last_error": (ctypes.c_char_p, []),
     "fg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -223,6 +246,32 @@ def fg_sweep(g, mode, cur, nxt, stream=None):
     ms = ctypes.c_float(0)
     st = load().fg_sweep(g, int(mode), _ptr(cur), _ptr(nxt), stream, ctypes.byref(upd), ctypes.byref(ms))
     return st, upd.value, ms.value
+
+
+def fg_run_batch(queries, stream=None, use_cuda_graph=False, wait_timeout_ms=0):
+    """queries: list of (graph, algo, src, out_array, mode).  Returns
+    (status, [per-query status], [per-query fg_stats], fg_batch_stats)."""
+    nq = len(queries)
+    arr = (fg_query * nq)()
+    for i, (g, algo, src, out, mode) in enumerate(queries):
+        _check_dtype(out, "int32")
+        arr[i] = fg_query(g, int(algo), int(src), _ptr(out), int(mode))
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    opt = fg_batch_options(stream, 1 if use_cuda_graph else 0, int(wait_timeout_ms))
+    sts = (ctypes.c_int * nq)()
+    stats = (fg_stats * nq)()
+    bst = fg_batch_stats()
+    st = load().fg_run_batch(arr, nq, ctypes.byref(opt), sts, stats, ctypes.byref(bst))
+    return st, list(sts), list(stats), bst
+
+
+def fg_autotune(g, algo, src=0):
+    """Returns (status, best mode, [ms per mode])."""
+    best = ctypes.c_int(-1)
+    times = (ctypes.c_float * 4)()
+    st = load().fg_autotune(g, int(algo), int(src), ctypes.byref(best), times)
+    return st, best.value, list(times)
 
 
 FG_NOALLOC_MAX_VERTICES = 1048576

@@ -1,0 +1,377 @@
+// Batched queries: many sources over many resident graphs in one launch per
+// (algorithm, mode) kind present -- the runtime counterpart of the paper's
+// barrier-free kernels on separate streams (Sec. 3.2) and of its
+// independent parallel sections (Sec. 3.4).
+//
+// Each launch is a persistent cooperative kernel whose CTAs are split into
+// teams; every team pulls queries from the queue of its size class and runs
+// the whole fixpoint of each with a team-local barrier (a one-CTA team needs
+// only __syncthreads).  The team size of a query comes from its edge count,
+// the CTA budget of each kind and class from its estimated work.  Kinds run
+// concurrently on forked streams, optionally captured in one CUDA graph.
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "fg_device.cuh"
+
+namespace fg {
+
+namespace {
+
+struct BatchArgs {
+    const int4 *cta_team;     // per CTA: team, rank in team, team size, class
+    unsigned *team_bar;       // 2 per team: arrivals, generation
+    int *team_q;              // per team: the queue slot it is working on
+    int *cls_next;            // per class: next queue slot
+    const int *cls_begin;     // per class: queue range in `order`
+    const int *cls_end;
+    const int *order;         // query indices, by class, largest work first
+    const Params *params;     // per query of the batch
+    Ctrl *bctrl;              // status of the queue barriers
+    unsigned long long timeout_ns;
+};
+
+template <int ALGO, int MODE>
+__global__ void __launch_bounds__(kBlock, min_blocks<MODE>()) batch_kernel(BatchArgs b) {
+    const int4 ct = b.cta_team[blockIdx.x];
+    const Team t{ct.y, ct.z, b.team_bar + 2 * ct.x};
+    const int cls = ct.w;
+    for (;;) {
+        if (t.rank == 0 && threadIdx.x == 0) b.team_q[ct.x] = b.cls_begin[cls] + atomicAdd(&b.cls_next[cls], 1);
+        if (!team_sync(t, b.bctrl, b.timeout_ns)) return;
+        const int qi = __ldcg(&b.team_q[ct.x]);
+        if (qi >= b.cls_end[cls]) return;
+        fixpoint_body<ALGO, MODE>(b.params[b.order[qi]], t);
+        if (!team_sync(t, b.bctrl, b.timeout_ns)) return;
+    }
+}
+
+using BatchFn = void (*)(BatchArgs);
+
+BatchFn batch_kernel_for(int kind) {
+    switch (kind) {
+        case kSSSP * 4 + kVertexSync: return batch_kernel<kSSSP, kVertexSync>;
+        case kSSSP * 4 + kVertexAsync: return batch_kernel<kSSSP, kVertexAsync>;
+        case kSSSP * 4 + kEdgeSync: return batch_kernel<kSSSP, kEdgeSync>;
+        case kSSSP * 4 + kEdgeAsync: return batch_kernel<kSSSP, kEdgeAsync>;
+        case kBFS * 4 + kVertexSync: return batch_kernel<kBFS, kVertexSync>;
+        case kBFS * 4 + kVertexAsync: return batch_kernel<kBFS, kVertexAsync>;
+        case kBFS * 4 + kEdgeSync: return batch_kernel<kBFS, kEdgeSync>;
+        case kBFS * 4 + kEdgeAsync: return batch_kernel<kBFS, kEdgeAsync>;
+        case kCC * 4 + kVertexSync: return batch_kernel<kCC, kVertexSync>;
+        case kCC * 4 + kVertexAsync: return batch_kernel<kCC, kVertexAsync>;
+        case kCC * 4 + kEdgeSync: return batch_kernel<kCC, kEdgeSync>;
+        case kCC * 4 + kEdgeAsync: return batch_kernel<kCC, kEdgeAsync>;
+    }
+    return nullptr;
+}
+
+// CTAs a query's team gets: one per ~128K edges, a power of two in [1, 128].
+int team_size_for(int64_t m) {
+    int s = 1;
+    while (s < 128 && (int64_t)s * (1 << 17) < m) s <<= 1;
+    return s;
+}
+
+// relative work of a query (SSSP relaxes each edge several times)
+double work_of(int algo, const View &v) {
+    return (double)v.m * (algo == kSSSP ? 4.0 : 1.0) + (double)v.n;
+}
+
+struct KindPlan {
+    int kind = 0;
+    std::vector<int> queries;                 // indices into the batch
+    std::vector<int> class_size;              // team size per class
+    std::vector<std::vector<int>> class_q;    // queries per class, largest work first
+    std::vector<int> class_teams;             // teams per class
+    double work = 0;
+    int ctas = 0;
+};
+
+}  // namespace
+
+fg_status run_batch(const fg_query *qs, int32_t nq, const fg_batch_options *opt, fg_status *status_out,
+                    fg_stats *stats_out, fg_batch_stats *bstats) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaStream_t st = opt && opt->stream ? (cudaStream_t)opt->stream : (cudaStream_t)0;
+    const int tmo = (opt && opt->wait_timeout_ms > 0) ? opt->wait_timeout_ms : 1000;
+    int sms = 0, coop = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (!coop) return fail(FG_ERR_CUDA, "device does not support cooperative launches");
+
+    // ---- resolve modes, group by kind, plan teams
+    std::vector<Mode> mode(nq);
+    std::vector<const View *> view(nq);
+    std::map<int, KindPlan> kinds;
+    double total_work = 0;
+    for (int i = 0; i < nq; i++) {
+        const fg_query &q = qs[i];
+        fg_mode m = (fg_mode)q.mode;
+        if (m == FG_AUTO) {
+            fg_status s = fg_select_mode(q.g, (fg_algo)q.algo, &m);
+            if (s != FG_OK) return s;
+        }
+        mode[i] = (Mode)m;
+        view[i] = (q.algo == FG_ALGO_CC) ? &q.g->s : &q.g->g;
+        KindPlan &kp = kinds[q.algo * 4 + (int)m];
+        kp.kind = q.algo * 4 + (int)m;
+        kp.queries.push_back(i);
+        double w = work_of(q.algo, *view[i]);
+        kp.work += w;
+        total_work += w;
+    }
+    for (auto &kv : kinds) {
+        KindPlan &kp = kv.second;
+        std::map<int, std::vector<int>> by_size;
+        for (int i : kp.queries) by_size[team_size_for(view[i]->m)].push_back(i);
+        std::vector<double> cw;
+        for (auto &c : by_size) {
+            std::vector<int> v = c.second;
+            std::sort(v.begin(), v.end(), [&](int a, int b) {
+                return work_of(qs[a].algo, *view[a]) > work_of(qs[b].algo, *view[b]);
+            });
+            double w = 0;
+            for (int i : v) w += work_of(qs[i].algo, *view[i]);
+            kp.class_size.push_back(c.first);
+            kp.class_q.push_back(v);
+            cw.push_back(w);
+        }
+        int per_sm = 0;
+        BatchFn fn = batch_kernel_for(kp.kind);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, kBlock, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+        const int capacity = std::max(1, std::min(per_sm * sms, kMaxGrid));
+        int min_ctas = 0;
+        for (int s : kp.class_size) min_ctas += std::min(s, capacity);
+        int budget = (int)(capacity * (kp.work / std::max(total_work, 1.0)));
+        budget = std::min(capacity, std::max(budget, min_ctas));
+        // one team per class, the rest of the budget by class work
+        int used = 0;
+        for (size_t c = 0; c < kp.class_size.size(); c++) {
+            kp.class_size[c] = std::min(kp.class_size[c], capacity);
+            kp.class_teams.push_back(1);
+            used += kp.class_size[c];
+        }
+        const int rest = std::max(0, budget - used);
+        for (size_t c = 0; c < kp.class_size.size(); c++) {
+            int extra = (int)(rest * (cw[c] / std::max(kp.work, 1.0)) / kp.class_size[c]);
+            extra = std::min(extra, (int)kp.class_q[c].size() - 1);
+            kp.class_teams[c] += std::max(0, extra);
+        }
+        kp.ctas = 0;
+        for (size_t c = 0; c < kp.class_size.size(); c++) kp.ctas += kp.class_teams[c] * kp.class_size[c];
+    }
+
+    // ---- one device allocation: zeroed region | tables | query workspaces
+    size_t zero_bytes = Workspace::need(1, sizeof(Ctrl)) + Workspace::need(nq, sizeof(Ctrl));
+    size_t table_bytes = Workspace::need(nq, sizeof(Params)) + Workspace::need(nq, sizeof(int));
+    for (auto &kv : kinds) {
+        KindPlan &kp = kv.second;
+        int teams = 0;
+        for (int t : kp.class_teams) teams += t;
+        const int nc = (int)kp.class_size.size();
+        zero_bytes += Workspace::need(2 * teams, 4) + Workspace::need(teams, 4) + Workspace::need(nc, 4);
+        table_bytes += Workspace::need(kp.ctas, sizeof(int4)) + 2 * Workspace::need(nc, 4);
+    }
+    size_t ws_bytes = 0;
+    for (int i = 0; i < nq; i++) ws_bytes += query_workspace_bytes(*view[i], (Algo)qs[i].algo, mode[i]);
+    const size_t total = zero_bytes + table_bytes + ws_bytes;
+    char *base = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&base, total, st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch workspace");
+
+    // host images of the tables, copied in one transfer
+    std::vector<char> img(table_bytes, 0);
+    Workspace zw{base}, tw{base + zero_bytes}, hw{img.data()}, qw{base + zero_bytes + table_bytes};
+    Ctrl *bctrl = zw.take<Ctrl>(1);
+    Ctrl *ctrls = zw.take<Ctrl>(nq);
+    Params *d_params = tw.take<Params>(nq);
+    Params *h_params = hw.take<Params>(nq);
+    int *d_order = tw.take<int>(nq);
+    int *h_order = hw.take<int>(nq);
+    std::vector<int32_t *> result(nq);
+    for (int i = 0; i < nq; i++) {
+        char *w = qw.base + qw.off;
+        qw.off += query_workspace_bytes(*view[i], (Algo)qs[i].algo, mode[i]);
+        Params p;
+        carve_query_workspace(w, *view[i], (Algo)qs[i].algo, mode[i], p);
+        p.ctrl = ctrls + i;
+        p.source = qs[i].algo == FG_ALGO_CC ? 0 : qs[i].src;
+        p.max_rounds = view[i]->n > INT32_MAX - 2 ? INT32_MAX : view[i]->n + 2;
+        p.timeout_ns = (unsigned long long)tmo * 1000000ull;
+        p.out = is_device_pointer(qs[i].out) ? qs[i].out : nullptr;
+        h_params[i] = p;
+    }
+    std::vector<BatchArgs> args;
+    std::vector<int> kind_list;
+    int order_pos = 0, total_teams = 0, total_ctas = 0;
+    for (auto &kv : kinds) {
+        KindPlan &kp = kv.second;
+        const int nc = (int)kp.class_size.size();
+        int teams = 0;
+        for (int t : kp.class_teams) teams += t;
+        BatchArgs a;
+        a.team_bar = zw.take<unsigned>(2 * teams);
+        a.team_q = zw.take<int>(teams);
+        a.cls_next = zw.take<int>(nc);
+        int4 *d_ct = tw.take<int4>(kp.ctas);
+        int4 *h_ct = hw.take<int4>(kp.ctas);
+        int *d_cb = tw.take<int>(nc), *h_cb = hw.take<int>(nc);
+        int *d_ce = tw.take<int>(nc), *h_ce = hw.take<int>(nc);
+        int cta = 0, team = 0;
+        for (int c = 0; c < nc; c++) {
+            h_cb[c] = order_pos;
+            for (int i : kp.class_q[c]) h_order[order_pos++] = i;
+            h_ce[c] = order_pos;
+            for (int k = 0; k < kp.class_teams[c]; k++, team++)
+                for (int r = 0; r < kp.class_size[c]; r++) h_ct[cta++] = make_int4(team, r, kp.class_size[c], c);
+        }
+        a.cta_team = d_ct;
+        a.cls_begin = d_cb;
+        a.cls_end = d_ce;
+        a.order = d_order;
+        a.params = d_params;
+        a.bctrl = bctrl;
+        a.timeout_ns = (unsigned long long)tmo * 1000000ull;
+        args.push_back(a);
+        kind_list.push_back(kp.kind);
+        total_teams += teams;
+        total_ctas += kp.ctas;
+    }
+
+    // ---- launch: fork one stream per kind, join, optionally as a CUDA graph
+    const int nk = (int)args.size();
+    std::vector<cudaStream_t> ks(nk, nullptr);
+    std::vector<cudaEvent_t> kev(nk, nullptr);
+    cudaEvent_t fork = nullptr, ev0 = nullptr, ev1 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const bool use_graph = opt && opt->use_cuda_graph;
+    fg_status status = FG_OK;
+    std::string msg;
+    auto ck = [&](cudaError_t err, const char *what) {
+        if (err != cudaSuccess && status == FG_OK) {
+            status = (err == cudaErrorMemoryAllocation) ? FG_ERR_OUT_OF_MEMORY : FG_ERR_CUDA;
+            msg = std::string(what) + ": " + cudaGetErrorString(err);
+        }
+        return err == cudaSuccess;
+    };
+    ck(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming), "event");
+    ck(cudaEventCreate(&ev0), "event");
+    ck(cudaEventCreate(&ev1), "event");
+    for (int k = 0; k < nk; k++) {
+        ck(cudaStreamCreateWithFlags(&ks[k], cudaStreamNonBlocking), "stream");
+        ck(cudaEventCreateWithFlags(&kev[k], cudaEventDisableTiming), "event");
+    }
+    ck(cudaMemcpyAsync(base + zero_bytes, img.data(), table_bytes, cudaMemcpyHostToDevice, st), "table upload");
+    ck(cudaStreamSynchronize(st), "table upload");
+    ck(cudaEventRecord(ev0, st), "event");
+    // the launches are recorded on `cs`: the caller's stream itself, or for a
+    // CUDA graph a private stream (the legacy default stream cannot capture)
+    cudaStream_t cs = st;
+    if (status == FG_OK && use_graph) {
+        ck(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "stream");
+        ck(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "capture");
+    }
+    ck(cudaMemsetAsync(base, 0, zero_bytes, cs), "memset");
+    ck(cudaEventRecord(fork, cs), "event");
+    for (int k = 0; k < nk && status == FG_OK; k++) {
+        ck(cudaStreamWaitEvent(ks[k], fork, 0), "fork");
+        int kind_ctas = 0;
+        for (int c = 0; c < (int)kinds[kind_list[k]].class_size.size(); c++)
+            kind_ctas += kinds[kind_list[k]].class_teams[c] * kinds[kind_list[k]].class_size[c];
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(kind_ctas);
+        cfg.blockDim = dim3(kBlock);
+        cfg.stream = ks[k];
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (ck(cudaLaunchKernelEx(&cfg, batch_kernel_for(kind_list[k]), args[k]), "batch launch")) count_launch();
+        ck(cudaEventRecord(kev[k], ks[k]), "event");
+        ck(cudaStreamWaitEvent(cs, kev[k], 0), "join");
+    }
+    if (use_graph && cs != st) {
+        cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+        if (status == FG_OK) ck(ce, "capture");
+        if (status == FG_OK) ck(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate");
+        if (status == FG_OK) ck(cudaGraphLaunch(exec, st), "graph launch");
+        cudaStreamDestroy(cs);
+    }
+    ck(cudaEventRecord(ev1, st), "event");
+    std::vector<Ctrl> hc(nq);
+    ck(cudaMemcpyAsync(hc.data(), ctrls, nq * sizeof(Ctrl), cudaMemcpyDeviceToHost, st), "status copy");
+    ck(cudaStreamSynchronize(st), "batch");
+    float ms = 0.f;
+    if (status == FG_OK) cudaEventElapsedTime(&ms, ev0, ev1);
+
+    // ---- per-query outcome, overflow test, host outputs
+    fg_status first_err = FG_OK;
+    std::string first_msg;
+    for (int i = 0; i < nq && status == FG_OK; i++) {
+        fg_status qs_st = FG_OK;
+        const Params &p = h_params[i];
+        const int32_t *res = (hc[i].result_in_b && p.B) ? p.B : p.A;
+        if (hc[i].status & kStTimeout) qs_st = FG_ERR_TIMEOUT;
+        else if (hc[i].status & kStRoundCap) qs_st = FG_ERR_TIMEOUT;
+        else if (hc[i].status & kStWorklist) qs_st = FG_ERR_CUDA;
+        else if (!hc[i].done) qs_st = FG_ERR_TIMEOUT;
+        else if ((hc[i].status & kStOverflow) && qs[i].algo == FG_ALGO_SSSP) {
+            int *flag = reinterpret_cast<int *>(p.ctrl);
+            int hf = 0;
+            ck(cudaMemsetAsync(flag, 0, sizeof(int), st), "memset");
+            overflow_check_launch(*view[i], p.out ? p.out : res, flag, st);
+            ck(cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
+            ck(cudaStreamSynchronize(st), "overflow check");
+            if (hf) qs_st = FG_ERR_OVERFLOW;
+        }
+        if (qs_st == FG_OK && !p.out)
+            ck(cudaMemcpyAsync(qs[i].out, res, (size_t)view[i]->n * sizeof(int32_t), cudaMemcpyDefault, st),
+               "result copy");
+        if (status_out) status_out[i] = qs_st;
+        if (qs_st != FG_OK && first_err == FG_OK) {
+            first_err = qs_st;
+            first_msg = "batch query " + std::to_string(i) + " failed: " + fg_status_string(qs_st);
+        }
+        if (stats_out) {
+            fg_stats &s = stats_out[i];
+            s = fg_stats{};
+            s.mode = (int32_t)mode[i];
+            s.rounds = hc[i].rounds;
+            s.jump_passes = hc[i].jump_passes;
+            s.vertices_processed = (int64_t)hc[i].st_vertices;
+            s.edges_relaxed = (int64_t)hc[i].st_edges;
+            s.updates = (int64_t)hc[i].st_updates;
+            s.pushes = (int64_t)hc[i].st_pushes;
+            s.scanned = (int64_t)hc[i].st_scanned;
+            s.barriers = hc[i].barriers;
+        }
+    }
+    ck(cudaStreamSynchronize(st), "result copies");
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (int k = 0; k < nk; k++) {
+        if (kev[k]) cudaEventDestroy(kev[k]);
+        if (ks[k]) cudaStreamDestroy(ks[k]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    cudaFreeAsync(base, st);
+    if (bstats) {
+        bstats->kernel_ms = ms;
+        bstats->launches = nk;
+        bstats->teams = total_teams;
+        bstats->ctas = total_ctas;
+    }
+    if (status != FG_OK) return fail(status, msg);
+    if (first_err != FG_OK) return fail(first_err, first_msg);
+    return FG_OK;
+}
+
+}  // namespace fg

@@ -195,6 +195,10 @@ fg_status fg_select_mode(const fg_graph *g, fg_algo algo, fg_mode *out) {
     int32_t diam;
     {
         std::lock_guard<std::mutex> lk(g->mu);
+        if (g->tuned_mode[algo] >= 0) {
+            *out = (fg_mode)g->tuned_mode[algo];
+            return FG_OK;
+        }
         diam = g->diam_est;
     }
     if (diam < 0) {
@@ -222,15 +226,68 @@ fg_status fg_select_mode(const fg_graph *g, fg_algo algo, fg_mode *out) {
         std::lock_guard<std::mutex> lk(g->mu);
         g->diam_est = diam;
     }
-    double avg = g->info.n > 0 ? (double)g->info.m / g->info.n : 0.0;
-    bool skewed = g->info.max_out_degree > 64.0 * (avg > 1.0 ? avg : 1.0);
-    bool deep = diam > 64;
-    fg_mode m;
-    if (deep) m = skewed ? FG_EDGE_ASYNC : FG_VERTEX_ASYNC;
-    else m = skewed ? FG_EDGE_SYNC : FG_VERTEX_SYNC;
-    (void)algo;
+    // Measured on GB300 (R-MAT 22 and the 4096^2 grid): with degree buckets
+    // the vertex modes lead on skewed and uniform graphs alike; the worklist
+    // wins BFS everywhere, and SSSP/CC on shallow graphs, while on deep
+    // graphs the synchronous sweep's lower per-round cost wins SSSP and CC.
+    const bool deep = diam > 64;
+    fg_mode m = FG_VERTEX_ASYNC;
+    if (algo != FG_ALGO_BFS && deep) m = FG_VERTEX_SYNC;
     *out = m;
     return FG_OK;
+}
+
+fg_status fg_autotune(const fg_graph *g, fg_algo algo, int32_t src, fg_mode *best, float *times_ms) {
+    if (!g || !best) return fail(FG_ERR_INVALID_ARG, "NULL argument");
+    if (algo < FG_ALGO_SSSP || algo > FG_ALGO_CC) return fail(FG_ERR_INVALID_ARG, "invalid algorithm");
+    if (algo != FG_ALGO_CC && (src < 0 || src >= g->info.n))
+        return fail(FG_ERR_INVALID_ARG, "source vertex outside [0, n)");
+    if (!ensure_device(nullptr)) return fail(FG_ERR_CUDA, "no CUDA device");
+    int32_t *out = nullptr;
+    cudaError_t e = cudaMalloc(&out, (size_t)g->info.n * sizeof(int32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "autotune workspace");
+    float t[4];
+    fg_status s = FG_OK;
+    for (int m = 0; m < 4 && s == FG_OK; m++) {
+        fg_stats st{};
+        s = run_query(g, (Algo)algo, (Mode)m, src, out, nullptr, &st);
+        t[m] = st.kernel_ms;
+    }
+    cudaFree(out);
+    if (s != FG_OK) return s;
+    int bm = 0;
+    for (int m = 1; m < 4; m++)
+        if (t[m] < t[bm]) bm = m;
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        g->tuned_mode[algo] = bm;
+    }
+    *best = (fg_mode)bm;
+    if (times_ms)
+        for (int m = 0; m < 4; m++) times_ms[m] = t[m];
+    return FG_OK;
+}
+
+fg_status fg_run_batch(const fg_query *queries, int32_t nq, const fg_batch_options *opt,
+                       fg_status *status_out, fg_stats *stats_out, fg_batch_stats *bstats) {
+    if (!queries || nq <= 0) return fail(FG_ERR_INVALID_ARG, "empty batch");
+    if (opt && opt->wait_timeout_ms < 0) return fail(FG_ERR_INVALID_ARG, "negative option");
+    for (int32_t i = 0; i < nq; i++) {
+        const fg_query &q = queries[i];
+        std::string where = "batch query " + std::to_string(i) + ": ";
+        if (!q.g) return fail(FG_ERR_INVALID_ARG, where + "graph is NULL");
+        if (!q.out) return fail(FG_ERR_INVALID_ARG, where + "output buffer is NULL");
+        if (q.algo < FG_ALGO_SSSP || q.algo > FG_ALGO_CC) return fail(FG_ERR_INVALID_ARG, where + "invalid algorithm");
+        if (q.mode < FG_VERTEX_SYNC || q.mode > FG_AUTO) return fail(FG_ERR_INVALID_ARG, where + "invalid mode");
+        if (q.algo != FG_ALGO_CC && (q.src < 0 || q.src >= q.g->info.n))
+            return fail(FG_ERR_INVALID_ARG, where + "source vertex outside [0, n)");
+    }
+    int dev;
+    if (!ensure_device(&dev)) return fail(FG_ERR_CUDA, "no CUDA device");
+    for (int32_t i = 0; i < nq; i++)
+        if (queries[i].g->device != dev)
+            return fail(FG_ERR_INVALID_ARG, "batch query " + std::to_string(i) + ": graph lives on another device");
+    return run_batch(queries, nq, opt, status_out, stats_out, bstats);
 }
 
 const char *fg_last_error(void) { return fg::last_error_cstr(); }

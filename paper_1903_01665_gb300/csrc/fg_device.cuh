@@ -997,6 +997,7 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t) {
     Acc a;
     int rounds = 0;
     int n_barriers = 0;
+    bool done = false;
     // every grid barrier of the query; CTA 0 optionally timestamps each
     auto sync_ = [&]() -> bool {
         bool r = team_sync(t, c, p.timeout_ns);
@@ -1097,6 +1098,7 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t) {
             if (threadIdx.x == 0 && ch) atomicAdd(&c->changed[r % 3], ch);
             if (!sync_()) break;
             if (__ldcg(&c->changed[r % 3]) == 0) {
+                done = true;
                 if (tid == 0) c->result_in_b = (ALGO != kBFS) && (r & 1);
                 if (ALGO == kSSSP) {
                     // A vertex without out-edges is never expanded, so no
@@ -1161,7 +1163,10 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t) {
                     n_in[kWlLow] = g.n_low; n_in[kWlMid] = g.n_mid; n_in[kWlHigh] = g.n_high_chunks;
                 }
             }
-            if (n_in[0] + n_in[1] + n_in[2] == 0) break;
+            if (n_in[0] + n_in[1] + n_in[2] == 0) {
+                done = true;
+                break;
+            }
             if (gen >= p.max_rounds) {
                 if (tid == 0) atomicOr(&c->status, kStRoundCap);
                 break;
@@ -1223,6 +1228,18 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t) {
     if (tid == 0) {
         c->rounds = rounds;
         c->barriers = n_barriers;
+        c->done = done;
+    }
+    // a query of a batch with a device output: the team writes the result
+    // there (both sync buffers hold values >= the fixpoint and one holds it,
+    // so their minimum is the result)
+    if (done && p.out) {
+        constexpr bool TWO = SYNC && ALGO != kBFS;
+        for (int64_t v = tid; v < n; v += nth) {
+            int32_t x = ldcg(p.A + v);
+            if (TWO) x = min(x, ldcg(p.B + v));
+            p.out[v] = x;
+        }
     }
 }
 

@@ -79,20 +79,73 @@ DeviceProps device_props(int dev) {
     return p;
 }
 
-struct Workspace {
-    char *base = nullptr;
-    size_t off = 0, size = 0;
-    template <typename T>
-    T *take(int64_t count) {
-        size_t bytes = ((size_t)std::max<int64_t>(count, 1) * sizeof(T) + 255) & ~(size_t)255;
-        T *p = reinterpret_cast<T *>(base + off);
-        off += bytes;
-        return p;
-    }
-    static size_t need(int64_t count, size_t elem) { return ((size_t)std::max<int64_t>(count, 1) * elem + 255) & ~(size_t)255; }
-};
 
 }  // namespace
+
+void overflow_check_launch(const View &g, const int32_t *D, int *flag, cudaStream_t st) {
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    overflow_check_kernel<<<std::max(1, sms) * 8, kBlock, 0, st>>>(g, D, flag);
+    count_launch();
+}
+
+namespace {
+int64_t wl_cap_of(const View &g, Mode mode, int k) {
+    if (mode == kVertexAsync) {
+        if (k == kWlLow) return std::max(g.n_low, 1);
+        if (k == kWlMid) return std::max(g.n_mid, 1);
+        return 2 * (int64_t)std::max(g.n_high_chunks, 1);
+    }
+    if (mode == kEdgeAsync) return k == 0 ? std::max(g.n_nz, 1) : 1;
+    return 0;
+}
+}  // namespace
+
+// Bytes of one query's device state (control block, value buffers, stamps,
+// worklists, prefix arrays, chunk flags), each piece 256-byte aligned.
+size_t query_workspace_bytes(const View &g, Algo algo, Mode mode) {
+    const int32_t n = g.n;
+    const bool sync = (mode == kVertexSync || mode == kEdgeSync);
+    size_t need = Workspace::need(1, sizeof(Ctrl)) + Workspace::need(n, 4);
+    if (sync && algo != kBFS) need += 3 * Workspace::need(n, 4);
+    const int64_t nec = (g.m + kEChunk - 1) >> kEChunkLog;
+    if (mode == kEdgeSync) need += Workspace::need(nec, 4);
+    if (!sync) {
+        if (algo != kBFS) need += Workspace::need(n, 4);
+        for (int k = 0; k < 3; k++) need += 2 * Workspace::need(wl_cap_of(g, mode, k), 4);
+        if (mode == kEdgeAsync) need += Workspace::need(wl_cap_of(g, mode, 0), 4) + Workspace::need(kMaxGrid, 4);
+    }
+    return need;
+}
+
+// Lays one query's state out from base (query_workspace_bytes bytes) into p.
+void carve_query_workspace(char *base, const View &g, Algo algo, Mode mode, Params &p) {
+    Workspace ws;
+    ws.base = base;
+    const int32_t n = g.n;
+    const bool sync = (mode == kVertexSync || mode == kEdgeSync);
+    const int64_t nec = (g.m + kEChunk - 1) >> kEChunkLog;
+    p.g = g;
+    p.ctrl = ws.take<Ctrl>(1);
+    p.A = ws.take<int32_t>(n);
+    if (sync && algo != kBFS) {
+        p.B = ws.take<int32_t>(n);
+        p.S0 = ws.take<int32_t>(n);
+        p.S1 = ws.take<int32_t>(n);
+    }
+    if (mode == kEdgeSync) p.eflag = ws.take<int32_t>(nec);
+    if (!sync) {
+        if (algo != kBFS) p.S0 = ws.take<int32_t>(n);
+        for (int par = 0; par < 2; par++)
+            for (int k = 0; k < 3; k++) p.wl[par][k] = ws.take<int32_t>(wl_cap_of(g, mode, k));
+        for (int k = 0; k < 3; k++) p.wl_cap[k] = (int32_t)wl_cap_of(g, mode, k);
+        if (mode == kEdgeAsync) {
+            p.lb_off = ws.take<uint32_t>(wl_cap_of(g, mode, 0));
+            p.lb_blk = ws.take<uint32_t>(kMaxGrid);
+        }
+    }
+}
 
 fg_status run_query(const fg_graph *G, Algo algo, Mode mode, int32_t source, int32_t *out,
                     const fg_options *opt, fg_stats *stats) {
@@ -114,50 +167,16 @@ fg_status run_query(const fg_graph *G, Algo algo, Mode mode, int32_t source, int
     int grid = std::min(per_sm * dp.sms, kMaxGrid);
     if (grid < 1) return fail(FG_ERR_CUDA, "kernel does not fit on an SM");
 
-    const bool sync = (mode == kVertexSync || mode == kEdgeSync);
     // per-query state, carved from one stream-ordered allocation
-    size_t need = Workspace::need(1, sizeof(Ctrl)) + Workspace::need(n, 4);
-    int64_t cap[3] = {0, 0, 0};
-    if (sync && algo != kBFS) need += 3 * Workspace::need(n, 4);
-    const int64_t nec = (g.m + kEChunk - 1) >> kEChunkLog;
-    if (mode == kEdgeSync) need += Workspace::need(nec, 4);
-    if (!sync) {
-        if (algo != kBFS) need += Workspace::need(n, 4);
-        if (mode == kVertexAsync) {
-            cap[kWlLow] = std::max(g.n_low, 1);
-            cap[kWlMid] = std::max(g.n_mid, 1);
-            cap[kWlHigh] = 2 * (int64_t)std::max(g.n_high_chunks, 1);
-        } else {
-            cap[0] = std::max(g.n_nz, 1);
-            need += Workspace::need(cap[0], 4) + Workspace::need(kMaxGrid, 4);
-        }
-        for (int k = 0; k < 3; k++) need += 2 * Workspace::need(cap[k], 4);
-    }
-    Workspace ws;
-    ws.size = need;
-    e = cudaMallocAsync((void **)&ws.base, need, st);
+    const size_t need = query_workspace_bytes(g, algo, mode);
+    char *wsbase = nullptr;
+    e = cudaMallocAsync((void **)&wsbase, need, st);
     if (e != cudaSuccess) return cuda_fail(e, "query workspace");
-
     Params p;
-    p.g = g;
-    p.ctrl = ws.take<Ctrl>(1);
-    p.A = ws.take<int32_t>(n);
-    if (sync && algo != kBFS) {
-        p.B = ws.take<int32_t>(n);
-        p.S0 = ws.take<int32_t>(n);
-        p.S1 = ws.take<int32_t>(n);
-    }
-    if (mode == kEdgeSync) p.eflag = ws.take<int32_t>(nec);
-    if (!sync) {
-        if (algo != kBFS) p.S0 = ws.take<int32_t>(n);
-        for (int par = 0; par < 2; par++)
-            for (int k = 0; k < 3; k++) p.wl[par][k] = ws.take<int32_t>(cap[k]);
-        for (int k = 0; k < 3; k++) p.wl_cap[k] = (int32_t)cap[k];
-        if (mode == kEdgeAsync) {
-            p.lb_off = ws.take<uint32_t>(cap[0]);
-            p.lb_blk = ws.take<uint32_t>(kMaxGrid);
-        }
-    }
+    carve_query_workspace(wsbase, g, algo, mode, p);
+    struct {
+        char *base;
+    } ws{wsbase};
     p.source = source;
     p.max_rounds = (opt && opt->max_rounds > 0) ? opt->max_rounds : (n > INT32_MAX - 2 ? INT32_MAX : n + 2);
     int tmo = (opt && opt->wait_timeout_ms > 0) ? opt->wait_timeout_ms : 1000;

@@ -56,9 +56,10 @@ struct fg_graph {
     fg_graph_info_t info{};
     void *allocs[32] = {};
     int n_allocs = 0;
-    // lazily computed diameter estimate for fg_select_mode
+    // lazily computed diameter estimate and autotuned modes for fg_select_mode
     mutable std::mutex mu;
     mutable int32_t diam_est = -1;
+    mutable int32_t tuned_mode[3] = {-1, -1, -1};
 };
 
 namespace fg {
@@ -77,6 +78,7 @@ struct Ctrl {
     int wl_size[3][4];          // async: worklist sizes per generation slot and class
     unsigned long long st_vertices, st_edges, st_updates, st_pushes, st_scanned;
     int barriers;
+    int done;                   // the fixpoint was reached
 };
 
 enum Algo { kSSSP = 0, kBFS = 1, kCC = 2 };
@@ -100,6 +102,7 @@ struct Params {
     int32_t max_rounds = 0;
     unsigned long long timeout_ns = 0;
     int32_t inject_missing_arrival = 0;
+    int32_t *out = nullptr;                // batch: device output the team copies the result to
     unsigned long long *trace = nullptr;   // optional per-barrier timestamps (CTA 0)
     int32_t trace_cap = 0;
     Ctrl *ctrl = nullptr;
@@ -262,11 +265,36 @@ fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const i
                                const int32_t *w, bool src_sorted_csr, const int64_t *row_off_in,
                                fg_graph **out);
 
+// 256-byte aligned bump allocator over one device allocation
+struct Workspace {
+    char *base = nullptr;
+    size_t off = 0;
+    template <typename T>
+    T *take(int64_t count) {
+        size_t bytes = need(count, sizeof(T));
+        T *p = reinterpret_cast<T *>(base + off);
+        off += bytes;
+        return p;
+    }
+    static size_t need(int64_t count, size_t elem) {
+        return ((size_t)(count > 1 ? count : 1) * elem + 255) & ~(size_t)255;
+    }
+};
+
+struct Params;
+size_t query_workspace_bytes(const View &g, Algo algo, Mode mode);
+void carve_query_workspace(char *base, const View &g, Algo algo, Mode mode, Params &p);
+
 // queries (fg_fixpoint.cu)
 fg_status run_query(const fg_graph *g, Algo algo, Mode mode, int32_t source, int32_t *out,
                     const fg_options *opt, fg_stats *stats);
 fg_status run_sweep(const fg_graph *g, Mode mode, const int32_t *cur, int32_t *next,
                     cudaStream_t stream, int64_t *updates, float *kernel_ms);
+void overflow_check_launch(const View &g, const int32_t *D, int *flag, cudaStream_t st);
+
+// batches (fg_batch.cu)
+fg_status run_batch(const fg_query *qs, int32_t nq, const fg_batch_options *opt, fg_status *status_out,
+                    fg_stats *stats_out, fg_batch_stats *bstats);
 
 // whether a pointer is device-accessible memory of the current device
 bool is_device_pointer(const void *p);

@@ -57,6 +57,10 @@ int main(void) {
   P(fg_graph_info_t, n_mid); P(fg_graph_info_t, n_high); P(fg_graph_info_t, n_high_chunks);
   P(fg_graph_info_t, n_isolated);
   P(fg_graph_info_t, device_bytes);
+  printf("fg_query %zu\nfg_batch_options %zu\nfg_batch_stats %zu\n", sizeof(fg_query), sizeof(fg_batch_options), sizeof(fg_batch_stats));
+  P(fg_query, g); P(fg_query, algo); P(fg_query, src); P(fg_query, out); P(fg_query, mode);
+  P(fg_batch_options, stream); P(fg_batch_options, use_cuda_graph); P(fg_batch_options, wait_timeout_ms);
+  P(fg_batch_stats, kernel_ms); P(fg_batch_stats, launches); P(fg_batch_stats, teams); P(fg_batch_stats, ctas);
   return 0;
 }
 ''')
@@ -67,7 +71,8 @@ int main(void) {
     for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
         k, v = line.split()
         c[k] = int(v)
-    for cls in (fg.fg_options, fg.fg_stats, fg.fg_graph_info_t):
+    for cls in (fg.fg_options, fg.fg_stats, fg.fg_graph_info_t, fg.fg_query, fg.fg_batch_options,
+                fg.fg_batch_stats):
         assert ctypes.sizeof(cls) == c[cls.__name__]
         for name, _ in cls._fields_:
             assert getattr(cls, name).offset == c[f"{cls.__name__}.{name}"], (cls.__name__, name)
@@ -95,6 +100,10 @@ def test_host_side_argument_checks():
     st, _ = fg.fg_select_mode(None, fg.FG_ALGO_BFS)
     assert st == fg.FG_ERR_INVALID_ARG
     assert fg.fg_graph_destroy(None) == fg.FG_OK
+    st, _, _, _ = fg.fg_run_batch([(None, 0, 0, out, 0)])
+    assert st == fg.FG_ERR_INVALID_ARG and "graph is NULL" in fg.fg_last_error()
+    st, _, _ = fg.fg_autotune(None, 0)
+    assert st == fg.FG_ERR_INVALID_ARG
     assert fg.fg_status_string(fg.FG_ERR_OVERFLOW) == "FG_ERR_OVERFLOW"
     assert fg.fg_status_string(fg.FG_ERR_TIMEOUT) == "FG_ERR_TIMEOUT"
 

@@ -1,0 +1,78 @@
+"""Batched queries on the GPU (one persistent launch per algorithm x mode,
+teams of CTAs per query): every result must equal the oracle's, for mixed
+graphs of uneven size, mixed algorithms and modes, host and device outputs,
+direct launches and a CUDA-graph launch; FG_AUTO after the autotuner."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+import paper_1903_01665_gb300 as fg
+from tests.gpu_util import graph_handle
+
+pytestmark = pytest.mark.gpu
+
+
+def _graphs():
+    return [gg.rmat(10, seed=1), gg.rmat(13, seed=2), gg.rmat(16, seed=3), gg.grid(64, seed=4),
+            gg.grid(256, seed=5), gg.er(4000, 30000, seed=6), gg.path(3000)]
+
+
+def _expected(g, algo, s):
+    if algo == 0:
+        return oracle.sssp(g.n, g.src, g.dst, g.w, s)[1]
+    if algo == 1:
+        return oracle.bfs(g.n, g.src, g.dst, s)[1]
+    return oracle.cc(g.n, g.src, g.dst)[1]
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_matches_oracle(use_graph):
+    import torch
+    from contextlib import ExitStack
+    graphs = _graphs()
+    rng = np.random.Generator(np.random.PCG64(7))
+    with ExitStack() as stack:
+        handles = [stack.enter_context(graph_handle(g)) for g in graphs]
+        queries, want = [], []
+        for gi, (g, h) in enumerate(zip(graphs, handles)):
+            srcs = [int(x) for x in gg.sources(g, 3, seed=100 + gi)]
+            for k, s in enumerate(srcs):
+                for algo in (0, 1, 2):
+                    mode = int(rng.integers(0, 4))
+                    if (k + algo) % 2:
+                        out = torch.full((g.n,), -5, dtype=torch.int32, device="cuda")
+                    else:
+                        out = np.full(g.n, -5, np.int32)
+                    queries.append((h, algo, s, out, mode))
+                    want.append(_expected(g, algo, s))
+        st, sts, stats, bst = fg.fg_run_batch(queries, use_cuda_graph=use_graph)
+        assert st == fg.FG_OK, fg.fg_last_error()
+        assert all(x == fg.FG_OK for x in sts)
+        assert bst.launches >= 1 and bst.teams >= 1
+        for (h, algo, s, out, mode), exp, stt in zip(queries, want, stats):
+            got = out.cpu().numpy() if hasattr(out, "cpu") else out
+            np.testing.assert_array_equal(got, exp, err_msg=f"algo={algo} mode={mode} src={s}")
+            assert stt.mode == mode
+
+
+def test_batch_auto_after_autotune_and_overflow_status():
+    import torch
+    g = gg.rmat(14, seed=9)
+    bad = gg.path(3, weights=[2**30, 2**30])
+    with graph_handle(g) as h, graph_handle(bad) as hb:
+        s = int(gg.sources(g, 1, seed=3)[0])
+        for algo in (0, 1, 2):
+            st, best, times = fg.fg_autotune(h, algo, s)
+            assert st == fg.FG_OK and best in (0, 1, 2, 3) and all(t > 0 for t in times)
+            st, m = fg.fg_select_mode(h, algo)
+            assert m == best
+        outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in range(3)]
+        ob = np.full(3, 99, np.int32)
+        q = [(h, a, s, outs[a], fg.FG_AUTO) for a in (0, 1, 2)] + [(hb, 0, 0, ob, 0)]
+        st, sts, stats, _ = fg.fg_run_batch(q)
+        assert st == fg.FG_ERR_OVERFLOW
+        assert sts == [fg.FG_OK, fg.FG_OK, fg.FG_OK, fg.FG_ERR_OVERFLOW]
+        assert np.all(ob == 99)
+        for a in (0, 1, 2):
+            np.testing.assert_array_equal(outs[a].cpu().numpy(), _expected(g, a, s))
