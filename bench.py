@@ -239,6 +239,69 @@ class Runner:
         return units
 
 
+def run_batched(device, reps: int = 3) -> dict:
+    """The batched workload: 512 SSSP/BFS queries (8 seeded sources per
+    graph, alternating) over 64 resident graphs of uneven size (R-MAT scales
+    10-20, grids 256^2-2048^2, weights U[1,1000]), FG_AUTO after the
+    autotuner, run one query at a time with the plain per-query kernels and
+    as one batched CUDA-graph launch; every output compared bit for bit."""
+    import torch
+    import paper_1903_01665_gb300 as fg
+    graphs = gg.batched_graphs()
+    queries = gg.batched_queries(graphs)
+    handles, degs = [], []
+    try:
+        for g in graphs:
+            st, h = fg.fg_graph_create_coo(g.n, torch.from_numpy(g.src).to(device),
+                                           torch.from_numpy(g.dst).to(device), torch.from_numpy(g.w).to(device))
+            fg.check(st)
+            handles.append(h)
+            degs.append(torch.from_numpy(np.bincount(g.src, minlength=g.n).astype(np.int64)).to(device))
+        tune = {}
+        for gi, algo, s in queries:
+            if (gi, algo) not in tune:
+                st, best, _ = fg.fg_autotune(handles[gi], algo, s)
+                fg.check(st)
+                tune[(gi, algo)] = best
+        outs1 = [torch.empty(graphs[gi].n, dtype=torch.int32, device=device) for gi, _, _ in queries]
+        outs2 = [torch.empty(graphs[gi].n, dtype=torch.int32, device=device) for gi, _, _ in queries]
+        batch = [(handles[gi], algo, s, outs2[i], fg.FG_AUTO) for i, (gi, algo, s) in enumerate(queries)]
+        t_one, t_batch = [], []
+        for _ in range(reps + 1):          # the first repetition is a warm-up
+            torch.cuda.synchronize(device)
+            t0 = time.perf_counter()
+            for i, (gi, algo, s) in enumerate(queries):
+                st, _ = fg.fg_run(handles[gi], algo, s, outs1[i], fg.FG_AUTO)
+                fg.check(st)
+            torch.cuda.synchronize(device)
+            t_one.append(time.perf_counter() - t0)
+            t0 = time.perf_counter()
+            st, sts, _, bst = fg.fg_run_batch(batch, use_cuda_graph=True)
+            fg.check(st)
+            torch.cuda.synchronize(device)
+            t_batch.append(time.perf_counter() - t0)
+        exact = all(torch.equal(a, b) for a, b in zip(outs1, outs2))
+        edges = 0
+        for i, (gi, algo, s) in enumerate(queries):
+            edges += int(degs[gi][outs1[i] != fg.FG_INF].sum().item())
+        one = statistics.median(t_one[1:])
+        bat = statistics.median(t_batch[1:])
+        modes = {}
+        for (gi, algo), m in tune.items():
+            key = f"{ALGO_NAMES[algo]}/{MODE_NAMES[m]}"
+            modes[key] = modes.get(key, 0) + 1
+        return {"queries": len(queries), "graphs": len(graphs),
+                "one_at_a_time_qps": round(len(queries) / one, 1), "batched_qps": round(len(queries) / bat, 1),
+                "speedup": round(one / bat, 3), "one_at_a_time_gteps": round(edges / one / 1e9, 3),
+                "batched_gteps": round(edges / bat / 1e9, 3), "bit_exact": exact,
+                "batch_kernel_ms": round(bst.kernel_ms, 3), "launches": bst.launches, "teams": bst.teams,
+                "ctas": bst.ctas, "autotuned_modes": modes,
+                "timing": "wall clock around each run, median of %d, after one warm-up" % reps}
+    finally:
+        for h in handles:
+            fg.fg_graph_destroy(h)
+
+
 def dist_setup(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -353,18 +416,24 @@ def run_ours(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample(r.g, r.srcs, r.deg, args.workload)
+    desc, nqueries = r.desc, len(r.queries)
+    batched = None
+    if not args.no_batched:
+        del r
+        torch.cuda.empty_cache()
+        batched = run_batched(device)
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
                 "data": "synthetic (seeded generators in graphgen/)",
-                "config": {"workload": r.desc, "queries_per_step": len(r.queries),
+                "config": {"workload": desc, "queries_per_step": nqueries,
                            "teps_edges_per_step": units // max(args.steps, 1),
                            "l2": "inputs larger than L2 (graph ~1.9-2.2 GB built per step)",
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "per_kernel": per_mode}
+                "clocks": clk, "per_kernel": per_mode, "batched": batched}
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
@@ -472,6 +541,7 @@ def main():
     ap.add_argument("--workload", default="rmat22", choices=["rmat22", "grid4096", "er16k"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload comparison")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

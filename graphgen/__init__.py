@@ -250,3 +250,30 @@ def hub(n: int, hub_degree: int, extra_m: int, seed: int = 5, wlo: int = 1, whi:
     src = np.concatenate([hs, es]); dst = np.concatenate([hd, ed])
     w = rng.integers(wlo, whi + 1, src.size)
     return Graph(n, src, dst, w, f"hub-{n}-{hub_degree}")
+
+
+# ---- the batched workload: 64 resident graphs of uneven size, 512 queries
+
+SEED_BATCH = 0x1903_0166_5005
+
+
+def batched_graphs(seed: int = SEED_BATCH):
+    """32 R-MAT graphs of scale 10 + (i mod 11) and 32 grids of side
+    256 * 2^(i mod 4) (2 % deletions, 0.1 % shortcuts), weights U[1,1000]."""
+    out = []
+    for i in range(32):
+        out.append(rmat(10 + (i % 11), seed=seed + i, whi=1000))
+    for i in range(32):
+        out.append(grid(256 << (i % 4), seed=seed + 100 + i, whi=1000))
+    return out
+
+
+def batched_queries(graphs, per_graph: int = 8, seed: int = SEED_BATCH):
+    """per_graph seeded sources per graph, alternating SSSP (0) and BFS (1):
+    a list of (graph index, algorithm, source)."""
+    q = []
+    for gi, g in enumerate(graphs):
+        srcs = sources(g, per_graph, seed=seed + 1000 + gi)
+        for k, s in enumerate(srcs):
+            q.append((gi, k % 2, int(s)))
+    return q
