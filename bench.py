@@ -302,6 +302,84 @@ def run_batched(device, reps: int = 3) -> dict:
             fg.fg_graph_destroy(h)
 
 
+def run_serving(device, full: bool = False, rates=(100, 1000, 10000), n_req: int = 1000,
+                seed: int = 0x5E57) -> dict:
+    """Poisson arrivals of SSSP/BFS/CC requests (40/40/20, uniform over the
+    resident graphs, seeded sources) served (a) by the continuous-batching
+    server and (b) one request at a time with the plain kernels; p50/p99
+    latency (submission to completion) and completed requests per second."""
+    import torch
+    import paper_1903_01665_gb300 as fg
+    if full:
+        graphs = [gg.rmat(24), gg.rmat(25), gg.rmat(26), gg.grid(8192, whi=1000)]
+    else:
+        graphs = [gg.rmat(20), gg.rmat(21), gg.rmat(22), gg.grid(2048, whi=1000)]
+    handles = []
+    try:
+        device_bytes = 0
+        for g in graphs:
+            st, h = fg.fg_graph_create_coo(g.n, torch.from_numpy(g.src).to(device),
+                                           torch.from_numpy(g.dst).to(device), torch.from_numpy(g.w).to(device))
+            fg.check(st)
+            handles.append(h)
+            device_bytes += fg.fg_graph_info(h)[1].device_bytes
+        srcs = [gg.sources(g, 64, seed=seed + i) for i, g in enumerate(graphs)]
+        for gi, h in enumerate(handles):
+            for algo in (0, 1, 2):
+                fg.check(fg.fg_autotune(h, algo, int(srcs[gi][0]))[0])
+        # output buffers: one per request (recycled round-robin on the large set)
+        ring = 16 if full else n_req
+        outs = [[torch.empty(g.n, dtype=torch.int32, device=device) for _ in range(min(ring, n_req))]
+                for g in graphs]
+        result = {"resident_graphs": [f"{g.name} ({g.n} V, {g.m} E)" for g in graphs],
+                  "resident_device_gb": round(device_bytes / 1e9, 2), "requests_per_rate": n_req,
+                  "mix": "40% SSSP / 40% BFS / 20% CC, uniform over graphs, FG_AUTO after the autotuner",
+                  "rates": []}
+        for rate in rates:
+            rng = np.random.Generator(np.random.PCG64(seed + int(rate)))
+            gaps = rng.exponential(1.0 / rate, n_req)
+            arrive = np.cumsum(gaps) - gaps[0]
+            gis = rng.integers(0, len(graphs), n_req)
+            u = rng.random(n_req)
+            algos = np.where(u < 0.4, 0, np.where(u < 0.8, 1, 2))
+            pick = rng.integers(0, 64, n_req)
+            row = {"rate_per_s": rate}
+            for kind in ("batched", "one_at_a_time"):
+                if kind == "batched":
+                    st, srv = fg.fg_server_create(hbm_budget_bytes=16 << 30, max_inflight=4, max_wave=64)
+                else:
+                    st, srv = fg.fg_server_create(one_at_a_time=True)
+                fg.check(st)
+                counters = [0] * len(graphs)
+                torch.cuda.synchronize(device)
+                t0 = time.perf_counter()
+                for i in range(n_req):
+                    while time.perf_counter() - t0 < arrive[i]:
+                        pass
+                    gi = int(gis[i])
+                    out = outs[gi][counters[gi] % len(outs[gi])]
+                    counters[gi] += 1
+                    st, _ = fg.fg_server_submit(srv, handles[gi], int(algos[i]), int(srcs[gi][pick[i]]), out,
+                                                fg.FG_AUTO)
+                    fg.check(st)
+                fg.check(fg.fg_server_drain(srv, 0))
+                span = time.perf_counter() - t0
+                comps = fg.fg_server_poll(srv, cap=n_req + 16)
+                fg.check(fg.fg_server_destroy(srv))
+                lat = np.array([c[3] for c in comps])
+                ok = all(c[1] == fg.FG_OK for c in comps)
+                row[kind] = {"p50_ms": round(float(np.percentile(lat, 50)), 3),
+                             "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                             "mean_ms": round(float(lat.mean()), 3),
+                             "completed_per_s": round(len(comps) / span, 1), "all_ok": ok,
+                             "mean_wave": round(float(np.mean([c[2] for c in comps])), 2)}
+            result["rates"].append(row)
+        return result
+    finally:
+        for h in handles:
+            fg.fg_graph_destroy(h)
+
+
 def dist_setup(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -417,11 +495,13 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample(r.g, r.srcs, r.deg, args.workload)
     desc, nqueries = r.desc, len(r.queries)
-    batched = None
+    batched = serving = None
+    del r
+    torch.cuda.empty_cache()
     if not args.no_batched:
-        del r
-        torch.cuda.empty_cache()
         batched = run_batched(device)
+    if not args.no_serving:
+        serving = run_serving(device, full=args.serving_full, n_req=args.serving_requests)
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": ws,
@@ -433,7 +513,7 @@ def run_ours(args):
                            "l2": "inputs larger than L2 (graph ~1.9-2.2 GB built per step)",
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "per_kernel": per_mode, "batched": batched}
+                "clocks": clk, "per_kernel": per_mode, "batched": batched, "serving": serving}
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
@@ -542,6 +622,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload comparison")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving comparison")
+    ap.add_argument("--serving-full", action="store_true",
+                    help="serve the R-MAT 24-26 + 8192^2 grid resident set (~60 GB) instead of the reduced one")
+    ap.add_argument("--serving-requests", type=int, default=1000)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

@@ -267,6 +267,51 @@ fg_status fg_run_batch(const fg_query *queries, int32_t nq, const fg_batch_optio
                        fg_status *status_out, fg_stats *stats_out, fg_batch_stats *bstats);
 
 /*
+ * Query server with continuous batching (no paper counterpart beyond the
+ * independent-kernel overlap of Sec. 3.2; this is the serving loop around
+ * the batched path).  Requests are queued by fg_server_submit from any host
+ * thread; a native worker admits them in waves -- whenever one of
+ * max_inflight wave slots is free and the device memory of the in-flight
+ * queries' state stays within hbm_budget_bytes, up to max_wave requests from
+ * the head of the queue are launched together on the slot's stream -- so
+ * waves overlap on the device and new requests start as soon as a slot and
+ * memory free up.  one_at_a_time = 1 serves the queue strictly in order, one
+ * request at a time, with the plain per-query kernel (the baseline).
+ * A request's work is ordered after all work enqueued on the legacy default
+ * stream before it was submitted (so outputs prepared there are safe); it
+ * runs on the server's own streams otherwise.  Graphs must stay alive and
+ * outputs untouched until their requests complete; host outputs should be
+ * pinned memory (pageable memory makes the worker wait on each copy).  A
+ * failed request's output is unspecified.
+ */
+typedef struct fg_server fg_server;
+
+typedef struct {
+    int64_t hbm_budget_bytes;   /* in-flight query state limit; 0 = 8 GiB */
+    int32_t max_inflight;       /* concurrent waves; 0 = 4 */
+    int32_t max_wave;           /* requests per wave at most; 0 = 64 */
+    int32_t one_at_a_time;      /* nonzero: the one-query-at-a-time baseline */
+    int32_t wait_timeout_ms;    /* bound on any device-side wait; 0 = 1000 ms */
+} fg_server_options;
+
+typedef struct {
+    uint64_t ticket;            /* as returned by fg_server_submit */
+    int32_t status;             /* fg_status of the request */
+    int32_t wave_size;          /* requests in the wave it ran in */
+    double latency_ms;          /* submission to completion */
+} fg_completion;
+
+fg_status fg_server_create(const fg_server_options *opt, fg_server **out);
+/* Queues one request (FG_AUTO is resolved here); *ticket identifies it. */
+fg_status fg_server_submit(fg_server *s, const fg_query *q, uint64_t *ticket);
+/* Moves up to cap completions (any order) into out; returns how many. */
+int32_t fg_server_poll(fg_server *s, fg_completion *out, int32_t cap);
+/* Waits until every submitted request has completed (timeout_ms 0 = no limit). */
+fg_status fg_server_drain(fg_server *s, int32_t timeout_ms);
+/* Serves what is queued, stops the worker and frees the server. */
+fg_status fg_server_destroy(fg_server *s);
+
+/*
  * Autotuner: times the four modes on this graph (one query each from src,
  * ignored for CC), writes their device times in ms to times_ms[4] (may be
  * NULL) and the fastest mode to *best, and caches it on the handle:

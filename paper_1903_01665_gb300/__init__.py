@@ -88,6 +88,17 @@ class fg_batch_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class fg_server_options(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
+                ("max_wave", ctypes.c_int32), ("one_at_a_time", ctypes.c_int32),
+                ("wait_timeout_ms", ctypes.c_int32)]
+
+
+class fg_completion(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("wave_size", ctypes.c_int32),
+                ("latency_ms", ctypes.c_double)]
+
+
 _lib = None
 _VP = ctypes.c_void_p
 _SIGNATURES = {
@@ -110,6 +121,11 @@ _SIGNATURES = {
                                     ctypes.POINTER(fg_batch_stats)]),
     "fg_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_float)]),
+    "fg_server_create": (ctypes.c_int, [ctypes.POINTER(fg_server_options), ctypes.POINTER(_VP)]),
+    "fg_server_submit": (ctypes.c_int, [_VP, ctypes.POINTER(fg_query), ctypes.POINTER(ctypes.c_uint64)]),
+    "fg_server_poll": (ctypes.c_int32, [_VP, ctypes.POINTER(fg_completion), ctypes.c_int32]),
+    "fg_server_drain": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "fg_server_destroy": (ctypes.c_int, [_VP]),
     "fg_kernel_launches": (ctypes.c_uint64, []),
     "fg_last_error": (ctypes.c_char_p, []),
     "fg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -272,6 +288,39 @@ def fg_autotune(g, algo, src=0):
     times = (ctypes.c_float * 4)()
     st = load().fg_autotune(g, int(algo), int(src), ctypes.byref(best), times)
     return st, best.value, list(times)
+
+
+def fg_server_create(hbm_budget_bytes=0, max_inflight=0, max_wave=0, one_at_a_time=False, wait_timeout_ms=0):
+    """Returns (status, server handle)."""
+    o = fg_server_options(int(hbm_budget_bytes), int(max_inflight), int(max_wave), 1 if one_at_a_time else 0,
+                          int(wait_timeout_ms))
+    h = _VP()
+    st = load().fg_server_create(ctypes.byref(o), ctypes.byref(h))
+    return st, (h.value if st == FG_OK else None)
+
+
+def fg_server_submit(server, g, algo, src, out, mode=FG_AUTO):
+    """Returns (status, ticket).  out must stay alive until the request completes."""
+    _check_dtype(out, "int32")
+    q = fg_query(g, int(algo), int(src), _ptr(out), int(mode))
+    t = ctypes.c_uint64(0)
+    st = load().fg_server_submit(server, ctypes.byref(q), ctypes.byref(t))
+    return st, t.value
+
+
+def fg_server_poll(server, cap=4096):
+    """Returns a list of completions (ticket, status, wave_size, latency_ms)."""
+    buf = (fg_completion * cap)()
+    n = load().fg_server_poll(server, buf, cap)
+    return [(c.ticket, c.status, c.wave_size, c.latency_ms) for c in buf[:n]]
+
+
+def fg_server_drain(server, timeout_ms=0):
+    return load().fg_server_drain(server, int(timeout_ms))
+
+
+def fg_server_destroy(server):
+    return load().fg_server_destroy(server)
 
 
 FG_NOALLOC_MAX_VERTICES = 1048576

@@ -91,11 +91,19 @@ struct KindPlan {
 
 }  // namespace
 
-fg_status run_batch(const fg_query *qs, int32_t nq, const fg_batch_options *opt, fg_status *status_out,
-                    fg_stats *stats_out, fg_batch_stats *bstats) {
+// Plans, allocates and enqueues a batch on opt->stream; nothing waits.  The
+// results reach device outputs directly; host outputs go to device staging
+// and, if enqueue_host_copies, are copied back on the stream (their contents
+// are then unspecified for a failed query).  cta_fraction scales the CTA
+// budget so that several batches can be resident at once.
+fg_status batch_launch(const fg_query *qs, int32_t nq, const fg_batch_options *opt, double cta_fraction,
+                       bool enqueue_host_copies, Ctrl *h_ctrls_pinned, BatchJob &job) {
+    job.nq = nq;
+    job.qs.assign(qs, qs + nq);
     int dev = 0;
     cudaGetDevice(&dev);
     cudaStream_t st = opt && opt->stream ? (cudaStream_t)opt->stream : (cudaStream_t)0;
+    job.st = st;
     const int tmo = (opt && opt->wait_timeout_ms > 0) ? opt->wait_timeout_ms : 1000;
     int sms = 0, coop = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -103,8 +111,10 @@ fg_status run_batch(const fg_query *qs, int32_t nq, const fg_batch_options *opt,
     if (!coop) return fail(FG_ERR_CUDA, "device does not support cooperative launches");
 
     // ---- resolve modes, group by kind, plan teams
-    std::vector<Mode> mode(nq);
-    std::vector<const View *> view(nq);
+    std::vector<Mode> &mode = job.mode;
+    std::vector<const View *> &view = job.view;
+    mode.resize(nq);
+    view.resize(nq);
     std::map<int, KindPlan> kinds;
     double total_work = 0;
     for (int i = 0; i < nq; i++) {
@@ -126,7 +136,16 @@ fg_status run_batch(const fg_query *qs, int32_t nq, const fg_batch_options *opt,
     for (auto &kv : kinds) {
         KindPlan &kp = kv.second;
         std::map<int, std::vector<int>> by_size;
-        for (int i : kp.queries) by_size[team_size_for(view[i]->m)].push_back(i);
+        // a kind with few queries (at most 8) gives each a larger team (a lone
+        // query the whole budget); otherwise the size follows its edge count
+        int per_sm0 = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm0, (const void *)batch_kernel_for(kp.kind), kBlock, 0);
+        const int cap0 = std::max(1, (int)(std::max(1, std::min(per_sm0 * sms, kMaxGrid)) * cta_fraction *
+                                           std::max(kp.work / std::max(total_work, 1.0), 0.0)));
+        int share = 1;
+        if (kp.queries.size() <= 8)
+            while (share * 2 <= cap0 / (int)kp.queries.size()) share *= 2;
+        for (int i : kp.queries) by_size[std::max(team_size_for(view[i]->m), share)].push_back(i);
         std::vector<double> cw;
         for (auto &c : by_size) {
             std::vector<int> v = c.second;
@@ -143,7 +162,8 @@ fg_status run_batch(const fg_query *qs, int32_t nq, const fg_batch_options *opt,
         BatchFn fn = batch_kernel_for(kp.kind);
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, kBlock, 0);
         if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
-        const int capacity = std::max(1, std::min(per_sm * sms, kMaxGrid));
+        int capacity = std::max(1, std::min(per_sm * sms, kMaxGrid));
+        capacity = std::max(1, (int)(capacity * cta_fraction));
         int min_ctas = 0;
         for (int s : kp.class_size) min_ctas += std::min(s, capacity);
         int budget = (int)(capacity * (kp.work / std::max(total_work, 1.0)));
@@ -165,7 +185,7 @@ fg_status run_batch(const fg_query *qs, int32_t nq, const fg_batch_options *opt,
         for (size_t c = 0; c < kp.class_size.size(); c++) kp.ctas += kp.class_teams[c] * kp.class_size[c];
     }
 
-    // ---- one device allocation: zeroed region | tables | query workspaces
+    // ---- one device allocation: zeroed region | tables | query workspaces | staging
     size_t zero_bytes = Workspace::need(1, sizeof(Ctrl)) + Workspace::need(nq, sizeof(Ctrl));
     size_t table_bytes = Workspace::need(nq, sizeof(Params)) + Workspace::need(nq, sizeof(int));
     for (auto &kv : kinds) {
@@ -176,38 +196,54 @@ fg_status run_batch(const fg_query *qs, int32_t nq, const fg_batch_options *opt,
         zero_bytes += Workspace::need(2 * teams, 4) + Workspace::need(teams, 4) + Workspace::need(nc, 4);
         table_bytes += Workspace::need(kp.ctas, sizeof(int4)) + 2 * Workspace::need(nc, 4);
     }
+    std::vector<bool> dev_out(nq);
     size_t ws_bytes = 0;
-    for (int i = 0; i < nq; i++) ws_bytes += query_workspace_bytes(*view[i], (Algo)qs[i].algo, mode[i]);
+    for (int i = 0; i < nq; i++) {
+        ws_bytes += query_workspace_bytes(*view[i], (Algo)qs[i].algo, mode[i]);
+        dev_out[i] = is_device_pointer(qs[i].out);
+        if (!dev_out[i]) ws_bytes += Workspace::need(view[i]->n, 4);
+    }
     const size_t total = zero_bytes + table_bytes + ws_bytes;
-    char *base = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&base, total, st);
-    if (e != cudaSuccess) return cuda_fail(e, "batch workspace");
+    job.device_bytes = total;
+    cudaError_t e = cudaMallocAsync((void **)&job.base, total, st);
+    if (e != cudaSuccess) {
+        job.base = nullptr;
+        return cuda_fail(e, "batch workspace");
+    }
+    char *base = job.base;
 
-    // host images of the tables, copied in one transfer
+    // host image of the tables, copied in one transfer
     std::vector<char> img(table_bytes, 0);
     Workspace zw{base}, tw{base + zero_bytes}, hw{img.data()}, qw{base + zero_bytes + table_bytes};
     Ctrl *bctrl = zw.take<Ctrl>(1);
-    Ctrl *ctrls = zw.take<Ctrl>(nq);
+    job.d_ctrls = zw.take<Ctrl>(nq);
     Params *d_params = tw.take<Params>(nq);
     Params *h_params = hw.take<Params>(nq);
     int *d_order = tw.take<int>(nq);
     int *h_order = hw.take<int>(nq);
-    std::vector<int32_t *> result(nq);
+    job.staging.assign(nq, nullptr);
     for (int i = 0; i < nq; i++) {
         char *w = qw.base + qw.off;
         qw.off += query_workspace_bytes(*view[i], (Algo)qs[i].algo, mode[i]);
         Params p;
         carve_query_workspace(w, *view[i], (Algo)qs[i].algo, mode[i], p);
-        p.ctrl = ctrls + i;
+        p.ctrl = job.d_ctrls + i;
         p.source = qs[i].algo == FG_ALGO_CC ? 0 : qs[i].src;
         p.max_rounds = view[i]->n > INT32_MAX - 2 ? INT32_MAX : view[i]->n + 2;
         p.timeout_ns = (unsigned long long)tmo * 1000000ull;
-        p.out = is_device_pointer(qs[i].out) ? qs[i].out : nullptr;
+        if (dev_out[i]) {
+            p.out = qs[i].out;
+        } else {
+            job.staging[i] = qw.take<int32_t>(view[i]->n);
+            p.out = job.staging[i];
+        }
         h_params[i] = p;
     }
+    job.params.assign(h_params, h_params + nq);
     std::vector<BatchArgs> args;
-    std::vector<int> kind_list;
-    int order_pos = 0, total_teams = 0, total_ctas = 0;
+    std::vector<int> kind_ctas;
+    std::vector<BatchFn> kind_fn;
+    int order_pos = 0;
     for (auto &kv : kinds) {
         KindPlan &kp = kv.second;
         const int nc = (int)kp.class_size.size();
@@ -237,102 +273,122 @@ fg_status run_batch(const fg_query *qs, int32_t nq, const fg_batch_options *opt,
         a.bctrl = bctrl;
         a.timeout_ns = (unsigned long long)tmo * 1000000ull;
         args.push_back(a);
-        kind_list.push_back(kp.kind);
-        total_teams += teams;
-        total_ctas += kp.ctas;
+        kind_ctas.push_back(kp.ctas);
+        kind_fn.push_back(batch_kernel_for(kp.kind));
+        job.teams += teams;
+        job.ctas += kp.ctas;
     }
 
-    // ---- launch: fork one stream per kind, join, optionally as a CUDA graph
+    // ---- enqueue: fork one stream per kind, join, optionally as a CUDA graph
     const int nk = (int)args.size();
-    std::vector<cudaStream_t> ks(nk, nullptr);
-    std::vector<cudaEvent_t> kev(nk, nullptr);
-    cudaEvent_t fork = nullptr, ev0 = nullptr, ev1 = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    job.launches = nk;
+    job.ks.assign(nk, nullptr);
+    job.kev.assign(nk, nullptr);
     const bool use_graph = opt && opt->use_cuda_graph;
-    fg_status status = FG_OK;
-    std::string msg;
     auto ck = [&](cudaError_t err, const char *what) {
-        if (err != cudaSuccess && status == FG_OK) {
-            status = (err == cudaErrorMemoryAllocation) ? FG_ERR_OUT_OF_MEMORY : FG_ERR_CUDA;
-            msg = std::string(what) + ": " + cudaGetErrorString(err);
+        if (err != cudaSuccess && job.status == FG_OK) {
+            job.status = (err == cudaErrorMemoryAllocation) ? FG_ERR_OUT_OF_MEMORY : FG_ERR_CUDA;
+            job.msg = std::string(what) + ": " + cudaGetErrorString(err);
         }
         return err == cudaSuccess;
     };
-    ck(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming), "event");
-    ck(cudaEventCreate(&ev0), "event");
-    ck(cudaEventCreate(&ev1), "event");
+    ck(cudaEventCreateWithFlags(&job.fork, cudaEventDisableTiming), "event");
+    ck(cudaEventCreate(&job.ev0), "event");
+    ck(cudaEventCreate(&job.ev1), "event");
+    ck(cudaEventCreateWithFlags(&job.done, cudaEventDisableTiming), "event");
     for (int k = 0; k < nk; k++) {
-        ck(cudaStreamCreateWithFlags(&ks[k], cudaStreamNonBlocking), "stream");
-        ck(cudaEventCreateWithFlags(&kev[k], cudaEventDisableTiming), "event");
+        ck(cudaStreamCreateWithFlags(&job.ks[k], cudaStreamNonBlocking), "stream");
+        ck(cudaEventCreateWithFlags(&job.kev[k], cudaEventDisableTiming), "event");
     }
     ck(cudaMemcpyAsync(base + zero_bytes, img.data(), table_bytes, cudaMemcpyHostToDevice, st), "table upload");
-    ck(cudaStreamSynchronize(st), "table upload");
-    ck(cudaEventRecord(ev0, st), "event");
+    ck(cudaEventRecord(job.ev0, st), "event");
     // the launches are recorded on `cs`: the caller's stream itself, or for a
     // CUDA graph a private stream (the legacy default stream cannot capture)
     cudaStream_t cs = st;
-    if (status == FG_OK && use_graph) {
+    if (job.status == FG_OK && use_graph) {
         ck(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "stream");
         ck(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "capture");
     }
     ck(cudaMemsetAsync(base, 0, zero_bytes, cs), "memset");
-    ck(cudaEventRecord(fork, cs), "event");
-    for (int k = 0; k < nk && status == FG_OK; k++) {
-        ck(cudaStreamWaitEvent(ks[k], fork, 0), "fork");
-        int kind_ctas = 0;
-        for (int c = 0; c < (int)kinds[kind_list[k]].class_size.size(); c++)
-            kind_ctas += kinds[kind_list[k]].class_teams[c] * kinds[kind_list[k]].class_size[c];
+    ck(cudaEventRecord(job.fork, cs), "event");
+    for (int k = 0; k < nk && job.status == FG_OK; k++) {
+        ck(cudaStreamWaitEvent(job.ks[k], job.fork, 0), "fork");
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(kind_ctas);
+        cfg.gridDim = dim3(kind_ctas[k]);
         cfg.blockDim = dim3(kBlock);
-        cfg.stream = ks[k];
+        cfg.stream = job.ks[k];
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeCooperative;
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        if (ck(cudaLaunchKernelEx(&cfg, batch_kernel_for(kind_list[k]), args[k]), "batch launch")) count_launch();
-        ck(cudaEventRecord(kev[k], ks[k]), "event");
-        ck(cudaStreamWaitEvent(cs, kev[k], 0), "join");
+        if (ck(cudaLaunchKernelEx(&cfg, kind_fn[k], args[k]), "batch launch")) count_launch();
+        ck(cudaEventRecord(job.kev[k], job.ks[k]), "event");
+        ck(cudaStreamWaitEvent(cs, job.kev[k], 0), "join");
     }
     if (use_graph && cs != st) {
-        cudaError_t ce = cudaStreamEndCapture(cs, &graph);
-        if (status == FG_OK) ck(ce, "capture");
-        if (status == FG_OK) ck(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate");
-        if (status == FG_OK) ck(cudaGraphLaunch(exec, st), "graph launch");
+        cudaError_t ce = cudaStreamEndCapture(cs, &job.graph);
+        if (job.status == FG_OK) ck(ce, "capture");
+        if (job.status == FG_OK) ck(cudaGraphInstantiate(&job.exec, job.graph, 0), "graph instantiate");
+        if (job.status == FG_OK) ck(cudaGraphLaunch(job.exec, st), "graph launch");
         cudaStreamDestroy(cs);
     }
-    ck(cudaEventRecord(ev1, st), "event");
-    std::vector<Ctrl> hc(nq);
-    ck(cudaMemcpyAsync(hc.data(), ctrls, nq * sizeof(Ctrl), cudaMemcpyDeviceToHost, st), "status copy");
-    ck(cudaStreamSynchronize(st), "batch");
-    float ms = 0.f;
-    if (status == FG_OK) cudaEventElapsedTime(&ms, ev0, ev1);
+    ck(cudaEventRecord(job.ev1, st), "event");
+    job.h_ctrls = h_ctrls_pinned;
+    if (!job.h_ctrls) {
+        job.own_ctrls.resize(nq);
+        job.h_ctrls = job.own_ctrls.data();
+    }
+    ck(cudaMemcpyAsync(job.h_ctrls, job.d_ctrls, nq * sizeof(Ctrl), cudaMemcpyDeviceToHost, st), "status copy");
+    if (enqueue_host_copies) {
+        for (int i = 0; i < nq; i++)
+            if (job.staging[i])
+                ck(cudaMemcpyAsync(qs[i].out, job.staging[i], (size_t)view[i]->n * sizeof(int32_t),
+                                   cudaMemcpyDeviceToHost, st), "result copy");
+        job.host_copies_done = true;
+    }
+    ck(cudaEventRecord(job.done, st), "event");
+    if (job.status != FG_OK) return fail(job.status, job.msg);
+    return FG_OK;
+}
 
-    // ---- per-query outcome, overflow test, host outputs
+// Waits for a launched batch, reports every query and releases the batch.
+fg_status batch_finish(BatchJob &job, fg_status *status_out, fg_stats *stats_out, fg_batch_stats *bstats) {
+    const int nq = job.nq;
+    cudaStream_t st = job.st;
+    auto ck = [&](cudaError_t err, const char *what) {
+        if (err != cudaSuccess && job.status == FG_OK) {
+            job.status = (err == cudaErrorMemoryAllocation) ? FG_ERR_OUT_OF_MEMORY : FG_ERR_CUDA;
+            job.msg = std::string(what) + ": " + cudaGetErrorString(err);
+        }
+        return err == cudaSuccess;
+    };
+    if (job.done) ck(cudaEventSynchronize(job.done), "batch");
+    float ms = 0.f;
+    if (job.status == FG_OK && job.ev0 && job.ev1) cudaEventElapsedTime(&ms, job.ev0, job.ev1);
     fg_status first_err = FG_OK;
     std::string first_msg;
-    for (int i = 0; i < nq && status == FG_OK; i++) {
+    for (int i = 0; i < nq && job.status == FG_OK; i++) {
+        const Ctrl &hc = job.h_ctrls[i];
+        const fg_query &q = job.qs[i];
+        const Params &p = job.params[i];
         fg_status qs_st = FG_OK;
-        const Params &p = h_params[i];
-        const int32_t *res = (hc[i].result_in_b && p.B) ? p.B : p.A;
-        if (hc[i].status & kStTimeout) qs_st = FG_ERR_TIMEOUT;
-        else if (hc[i].status & kStRoundCap) qs_st = FG_ERR_TIMEOUT;
-        else if (hc[i].status & kStWorklist) qs_st = FG_ERR_CUDA;
-        else if (!hc[i].done) qs_st = FG_ERR_TIMEOUT;
-        else if ((hc[i].status & kStOverflow) && qs[i].algo == FG_ALGO_SSSP) {
+        if (hc.status & kStTimeout) qs_st = FG_ERR_TIMEOUT;
+        else if (hc.status & kStRoundCap) qs_st = FG_ERR_TIMEOUT;
+        else if (hc.status & kStWorklist) qs_st = FG_ERR_CUDA;
+        else if (!hc.done) qs_st = FG_ERR_TIMEOUT;
+        else if ((hc.status & kStOverflow) && q.algo == FG_ALGO_SSSP) {
             int *flag = reinterpret_cast<int *>(p.ctrl);
             int hf = 0;
             ck(cudaMemsetAsync(flag, 0, sizeof(int), st), "memset");
-            overflow_check_launch(*view[i], p.out ? p.out : res, flag, st);
+            overflow_check_launch(*job.view[i], p.out, flag, st);
             ck(cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
             ck(cudaStreamSynchronize(st), "overflow check");
             if (hf) qs_st = FG_ERR_OVERFLOW;
         }
-        if (qs_st == FG_OK && !p.out)
-            ck(cudaMemcpyAsync(qs[i].out, res, (size_t)view[i]->n * sizeof(int32_t), cudaMemcpyDefault, st),
-               "result copy");
+        if (qs_st == FG_OK && job.staging[i] && !job.host_copies_done)
+            ck(cudaMemcpyAsync(q.out, job.staging[i], (size_t)job.view[i]->n * sizeof(int32_t),
+                               cudaMemcpyDeviceToHost, st), "result copy");
         if (status_out) status_out[i] = qs_st;
         if (qs_st != FG_OK && first_err == FG_OK) {
             first_err = qs_st;
@@ -341,37 +397,54 @@ fg_status run_batch(const fg_query *qs, int32_t nq, const fg_batch_options *opt,
         if (stats_out) {
             fg_stats &s = stats_out[i];
             s = fg_stats{};
-            s.mode = (int32_t)mode[i];
-            s.rounds = hc[i].rounds;
-            s.jump_passes = hc[i].jump_passes;
-            s.vertices_processed = (int64_t)hc[i].st_vertices;
-            s.edges_relaxed = (int64_t)hc[i].st_edges;
-            s.updates = (int64_t)hc[i].st_updates;
-            s.pushes = (int64_t)hc[i].st_pushes;
-            s.scanned = (int64_t)hc[i].st_scanned;
-            s.barriers = hc[i].barriers;
+            s.mode = (int32_t)job.mode[i];
+            s.rounds = hc.rounds;
+            s.jump_passes = hc.jump_passes;
+            s.vertices_processed = (int64_t)hc.st_vertices;
+            s.edges_relaxed = (int64_t)hc.st_edges;
+            s.updates = (int64_t)hc.st_updates;
+            s.pushes = (int64_t)hc.st_pushes;
+            s.scanned = (int64_t)hc.st_scanned;
+            s.barriers = hc.barriers;
         }
     }
+    if (job.status != FG_OK && status_out)
+        for (int i = 0; i < nq; i++) status_out[i] = job.status;
     ck(cudaStreamSynchronize(st), "result copies");
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
-    for (int k = 0; k < nk; k++) {
-        if (kev[k]) cudaEventDestroy(kev[k]);
-        if (ks[k]) cudaStreamDestroy(ks[k]);
+    if (job.exec) cudaGraphExecDestroy(job.exec);
+    if (job.graph) cudaGraphDestroy(job.graph);
+    for (size_t k = 0; k < job.ks.size(); k++) {
+        if (job.kev[k]) cudaEventDestroy(job.kev[k]);
+        if (job.ks[k]) cudaStreamDestroy(job.ks[k]);
     }
-    if (fork) cudaEventDestroy(fork);
-    if (ev0) cudaEventDestroy(ev0);
-    if (ev1) cudaEventDestroy(ev1);
-    cudaFreeAsync(base, st);
+    if (job.fork) cudaEventDestroy(job.fork);
+    if (job.ev0) cudaEventDestroy(job.ev0);
+    if (job.ev1) cudaEventDestroy(job.ev1);
+    if (job.done) cudaEventDestroy(job.done);
+    if (job.base) cudaFreeAsync(job.base, st);
+    job.exec = nullptr;
+    job.graph = nullptr;
+    job.ks.clear();
+    job.kev.clear();
+    job.fork = job.ev0 = job.ev1 = job.done = nullptr;
+    job.base = nullptr;
     if (bstats) {
         bstats->kernel_ms = ms;
-        bstats->launches = nk;
-        bstats->teams = total_teams;
-        bstats->ctas = total_ctas;
+        bstats->launches = job.launches;
+        bstats->teams = job.teams;
+        bstats->ctas = job.ctas;
     }
-    if (status != FG_OK) return fail(status, msg);
+    if (job.status != FG_OK) return fail(job.status, job.msg);
     if (first_err != FG_OK) return fail(first_err, first_msg);
     return FG_OK;
+}
+
+fg_status run_batch(const fg_query *qs, int32_t nq, const fg_batch_options *opt, fg_status *status_out,
+                    fg_stats *stats_out, fg_batch_stats *bstats) {
+    BatchJob job;
+    fg_status s = batch_launch(qs, nq, opt, 1.0, false, nullptr, job);
+    fg_status f = batch_finish(job, status_out, stats_out, bstats);
+    return s != FG_OK ? s : f;
 }
 
 }  // namespace fg

@@ -7,6 +7,7 @@
 
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/fg.h"
 
@@ -293,6 +294,32 @@ fg_status run_sweep(const fg_graph *g, Mode mode, const int32_t *cur, int32_t *n
 void overflow_check_launch(const View &g, const int32_t *D, int *flag, cudaStream_t st);
 
 // batches (fg_batch.cu)
+struct BatchJob {
+    int nq = 0;
+    std::vector<fg_query> qs;
+    std::vector<Mode> mode;
+    std::vector<const View *> view;
+    std::vector<Params> params;           // host copies of the device parameters
+    std::vector<int32_t *> staging;       // device staging of host outputs (null: device output)
+    bool host_copies_done = false;
+    char *base = nullptr;                 // the batch's one device allocation
+    size_t device_bytes = 0;
+    cudaStream_t st = 0;
+    std::vector<cudaStream_t> ks;
+    std::vector<cudaEvent_t> kev;
+    cudaEvent_t fork = nullptr, ev0 = nullptr, ev1 = nullptr, done = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    Ctrl *d_ctrls = nullptr;
+    Ctrl *h_ctrls = nullptr;
+    std::vector<Ctrl> own_ctrls;
+    int launches = 0, teams = 0, ctas = 0;
+    fg_status status = FG_OK;
+    std::string msg;
+};
+fg_status batch_launch(const fg_query *qs, int32_t nq, const fg_batch_options *opt, double cta_fraction,
+                       bool enqueue_host_copies, Ctrl *h_ctrls_pinned, BatchJob &job);
+fg_status batch_finish(BatchJob &job, fg_status *status_out, fg_stats *stats_out, fg_batch_stats *bstats);
 fg_status run_batch(const fg_query *qs, int32_t nq, const fg_batch_options *opt, fg_status *status_out,
                     fg_stats *stats_out, fg_batch_stats *bstats);
 

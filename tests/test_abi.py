@@ -61,6 +61,10 @@ int main(void) {
   P(fg_query, g); P(fg_query, algo); P(fg_query, src); P(fg_query, out); P(fg_query, mode);
   P(fg_batch_options, stream); P(fg_batch_options, use_cuda_graph); P(fg_batch_options, wait_timeout_ms);
   P(fg_batch_stats, kernel_ms); P(fg_batch_stats, launches); P(fg_batch_stats, teams); P(fg_batch_stats, ctas);
+  printf("fg_server_options %zu\nfg_completion %zu\n", sizeof(fg_server_options), sizeof(fg_completion));
+  P(fg_server_options, hbm_budget_bytes); P(fg_server_options, max_inflight); P(fg_server_options, max_wave);
+  P(fg_server_options, one_at_a_time); P(fg_server_options, wait_timeout_ms);
+  P(fg_completion, ticket); P(fg_completion, status); P(fg_completion, wave_size); P(fg_completion, latency_ms);
   return 0;
 }
 ''')
@@ -72,7 +76,7 @@ int main(void) {
         k, v = line.split()
         c[k] = int(v)
     for cls in (fg.fg_options, fg.fg_stats, fg.fg_graph_info_t, fg.fg_query, fg.fg_batch_options,
-                fg.fg_batch_stats):
+                fg.fg_batch_stats, fg.fg_server_options, fg.fg_completion):
         assert ctypes.sizeof(cls) == c[cls.__name__]
         for name, _ in cls._fields_:
             assert getattr(cls, name).offset == c[f"{cls.__name__}.{name}"], (cls.__name__, name)

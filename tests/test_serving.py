@@ -1,0 +1,96 @@
+"""The query server (continuous batching) on the GPU: every request served
+in a mix with others must return exactly what the same query returns alone
+(fg_run), whatever wave it ran in; the HBM budget and the one-at-a-time
+baseline change scheduling only."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import paper_1903_01665_gb300 as fg
+from tests.gpu_util import graph_handle, run
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests(graphs, count, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    srcs = [gg.sources(g, 16, seed=seed + i) for i, g in enumerate(graphs)]
+    reqs = []
+    for _ in range(count):
+        gi = int(rng.integers(0, len(graphs)))
+        u = rng.random()
+        algo = 0 if u < 0.4 else (1 if u < 0.8 else 2)
+        reqs.append((gi, algo, int(srcs[gi][rng.integers(0, len(srcs[gi]))])))
+    return reqs
+
+
+def _serve(handles, graphs, reqs, host_every=0, **opts):
+    import torch
+    st, srv = fg.fg_server_create(**opts)
+    assert st == fg.FG_OK, fg.fg_last_error()
+    outs, tickets = [], {}
+    try:
+        for i, (gi, algo, s) in enumerate(reqs):
+            n = graphs[gi].n
+            if host_every and i % host_every == 0:
+                out = torch.full((n,), -3, dtype=torch.int32).pin_memory()
+            else:
+                out = torch.full((n,), -3, dtype=torch.int32, device="cuda")
+            outs.append(out)
+            st, t = fg.fg_server_submit(srv, handles[gi], algo, s, out, fg.FG_AUTO)
+            assert st == fg.FG_OK, fg.fg_last_error()
+            tickets[t] = i
+        assert fg.fg_server_drain(srv, 120000) == fg.FG_OK
+        comps = fg.fg_server_poll(srv, cap=len(reqs) + 8)
+    finally:
+        assert fg.fg_server_destroy(srv) == fg.FG_OK
+    assert len(comps) == len(reqs)
+    assert all(c[1] == fg.FG_OK for c in comps)
+    return outs, comps
+
+
+@pytest.fixture(scope="module")
+def setup():
+    from contextlib import ExitStack
+    graphs = [gg.rmat(12, seed=21), gg.rmat(15, seed=22), gg.grid(128, seed=23), gg.er(4000, 30000, seed=24)]
+    with ExitStack() as stack:
+        handles = [stack.enter_context(graph_handle(g)) for g in graphs]
+        yield graphs, handles
+
+
+def _alone(graphs, handles, reqs):
+    want = {}
+    for gi, algo, s in set(reqs):
+        want[(gi, algo, s)] = run(handles[gi], graphs[gi].n, algo, s, fg.FG_AUTO)[0]
+    return want
+
+
+def test_results_in_the_mix_equal_results_alone(setup):
+    graphs, handles = setup
+    reqs = _requests(graphs, 300, seed=5)
+    outs, comps = _serve(handles, graphs, reqs, host_every=7, max_inflight=4, max_wave=32)
+    want = _alone(graphs, handles, reqs)
+    for (gi, algo, s), out in zip(reqs, outs):
+        np.testing.assert_array_equal(out.cpu().numpy(), want[(gi, algo, s)])
+    assert max(c[2] for c in comps) > 1, "requests submitted in a burst should share waves"
+    assert all(c[3] > 0 for c in comps)
+
+
+def test_tiny_budget_serves_one_per_wave(setup):
+    graphs, handles = setup
+    reqs = _requests(graphs, 40, seed=6)
+    outs, comps = _serve(handles, graphs, reqs, hbm_budget_bytes=1, max_inflight=2)
+    assert all(c[2] == 1 for c in comps)
+    want = _alone(graphs, handles, reqs)
+    for (gi, algo, s), out in zip(reqs, outs):
+        np.testing.assert_array_equal(out.cpu().numpy(), want[(gi, algo, s)])
+
+
+def test_one_at_a_time_baseline(setup):
+    graphs, handles = setup
+    reqs = _requests(graphs, 40, seed=7)
+    outs, comps = _serve(handles, graphs, reqs, one_at_a_time=True)
+    assert all(c[2] == 1 for c in comps)
+    want = _alone(graphs, handles, reqs)
+    for (gi, algo, s), out in zip(reqs, outs):
+        np.testing.assert_array_equal(out.cpu().numpy(), want[(gi, algo, s)])
