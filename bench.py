@@ -41,8 +41,9 @@ MODE_NAMES = ["vertex_sync", "vertex_async", "edge_sync", "edge_async"]
 ALGO_NAMES = ["sssp", "bfs", "cc"]
 
 # DRAM bytes per launch from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum), keyed by kernel; valid only while the kernel source
-# is unchanged (sha256 of csrc/fg_fixpoint.cu at capture time).
+# dram__bytes_write.sum), keyed by kernel; valid only while the device source
+# is unchanged (sha256 over fg_internal.cuh, fg_device.cuh and fg_fixpoint.cu
+# at capture time).
 NCU_TRAFFIC: dict = {
     # profiles/sssp_edge_sync_rmat22.md: one launch, first bench source, R-MAT 22
     "fixpoint_kernel<sssp,edge_sync>": {"bytes_per_launch": 6907746560 + 466209280,
@@ -50,9 +51,14 @@ NCU_TRAFFIC: dict = {
 }
 
 
+KERNEL_SOURCES = ("fg_internal.cuh", "fg_device.cuh", "fg_fixpoint.cu")
+
+
 def fixpoint_source_sha() -> str:
-    p = os.path.join(ROOT, "paper_1903_01665_gb300", "csrc", "fg_fixpoint.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1903_01665_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 # ---------------------------------------------------------------- workloads
@@ -400,6 +406,54 @@ def aggregate(units_local: int, seconds_local: float, pg=None, device=None):
     return int(u.item()), float(t.item())
 
 
+def run_sweep_roofline(r, peak_gbps: float, reps: int = 10, warm: int = 3) -> dict:
+    """The headline roofline test: one all-active relaxation round (fg_sweep)
+    over the workload graph, vertex variant (Alg. 1) and edge variant
+    (Alg. 2), from a fixed mid-run state: three synchronous rounds from the
+    first seeded source, then every vertex still unreached set to 2^30 so that
+    every vertex and edge is active.  Device time of each launch by CUDA
+    events inside the library; median of `reps` after `warm` warm-ups, next
+    reset to cur before every launch (outside the timed kernel).
+    Algorithmic bytes per round (4-byte offsets and values):
+      vertex: V*(4 row_off + 4 cur + 8 next init/copy) + E*(4 dst + 4 w + 4 next[dst]) + 4*lowered
+      edge:   V*8 + E*(12 src,dst,w + 4 cur[src] + 4 next[dst]) + 4*lowered"""
+    fg, torch, g = r.fg, r.torch, r.g
+    st, h = fg.fg_graph_create_coo(g.n, r.d_src, r.d_dst, r.d_w)
+    fg.check(st)
+    try:
+        inf = fg.FG_INF
+        cur = torch.full((g.n,), inf, dtype=torch.int32, device=r.d_src.device)
+        cur[int(r.srcs[0])] = 0
+        for _ in range(3):
+            nxt = cur.clone()
+            fg.check(fg.fg_sweep(h, fg.FG_VERTEX_SYNC, cur, nxt)[0])
+            cur = nxt
+        reached_after_3 = int((cur != inf).sum().item())
+        cur[cur == inf] = 1 << 30
+        nxt = torch.empty_like(cur)
+        out = {"state": "3 rounds from the first seeded source, unreached vertices set to 2^30 "
+                        "(every vertex and edge active)",
+               "reached_after_3_rounds": reached_after_3, "timing": f"median of {reps} launches"}
+        for mode, name in ((fg.FG_VERTEX_SYNC, "vertex_sync"), (fg.FG_EDGE_SYNC, "edge_sync")):
+            times = []
+            for i in range(warm + reps):
+                nxt.copy_(cur)
+                st, upd, ms = fg.fg_sweep(h, mode, cur, nxt)
+                fg.check(st)
+                if i >= warm:
+                    times.append(ms)
+            lowered = int((nxt < cur).sum().item())
+            v, e = g.n, g.m
+            nbytes = (16 * v + 12 * e if mode == fg.FG_VERTEX_SYNC else 8 * v + 20 * e) + 4 * lowered
+            med = float(np.median(times))
+            gbps = nbytes / (med * 1e-3) / 1e9
+            out[name] = {"us": round(med * 1e3, 1), "algorithmic_bytes": nbytes, "gbps": round(gbps, 1),
+                         "frac": round(gbps / peak_gbps, 4), "lowered": lowered, "writes": int(upd)}
+        return out
+    finally:
+        fg.check(fg.fg_graph_destroy(h))
+
+
 def run_ours(args):
     import torch
     import paper_1903_01665_gb300 as fg
@@ -491,6 +545,8 @@ def run_ours(args):
                "h2d_bytes_per_step": 3 * 4 * r.g.m,
                "d2h_bytes_per_step": 4 * r.g.n * len(r.queries), "steps": k2}
 
+    sweep = None if args.no_sweep else run_sweep_roofline(r, peaks[0])
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample(r.g, r.srcs, r.deg, args.workload)
@@ -512,7 +568,7 @@ def run_ours(args):
                            "teps_edges_per_step": units // max(args.steps, 1),
                            "l2": "inputs larger than L2 (graph ~1.9-2.2 GB built per step)",
                            "parallelism": f"replicas x{ws}"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "roofline": roofline, "sweep_roofline": sweep, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "per_kernel": per_mode, "batched": batched, "serving": serving}
         print(json.dumps(line), flush=True)
     if pg:
@@ -591,7 +647,6 @@ def run_case(args):
     import torch
     import paper_1903_01665_gb300 as fg
     algo_name, mode_name = args.case.split(":")
-    algo = ALGO_NAMES.index(algo_name)
     mode = MODE_NAMES.index(mode_name)
     if args.case_graph == "rmat":
         g = gg.rmat(args.case_scale)
@@ -601,6 +656,24 @@ def run_case(args):
     st, h = fg.fg_graph_create_coo(g.n, torch.from_numpy(g.src).cuda(), torch.from_numpy(g.dst).cuda(),
                                    torch.from_numpy(g.w).cuda())
     fg.check(st)
+    if algo_name == "sweep":
+        # the all-active round of the sweep roofline test, from its state
+        cur = torch.full((g.n,), fg.FG_INF, dtype=torch.int32, device="cuda")
+        cur[s] = 0
+        for _ in range(3):
+            nxt = cur.clone()
+            fg.check(fg.fg_sweep(h, fg.FG_VERTEX_SYNC, cur, nxt)[0])
+            cur = nxt
+        cur[cur == fg.FG_INF] = 1 << 30
+        nxt = torch.empty_like(cur)
+        for i in range(2):
+            nxt.copy_(cur)
+            st, upd, ms = fg.fg_sweep(h, mode, cur, nxt)
+            fg.check(st)
+            print(i, json.dumps({"writes": upd, "kernel_ms": ms}), flush=True)
+        fg.check(fg.fg_graph_destroy(h))
+        return
+    algo = ALGO_NAMES.index(algo_name)
     out = torch.empty(g.n, dtype=torch.int32, device="cuda")
     for i in range(2):
         st, stats = fg.fg_run(h, algo, s, out, mode)
@@ -611,7 +684,7 @@ def run_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default=None, help="profiling driver, e.g. sssp:edge_sync")
+    ap.add_argument("--case", default=None, help="profiling driver, e.g. sssp:edge_sync or sweep:edge_sync")
     ap.add_argument("--case-graph", default="rmat", choices=["rmat", "grid"])
     ap.add_argument("--case-scale", type=int, default=20, help="R-MAT scale or grid side")
     ap.add_argument("--gpus", type=int, default=1)
@@ -621,6 +694,7 @@ def main():
     ap.add_argument("--workload", default="rmat22", choices=["rmat22", "grid4096", "er16k"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the all-active sweep roofline test")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload comparison")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving comparison")
     ap.add_argument("--serving-full", action="store_true",

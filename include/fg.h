@@ -183,12 +183,19 @@ fg_status fg_run(const fg_graph *g, fg_algo algo, int32_t src, int32_t *out, fg_
 
 /*
  * One synchronous relaxation round with every vertex active, from caller
- * state: the topology-driven sweep of Alg. 1 (FG_VERTEX_SYNC) or Alg. 2
- * (FG_EDGE_SYNC) for SSSP.  cur and next are device int32[n]; next must
- * hold values <= cur elementwise (e.g. a copy of cur); next receives
- * min(next, cur[u] + w) over every edge.  Returns the number of lowered
- * values in *updates (may be NULL).  Used to measure the sweep against the
- * HBM roofline.
+ * state: the topology-driven body of Alg. 1 (FG_VERTEX_SYNC, over the CSR
+ * buckets) or Alg. 2 (FG_EDGE_SYNC, over the edge list) applied once, for
+ * SSSP.  cur and next are device int32[n] that must not overlap; for every
+ * edge u->v with cur[u] < INT32_MAX, next[v] = min(next[v], cur[u] + w).  A
+ * candidate that reaches INT32_MAX is not written; the call then returns
+ * FG_ERR_OVERFLOW after applying every other edge.  *updates (may be NULL)
+ * receives the number of successful lowering writes, which depends on the
+ * schedule: at least the number of lowered vertices, at most the number of
+ * edges.  *kernel_ms (may be NULL) receives the kernel's device time.  Runs
+ * on `stream` (NULL: legacy default stream) and blocks until done.  Used to
+ * measure the sweep against the HBM roofline.  Errors: FG_ERR_INVALID_ARG
+ * (NULL, host pointers, mode not FG_VERTEX_SYNC/FG_EDGE_SYNC, another
+ * device's graph), FG_ERR_OVERFLOW, FG_ERR_TIMEOUT, FG_ERR_CUDA.
  */
 fg_status fg_sweep(const fg_graph *g, fg_mode mode, const int32_t *cur, int32_t *next,
                    void *stream, int64_t *updates, float *kernel_ms);

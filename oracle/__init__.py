@@ -2,8 +2,9 @@
 
 Plain, sequential definitions of what the fixpoint relaxation sweep computes
 (Sec. 2, Algorithms 1-3): Dijkstra for SSSP, FIFO-queue BFS, union-find CC
-labelled by the minimum vertex id, and the Jacobi Bellman-Ford round count of
-the synchronous variant.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+labelled by the minimum vertex id, the Jacobi Bellman-Ford round count of
+the synchronous variant, and one double-buffered relaxation round from a given
+state (the all-active sweep).  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline leg may import this package; the CUDA library never
 does, and the two share no code.
 
@@ -59,6 +60,9 @@ def _bind(lib):
     lib.or_jacobi_rounds.restype = ctypes.c_int64
     lib.or_jacobi_rounds.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p,
                                      ctypes.c_int32, ctypes.c_int, ctypes.c_int64, i32p]
+    lib.or_sweep.restype = ctypes.c_int
+    lib.or_sweep.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, i32p, i32p,
+                             ctypes.POINTER(ctypes.c_int64)]
     return lib
 
 
@@ -120,3 +124,14 @@ def jacobi_rounds(n, src, dst, w, s, unit=False, max_rounds=None, lib=None):
     r = lib.or_jacobi_rounds(n, src.shape[0], _p(src), _p(dst), _p(w), s, 1 if unit else 0,
                              cap, _p(dist))
     return int(r), dist
+
+
+def sweep(n, src, dst, w, cur, nxt, lib=None):
+    """One double-buffered relaxation round (Alg. 1/2 body once) from state
+    (cur, nxt).  Returns (status, new next int32[n], lowered-vertex count)."""
+    lib = lib or _load()
+    src, dst, w, cur = _arr(src), _arr(dst), _arr(w), _arr(cur)
+    out = np.array(nxt, dtype=np.int32, copy=True)
+    low = ctypes.c_int64(0)
+    rc = lib.or_sweep(n, src.shape[0], _p(src), _p(dst), _p(w), _p(cur), _p(out), ctypes.byref(low))
+    return rc, out, low.value

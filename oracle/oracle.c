@@ -271,3 +271,36 @@ int64_t or_jacobi_rounds(int32_t n, int64_t m, const int32_t *src, const int32_t
     free(cur); free(next);
     return rounds;
 }
+
+/*
+ * One relaxation round from a given state, every vertex active: the body of
+ * Algorithm 1 (over CSR) and Algorithm 2 (over the edge list) applied once,
+ * double-buffered.  For every edge u->v with cur[u] finite, the candidate
+ * cur[u] + w (64-bit) lowers next[v] if smaller.  A candidate that reaches
+ * INT32_MAX is not written and makes the call return ORACLE_OVERFLOW (the
+ * other edges are still applied).  *lowered receives the number of vertices
+ * whose next value went down.  cur and next must not overlap.
+ */
+int or_sweep(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, const int32_t *w,
+             const int32_t *cur, int32_t *next, int64_t *lowered) {
+    int rc = check_edges(n, m, src, dst);
+    if (rc) return rc;
+    if (!cur || !next) return ORACLE_INVALID;
+    for (int64_t e = 0; e < m; e++)
+        if (w && w[e] < 0) return ORACLE_NEGATIVE_WEIGHT;
+    int32_t *before = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    if (!before) return ORACLE_NOMEM;
+    memcpy(before, next, (size_t)n * sizeof(int32_t));
+    int overflow = 0;
+    for (int64_t e = 0; e < m; e++) {
+        if (cur[src[e]] == UNREACHED) continue;
+        int64_t cand = (int64_t)cur[src[e]] + (w ? (int64_t)w[e] : 1);
+        if (cand >= INT32_MAX) { overflow = 1; continue; }
+        if (cand < next[dst[e]]) next[dst[e]] = (int32_t)cand;
+    }
+    int64_t count = 0;
+    for (int32_t v = 0; v < n; v++) count += next[v] < before[v];
+    free(before);
+    if (lowered) *lowered = count;
+    return overflow ? ORACLE_OVERFLOW : ORACLE_OK;
+}

@@ -37,12 +37,14 @@ __global__ void __launch_bounds__(kBlock, min_blocks<MODE>()) batch_kernel(Batch
     const int4 ct = b.cta_team[blockIdx.x];
     const Team t{ct.y, ct.z, b.team_bar + 2 * ct.x};
     const int cls = ct.w;
+    uint32_t ring_used;
+    fixpoint_prologue<ALGO, MODE>(ring_used);
     for (;;) {
         if (t.rank == 0 && threadIdx.x == 0) b.team_q[ct.x] = b.cls_begin[cls] + atomicAdd(&b.cls_next[cls], 1);
         if (!team_sync(t, b.bctrl, b.timeout_ns)) return;
         const int qi = __ldcg(&b.team_q[ct.x]);
         if (qi >= b.cls_end[cls]) return;
-        fixpoint_body<ALGO, MODE>(b.params[b.order[qi]], t);
+        fixpoint_body<ALGO, MODE>(b.params[b.order[qi]], t, ring_used);
         if (!team_sync(t, b.bctrl, b.timeout_ns)) return;
     }
 }

@@ -373,6 +373,12 @@ void make_buckets(Builder &b, View &v) {
     cudaFreeAsync(f, b.st);
     cudaFreeAsync(p, b.st);
     cudaFreeAsync(mx, b.st);
+    // the edge stream's bulk copies need the arrays 16-byte aligned, which
+    // device allocations are
+    if ((((uintptr_t)v.src | (uintptr_t)v.col | (uintptr_t)v.w) & 15u) != 0) {
+        b.status = FG_ERR_CUDA;
+        b.msg = "internal error: edge arrays not 16-byte aligned";
+    }
 }
 
 template <typename T>

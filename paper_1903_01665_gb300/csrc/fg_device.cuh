@@ -11,8 +11,10 @@
 //                  words, degree-bucketed lists) and expands those that
 //                  changed in the previous round; reads cur, MIN into next
 //                  (double-buffered, Jacobi), barrier, swap.
-//   edge-sync    : Alg. 2 -- every round streams the edges (src,dst,w) with
-//                  128-bit loads and relaxes those whose source changed.
+//   edge-sync    : Alg. 2 -- every round streams the edges (src,dst,w) in
+//                  1024-edge tiles by bulk copy (TMA) into a shared-memory
+//                  ring and relaxes those whose source changed; rounds with
+//                  few changes stream only the flagged tiles.
 //   vertex-async : data-driven (Sec. 3.3) -- worklists of vertices by degree
 //                  class, in-place atomic MIN, changed targets appended through
 //                  per-warp buffers, until the worklist is empty.
@@ -77,9 +79,10 @@ struct SyncOp {
     int32_t *snext;
     int32_t r;
 
+    // cur and scur are the previous round's: not written during the round
     __device__ __forceinline__ bool active(int32_t u, int32_t &val, bool &) const {
-        if (ldcg(scur + u) != r) return false;
-        val = ldcg(cur + u);
+        if (ldca(scur + u) != r) return false;
+        val = ldca(cur + u);
         return true;
     }
     __device__ __forceinline__ void own(int32_t u, int32_t val) const { red_min(next + u, val); }
@@ -94,7 +97,24 @@ struct SyncOp {
         }
         return true;
     }
-    __device__ __forceinline__ int32_t probe(int32_t v) const { return ldcg(cur + v); }
+    // staged-stream interface: the activity word and the value are loaded
+    // together (no dependent load), the weight comes from shared memory
+    __device__ __forceinline__ void load_act(int32_t u, int32_t &s, int32_t &v) const {
+        s = ldca(scur + u);
+        v = ldca(cur + u);
+    }
+    __device__ __forceinline__ bool is_act(int32_t s, int32_t) const { return s == r; }
+    __device__ __forceinline__ bool cand_w(int32_t val, int32_t wv, int32_t &c, Acc &a) const {
+        if (ALGO == kSSSP) {
+            uint32_t x = (uint32_t)val + (uint32_t)wv;
+            if (x >= (uint32_t)kInf) { a.overflow = 1; return false; }
+            c = (int32_t)x;
+        } else {
+            c = val;
+        }
+        return true;
+    }
+    __device__ __forceinline__ int32_t probe(int32_t v) const { return ldca(cur + v); }
     // v changes this round iff some candidate is below its previous-round
     // value, so any such candidate may mark it: the MIN needs no return value.
     __device__ __forceinline__ bool commit(int32_t v, int32_t c, int32_t pv, Acc &a) const {
@@ -120,6 +140,17 @@ struct BfsSyncOp {
     __device__ __forceinline__ void own(int32_t, int32_t) const {}
     __device__ __forceinline__ int32_t refresh(int32_t, int32_t val) const { return val; }
     __device__ __forceinline__ bool cand(int32_t, uint32_t, int32_t &c, Acc &) const {
+        c = lev + 1;
+        return true;
+    }
+    // a source's level was set in an earlier round (L1 is safe); the probe
+    // reads levels written during this round, through L2
+    __device__ __forceinline__ void load_act(int32_t u, int32_t &s, int32_t &v) const {
+        v = ldca(L + u);
+        s = v;
+    }
+    __device__ __forceinline__ bool is_act(int32_t, int32_t v) const { return v == lev; }
+    __device__ __forceinline__ bool cand_w(int32_t, int32_t, int32_t &c, Acc &) const {
         c = lev + 1;
         return true;
     }
@@ -221,8 +252,10 @@ struct SweepOp {
     const int32_t *cur;
     int32_t *next;
 
+    // cur is read-only during the sweep; a stale (larger) probe of next only
+    // lets through a candidate the atomic MIN then rejects
     __device__ __forceinline__ bool active(int32_t u, int32_t &val, bool &) const {
-        val = ldcg(cur + u);
+        val = ldca(cur + u);
         return val != kInf;
     }
     __device__ __forceinline__ void own(int32_t, int32_t) const {}
@@ -233,7 +266,18 @@ struct SweepOp {
         c = (int32_t)x;
         return true;
     }
-    __device__ __forceinline__ int32_t probe(int32_t v) const { return ldcg(next + v); }
+    __device__ __forceinline__ void load_act(int32_t u, int32_t &s, int32_t &v) const {
+        v = ldca(cur + u);
+        s = v;
+    }
+    __device__ __forceinline__ bool is_act(int32_t, int32_t v) const { return v != kInf; }
+    __device__ __forceinline__ bool cand_w(int32_t val, int32_t wv, int32_t &c, Acc &a) const {
+        uint32_t x = (uint32_t)val + (uint32_t)wv;
+        if (x >= (uint32_t)kInf) { a.overflow = 1; return false; }
+        c = (int32_t)x;
+        return true;
+    }
+    __device__ __forceinline__ int32_t probe(int32_t v) const { return ldca(next + v); }
     __device__ __forceinline__ bool commit(int32_t v, int32_t c, int32_t pv, Acc &a) const {
         if (c < pv) {
             if (atomicMin(next + v, c) > c) a.updates++;
@@ -620,80 +664,6 @@ __device__ __forceinline__ void expand_vertices(const Team &t, const uint32_t *_
     }
 }
 
-// Edge-parallel sweep over the source-sorted COO: each thread takes four
-// consecutive edges with a 128-bit load of src, and the activity test of a
-// source is reused across consecutive edges of the same source.  The thread
-// that holds an active source's first edge (the previous edge has another
-// source) also carries the source's value (op.own), so the synchronous
-// edge mode needs no separate pass over the vertices.
-template <class OP>
-__device__ __forceinline__ void expand_edges(const Team &t, const int32_t *__restrict__ src, const int32_t *__restrict__ col,
-                                             int64_t m, const OP &op, Acc &a) {
-    static_assert(kU == 4, "one int4 of sources per thread");
-    const int64_t tid = t.rank * (int64_t)kBlock + threadIdx.x;
-    const int64_t nth = (int64_t)t.size * kBlock;
-    const int64_t m4 = m >> 2;
-    const int4 *src4 = reinterpret_cast<const int4 *>(src);
-    const unsigned lane = lane_id();
-    if (tid == 0) a.scanned += (uint64_t)m;    // every edge's source is read once per round
-    for (int64_t q0 = tid - lane; q0 < m4; q0 += nth) {   // warp-uniform trip count
-        const int64_t q = q0 + lane;
-        int32_t us[4] = {-1, -1, -1, -1};
-        if (q < m4) {
-            int4 s4 = __ldg(src4 + q);
-            us[0] = s4.x; us[1] = s4.y; us[2] = s4.z; us[3] = s4.w;
-        }
-        // source of the edge before this thread's first edge
-        int32_t before = __shfl_up_sync(0xffffffffu, us[3], 1);
-        if (lane == 0) before = (q > 0 && q < m4) ? __ldg(src + 4 * q - 1) : -1;
-        uint32_t e[4];
-        int32_t val[4];
-        bool in[4];
-        int32_t prev = before, pval = 0;
-        bool pact = false;
-        if (before >= 0 && q < m4) {
-            bool rq;
-            pact = op.active(before, pval, rq);
-        }
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            if (us[j] < 0) {
-                pact = false;
-            } else if (us[j] != prev) {
-                bool rq;
-                pact = op.active(us[j], pval, rq);
-                if (pact) {
-                    op.own(us[j], pval);
-                    a.verts++;
-                }
-                prev = us[j];
-            }
-            e[j] = (uint32_t)(4 * q + j);
-            val[j] = pval;
-            in[j] = pact;
-            a.edges += pact;
-        }
-        relax_batch(col, op, NoPush{}, e, val, in, a);
-    }
-    for (int64_t x = 4 * m4 + tid; x < m; x += nth) {
-        int32_t vv;
-        bool rq;
-        int32_t u = __ldg(src + x);
-        if (op.active(u, vv, rq)) {
-            if (x == 0 || __ldg(src + x - 1) != u) {
-                op.own(u, vv);
-                a.verts++;
-            }
-            int32_t v = __ldg(col + x), c, pv;
-            if (op.cand(vv, (uint32_t)x, c, a)) {
-                pv = op.probe(v);
-                op.commit(v, c, pv, a);
-            }
-            a.edges++;
-        }
-    }
-}
-
 // Load-balanced expansion of a vertex worklist to its out-edges (edge-async).
 // Phase 1 (before the caller's grid barrier): each CTA takes a contiguous
 // slice of the worklist and writes the exclusive prefix sum of its items'
@@ -886,108 +856,305 @@ __device__ __forceinline__ void flag_edge_chunks(const Team &t, const uint32_t *
     }
 }
 
-// Stream pass of a sparse round: the 1024-edge chunks are dealt to the CTAs
-// round-robin; a CTA reads the flags of up to 256 of its chunks at once,
-// keeps the flagged ones and streams each with one 128-bit load of src per
-// thread (first-edge carry as in expand_edges).
+// ================================================================ staged edge stream
+// The edges of a synchronous edge round are streamed through shared memory,
+// each warp on its own: a 128-edge warp tile of (src, dst[, w]) arrives by
+// bulk copy (TMA) into one of the warp's kWStages buffers, completed on that
+// buffer's mbarrier, while the warp relaxes an earlier tile.  Each lane
+// copies its four edges into registers, forms their candidates (the
+// sources' values are read through L1: consecutive edges share sources), the
+// warp syncs and its buffer is refilled at once, then the lane probes the
+// targets and applies the updates.  No CTA-wide barrier is involved, so a
+// lane waiting on a contended target line holds up only its own warp.  The
+// copies carry an L2 evict-first hint so that the streamed edges do not push
+// the value and stamp arrays out of L2.  Two buffers per warp keep the
+// CTA's shared memory at 25 KB: on skewed graphs the targets' hot lines are
+// served from L1, which shares its capacity with shared memory (a third
+// buffer halved the throughput of an all-active R-MAT round).
+#ifndef FG_EDGE_STAGES
+#define FG_EDGE_STAGES 2
+#endif
+constexpr int kWTile = 128;             // edges per warp tile (4 per lane)
+constexpr int kWStages = FG_EDGE_STAGES;
+constexpr int kWTilesPerChunk = kEChunk / kWTile;
+
+template <bool W>
+struct __align__(16) WarpStage {
+    int32_t src[kWTile + 4];       // src[e0-4 .. e0+cnt): src[3] is the edge before the tile
+    int32_t col[kWTile];
+    int32_t w[W ? kWTile : 4];
+};
+
+template <bool W>
+struct __align__(16) WarpRing {
+    WarpStage<W> st[kWStages];
+    uint64_t full[kWStages];
+};
+
+template <bool W>
+struct EdgeRings {
+    WarpRing<W> warp[kWarps];
+    uint64_t pol;                  // L2 policy of the copies
+};
+
+template <bool W>
+__device__ __forceinline__ void rings_init(EdgeRings<W> &R) {
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kWarps; i++)
+            for (int j = 0; j < kWStages; j++) mbar_init(&R.warp[i].full[j], 1);
+        R.pol = l2_evict_first_policy();
+        mbar_init_fence();
+    }
+    __syncthreads();
+}
+
+// Lane 0: start the copies of warp tile `tile` into buffer `slot`.  The
+// copied prefix is a multiple of 4 edges (16 bytes); the last tile's ragged
+// tail (at most 3 edges) is read from global memory by its lane.  A tile
+// past the end copies nothing (the arrival alone completes the phase).
+template <bool W>
+__device__ __forceinline__ void wring_issue(WarpRing<W> &R, uint64_t pol, int slot, int64_t tile, const View &g) {
+    const int64_t e0 = tile * kWTile;
+    const int64_t cnt = max((int64_t)0, min((int64_t)kWTile, g.m - e0));
+    const uint32_t staged = (uint32_t)(cnt & ~3ll);
+    const uint32_t lead = (e0 > 0 && cnt > 0) ? 4u : 0u;
+    const uint32_t bytes = 4u * (staged + lead) + 4u * staged * (W ? 2u : 1u);
+    WarpStage<W> &S = R.st[slot];
+    mbar_expect_tx(&R.full[slot], bytes);
+    if (staged + lead) bulk_g2s(S.src + (4 - lead), g.src + e0 - lead, 4u * (staged + lead), &R.full[slot], pol);
+    if (staged) {
+        bulk_g2s(S.col, g.col + e0, 4u * staged, &R.full[slot], pol);
+        if (W) bulk_g2s(S.w, g.w + e0, 4u * staged, &R.full[slot], pol);
+    }
+}
+
+// Bounded wait for a buffer's copies: false after timeout_ns.
+__device__ __forceinline__ bool ring_wait(uint64_t *bar, uint32_t parity, unsigned long long timeout_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (uint32_t it = 0; it < (1u << 26); it++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63) == 63 && global_ns() - t0 > timeout_ns) return false;
+    }
+    return false;
+}
+
+// A lane's four edges of a tile after candidate formation: the targets, the
+// candidates and which of them to apply.
+struct Quad {
+    int32_t vs[4], c[4];
+    bool ok[4];
+};
+
+// From the warp tile in buffer S (tile starting at e0): the lane's four
+// edges, their sources' activity and values, the carry of each active
+// source's value into the other buffer at the source's first edge (the edge
+// before it has another source, so the synchronous edge mode needs no
+// separate pass over the vertices), and the candidates.  Nothing of the
+// buffer is needed after.
+template <bool W, class OP>
+__device__ __forceinline__ void quad_form(const WarpStage<W> &S, int64_t e0, const View &g, const OP &op, Quad &q,
+                                          Acc &a) {
+    const int cnt = (int)max((int64_t)0, min((int64_t)kWTile, g.m - e0));
+    const int staged = cnt & ~3;
+    const int i4 = 4 * (int)lane_id();
+    int32_t us[4] = {-1, -1, -1, -1}, ws[4] = {0, 0, 0, 0};
+    int nv = 0;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        q.vs[j] = 0;
+        q.c[j] = 0;
+        q.ok[j] = false;
+    }
+    if (i4 >= cnt) return;
+    if (i4 < staged) {
+        const int4 s4 = *reinterpret_cast<const int4 *>(S.src + 4 + i4);
+        const int4 c4 = *reinterpret_cast<const int4 *>(S.col + i4);
+        us[0] = s4.x; us[1] = s4.y; us[2] = s4.z; us[3] = s4.w;
+        q.vs[0] = c4.x; q.vs[1] = c4.y; q.vs[2] = c4.z; q.vs[3] = c4.w;
+        if (W) {
+            const int4 w4 = *reinterpret_cast<const int4 *>(S.w + i4);
+            ws[0] = w4.x; ws[1] = w4.y; ws[2] = w4.z; ws[3] = w4.w;
+        }
+        nv = 4;
+    } else {   // ragged tail of the last tile
+        nv = cnt - i4;
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            if (j < nv) {
+                us[j] = __ldg(g.src + e0 + i4 + j);
+                q.vs[j] = __ldg(g.col + e0 + i4 + j);
+                if (W) ws[j] = __ldg(g.w + e0 + i4 + j);
+            }
+    }
+    const int32_t before = (e0 + i4 == 0) ? -1 : S.src[3 + i4];
+    bool fresh[4];
+    int32_t st[4], vl[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        fresh[j] = j < nv && (j == 0 || us[j] != us[j - 1]);
+        st[j] = 0;
+        vl[j] = 0;
+        if (fresh[j]) op.load_act(us[j], st[j], vl[j]);
+    }
+    bool act[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        if (j >= nv) {
+            act[j] = false;
+        } else if (fresh[j]) {
+            act[j] = op.is_act(st[j], vl[j]);
+            if (act[j] && (j > 0 || us[0] != before)) {
+                op.own(us[j], vl[j]);
+                a.verts++;
+            }
+        } else {
+            act[j] = act[j - 1];
+            vl[j] = vl[j - 1];
+        }
+        q.ok[j] = act[j] && op.cand_w(vl[j], ws[j], q.c[j], a);
+        a.edges += act[j];
+    }
+}
+
+// Apply a quad: all probes of the targets, then the updates.
 template <class OP>
-__device__ __forceinline__ void expand_flagged_chunks(const Team &t, const int32_t *__restrict__ src, const int32_t *__restrict__ col,
-                                                      int64_t m, const int32_t *eflag, int32_t round, const OP &op,
-                                                      Acc &a) {
+__device__ __forceinline__ void quad_apply(const OP &op, const Quad &q, Acc &a) {
+    int32_t pv[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) pv[j] = q.ok[j] ? op.probe(q.vs[j]) : 0;
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+        if (q.ok[j]) op.commit(q.vs[j], q.c[j], pv[j], a);
+}
+
+// A warp streams `count` warp tiles, the k-th being tile_of(k), through its
+// ring and relaxes them.  All lanes call it with the same arguments; `used`
+// counts the tiles that went through the warp's ring so far (it fixes each
+// buffer's mbarrier phase) and is kept in a register by every lane.  Returns
+// false (with kStTimeout set) if a copy did not complete within timeout_ns;
+// the warp then waits, again bounded, for the copies it still has in flight.
+template <bool W, class TILE_OF, class OP>
+__device__ __forceinline__ bool warp_stream(WarpRing<W> &R, uint64_t pol, uint32_t &used, int count,
+                                            const TILE_OF &tile_of, const View &g, const OP &op, Acc &a, Ctrl *c,
+                                            unsigned long long timeout_ns) {
+    if (count <= 0) return true;
+    const bool leader = lane_id() == 0;
+    const uint32_t base = used;
+    if (leader)
+        for (int k = 0; k < min(count, kWStages); k++) wring_issue(R, pol, (int)((base + k) % kWStages), tile_of(k), g);
+    int k = 0;
+    bool ok = true;
+    for (; k < count; k++) {
+        const uint32_t gk = base + (uint32_t)k;
+        const int slot = (int)(gk % kWStages);
+        Quad q;
+        const bool mine = ring_wait(&R.full[slot], (gk / kWStages) & 1u, timeout_ns);
+        if (mine) quad_form(R.st[slot], tile_of(k) * kWTile, g, op, q, a);
+        // past this point every lane holds its part of tile k in registers:
+        // the buffer takes tile k + kWStages
+        ok = __all_sync(0xffffffffu, mine);
+        __syncwarp();
+        if (!ok) break;
+        if (leader && k + kWStages < count) wring_issue(R, pol, slot, tile_of(k + kWStages), g);
+        quad_apply(op, q, a);
+    }
+    const int issued = min(count, kWStages + k);
+    if (!ok && leader) {
+        // tiles k .. issued-1 may still be in flight
+        for (int j = k; j < issued; j++) {
+            const uint32_t gj = base + (uint32_t)j;
+            ring_wait(&R.full[gj % kWStages], (gj / kWStages) & 1u, timeout_ns);
+        }
+        atomicOr(&c->status, kStTimeout);
+    }
+    __syncwarp();
+    used = base + (uint32_t)(ok ? count : issued);
+    return ok;
+}
+
+// The CTA's rings; only kernels that stream edge tiles instantiate them.
+template <bool W>
+__device__ __forceinline__ EdgeRings<W> &edge_rings() {
+    __shared__ EdgeRings<W> rings;
+    return rings;
+}
+
+// Dense synchronous edge round: warp tiles dealt round-robin to the warps of
+// the team.
+template <bool W, class OP>
+__device__ __forceinline__ bool stream_all_edges(const Team &t, uint32_t &used, const View &g, const OP &op, Acc &a,
+                                                 Ctrl *c, unsigned long long timeout_ns) {
+    EdgeRings<W> &R = edge_rings<W>();
+    const int64_t ntiles = (g.m + kWTile - 1) / kWTile;
+    const int64_t gw = (int64_t)t.rank * kWarps + (threadIdx.x >> 5), nw = (int64_t)t.size * kWarps;
+    const int count = ntiles > gw ? (int)((ntiles - 1 - gw) / nw + 1) : 0;
+    if (t.rank == 0 && threadIdx.x == 0) a.scanned += (uint64_t)g.m;
+    const bool ok = warp_stream(R.warp[threadIdx.x >> 5], R.pol, used, count,
+                                [&](int k) { return gw + (int64_t)k * nw; }, g, op, a, c, timeout_ns);
+    return __syncthreads_and(ok);
+}
+
+// Sparse synchronous edge round: the 1024-edge chunks flagged by
+// flag_edge_chunks, dealt round-robin to the CTAs, 256 flags tested at once;
+// warp w of the CTA streams warp tile w of every flagged chunk.
+template <bool W, class OP>
+__device__ __forceinline__ bool stream_flagged_edges(const Team &t, uint32_t &used, const View &g,
+                                                     const int32_t *eflag, int32_t round, const OP &op, Acc &a,
+                                                     Ctrl *c, unsigned long long timeout_ns) {
     __shared__ int32_t s_klist[kBlock];
     __shared__ int s_kn;
-    const int64_t nec = (m + kEChunk - 1) >> kEChunkLog;
-    const int64_t m4 = m >> 2;
-    const int4 *src4 = reinterpret_cast<const int4 *>(src);
+    EdgeRings<W> &R = edge_rings<W>();
+    const int64_t nec = (g.m + kEChunk - 1) >> kEChunkLog;
     const int64_t G = t.size;
-    const unsigned lane = lane_id();
+    const int wid = threadIdx.x >> 5;
+    bool ok = true;
     for (int64_t base = t.rank; base < nec; base += G * kBlock) {
         const int64_t k = base + (int64_t)threadIdx.x * G;
         const bool act = k < nec && ldcg(eflag + k) == round;
         const int na = block_compact(act, (int32_t)k, s_klist, &s_kn);
-        for (int i = 0; i < na; i++) {
-            const int64_t kk = s_klist[i];
-            const int64_t e0 = kk << kEChunkLog, e1 = min(m, e0 + kEChunk);
-            if (threadIdx.x == 0) a.scanned += e1 - e0;
-            const int64_t q = (e0 >> 2) + threadIdx.x;
-            const bool qin = q < min(m4, (e1 + 3) >> 2) && q < m4;
-            int32_t us[4] = {-1, -1, -1, -1};
-            if (qin) {
-                int4 s4 = __ldg(src4 + q);
-                us[0] = s4.x; us[1] = s4.y; us[2] = s4.z; us[3] = s4.w;
-            }
-            int32_t before = __shfl_up_sync(0xffffffffu, us[3], 1);
-            if (lane == 0) before = (qin && q > 0) ? __ldg(src + 4 * q - 1) : -1;
-            uint32_t e[4];
-            int32_t val[4];
-            bool in[4];
-            int32_t prev = before, pval = 0;
-            bool pact = false;
-            if (before >= 0 && qin) {
-                bool rq;
-                pact = op.active(before, pval, rq);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                if (us[j] < 0) {
-                    pact = false;
-                } else if (us[j] != prev) {
-                    bool rq;
-                    pact = op.active(us[j], pval, rq);
-                    if (pact) {
-                        op.own(us[j], pval);
-                        a.verts++;
-                    }
-                    prev = us[j];
-                }
-                e[j] = (uint32_t)(4 * q + j);
-                val[j] = pval;
-                in[j] = pact;
-                a.edges += pact;
-            }
-            relax_batch(col, op, NoPush{}, e, val, in, a);
-            // the last chunk may end with up to three edges past the 128-bit part
-            const int64_t x = max(e0, 4 * m4) + threadIdx.x;
-            if (x < e1) {
-                int32_t vv;
-                bool rq;
-                int32_t u = __ldg(src + x);
-                if (op.active(u, vv, rq)) {
-                    if (x == 0 || __ldg(src + x - 1) != u) {
-                        op.own(u, vv);
-                        a.verts++;
-                    }
-                    int32_t v = __ldg(col + x), cc, pv;
-                    if (op.cand(vv, (uint32_t)x, cc, a)) {
-                        pv = op.probe(v);
-                        op.commit(v, cc, pv, a);
-                    }
-                    a.edges++;
-                }
-            }
-        }
-        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int i = 0; i < na; i++) a.scanned += (uint64_t)min((int64_t)kEChunk, g.m - ((int64_t)s_klist[i] << kEChunkLog));
+        ok = warp_stream(R.warp[wid], R.pol, used, na,
+                         [&](int i) { return (int64_t)s_klist[i] * kWTilesPerChunk + wid; }, g, op, a, c, timeout_ns);
+        if (!__syncthreads_and(ok)) return false;
     }
+    return true;
 }
 
 // ================================================================ the kernel
 // Resident CTAs per SM the register budget is sized for: the synchronous
-// modes gain from more warps in flight; the worklist modes do not.
+// modes gain from more warps in flight; the worklist modes do not; the
+// edge-sync kernels keep their tile state in 64 registers (four CTAs).
 #ifndef FG_SYNC_MIN_BLOCKS
 #define FG_SYNC_MIN_BLOCKS 6
 #endif
 #ifndef FG_ASYNC_MIN_BLOCKS
 #define FG_ASYNC_MIN_BLOCKS 4
 #endif
+#ifndef FG_EDGE_SYNC_MIN_BLOCKS
+#define FG_EDGE_SYNC_MIN_BLOCKS 4
+#endif
 template <int MODE>
 constexpr int min_blocks() {
-    return (MODE == kVertexSync || MODE == kEdgeSync) ? FG_SYNC_MIN_BLOCKS : FG_ASYNC_MIN_BLOCKS;
+    return MODE == kVertexSync ? FG_SYNC_MIN_BLOCKS
+                               : (MODE == kEdgeSync ? FG_EDGE_SYNC_MIN_BLOCKS : FG_ASYNC_MIN_BLOCKS);
 }
 
 // The whole query -- init, rounds, convergence -- run by one team of CTAs
 // (the full grid for a single query, a slice of it in a batch).
+// Once per kernel launch, before the first fixpoint_body: the edge-sync
+// kernels initialise their CTA's tile rings (their mbarriers live for the
+// whole launch; ring_used, kept by every lane, carries the phases of the
+// lane's warp ring from one query of the CTA to the next).
 template <int ALGO, int MODE>
-__device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t) {
+__device__ __forceinline__ void fixpoint_prologue(uint32_t &ring_used) {
+    ring_used = 0;
+    if constexpr (MODE == kEdgeSync) rings_init(edge_rings<ALGO == kSSSP>());
+}
+
+template <int ALGO, int MODE>
+__device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, uint32_t &ring_used) {
     constexpr bool SYNC = (MODE == kVertexSync || MODE == kEdgeSync);
     Ctrl *c = p.ctrl;
     const View &g = p.g;
@@ -1049,6 +1216,7 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t) {
 
     if (SYNC && ok) {
         int pass_ctr = 0;
+        constexpr bool kW = (ALGO == kSSSP);   // the edge rings carry weights for SSSP only
         // edge-sync: a round is sparse if the previous one accepted fewer
         // candidates than n/8 (round 1: only the source is active, except CC)
         auto sparse_round = [&](int r) -> bool {
@@ -1062,18 +1230,18 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t) {
             }
             if (tid == 0) c->changed[(r + 1) % 3] = 0;
             rounds = r;
-            if (ALGO == kBFS) {
+            if constexpr (ALGO == kBFS) {
                 BfsSyncOp op{p.A, r - 1};
-                if (MODE == kVertexSync) {
+                if constexpr (MODE == kVertexSync) {
                     expand_vertices(t, g.row_off, g.col, g.low, 0, g.mid, g.n_mid, g.high, g.n_high_chunks, op,
                                     NoPush{}, a);
                     expand_low_dense(t, g.row_off, g.col, p.A, r - 1, n, op, a);
                 } else if (sparse_round(r)) {
                     flag_edge_chunks(t, g.row_off, p.A, r - 1, n, p.eflag, r, a);
                     if (!sync_()) break;
-                    expand_flagged_chunks(t, g.src, g.col, g.m, p.eflag, r, op, a);
+                    if (!stream_flagged_edges<kW>(t, ring_used, g, p.eflag, r, op, a, c, p.timeout_ns)) break;
                 } else {
-                    expand_edges(t, g.src, g.col, g.m, op, a);
+                    if (!stream_all_edges<kW>(t, ring_used, g, op, a, c, p.timeout_ns)) break;
                 }
             } else {
                 const int32_t *cur = (r & 1) ? p.A : p.B;
@@ -1081,16 +1249,16 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t) {
                 const int32_t *scur = (r & 1) ? p.S1 : p.S0;
                 int32_t *snext = (r & 1) ? p.S0 : p.S1;
                 SyncOp<ALGO> op{g.w, cur, next, scur, snext, r};
-                if (MODE == kVertexSync) {
+                if constexpr (MODE == kVertexSync) {
                     expand_vertices(t, g.row_off, g.col, g.low, 0, g.mid, g.n_mid, g.high, g.n_high_chunks, op,
                                     NoPush{}, a);
                     expand_low_dense(t, g.row_off, g.col, scur, r, n, op, a);
                 } else if (sparse_round(r)) {
                     flag_edge_chunks(t, g.row_off, scur, r, n, p.eflag, r, a);
                     if (!sync_()) break;
-                    expand_flagged_chunks(t, g.src, g.col, g.m, p.eflag, r, op, a);
+                    if (!stream_flagged_edges<kW>(t, ring_used, g, p.eflag, r, op, a, c, p.timeout_ns)) break;
                 } else {
-                    expand_edges(t, g.src, g.col, g.m, op, a);
+                    if (!stream_all_edges<kW>(t, ring_used, g, op, a, c, p.timeout_ns)) break;
                 }
             }
             int ch = block_sum(a.changed);

@@ -12,21 +12,27 @@ namespace {
 template <int ALGO, int MODE>
 __global__ void __launch_bounds__(kBlock, min_blocks<MODE>()) fixpoint_kernel(Params p) {
     const Team t{(int)blockIdx.x, (int)gridDim.x, &p.ctrl->bar_count};
-    fixpoint_body<ALGO, MODE>(p, t);
+    uint32_t ring_used;
+    fixpoint_prologue<ALGO, MODE>(ring_used);
+    fixpoint_body<ALGO, MODE>(p, t, ring_used);
 }
 
 // One all-active sweep: vertex variant over the buckets, edge variant over
-// the COO.  Ordinary launch (no grid barrier).
+// the COO (staged edge stream).  Ordinary launch (no grid barrier).
+constexpr unsigned long long kSweepTimeoutNs = 2000000000ull;
 template <int MODE>
 __global__ void __launch_bounds__(kBlock) sweep_kernel(View g, const int32_t *cur, int32_t *next, Ctrl *c) {
     const Team t{(int)blockIdx.x, (int)gridDim.x, nullptr};
     Acc a;
     SweepOp op{g.w, cur, next};
-    if (MODE == kVertexSync)
+    if constexpr (MODE == kVertexSync) {
         expand_vertices(t, g.row_off, g.col, g.low, g.n_low, g.mid, g.n_mid, g.high, g.n_high_chunks, op, NoPush{},
                         a);
-    else
-        expand_edges(t, g.src, g.col, g.m, op, a);
+    } else {
+        uint32_t used = 0;
+        rings_init(edge_rings<true>());
+        stream_all_edges<true>(t, used, g, op, a, c, kSweepTimeoutNs);
+    }
     unsigned long long eu = block_sum(a.updates);
     int of = block_sum(a.overflow);
     if (threadIdx.x == 0) {
@@ -309,6 +315,8 @@ fg_status run_sweep(const fg_graph *G, Mode mode, const int32_t *cur, int32_t *n
     if (e != cudaSuccess) return cuda_fail(e, "sweep");
     if (updates) *updates = (int64_t)hc.st_updates;
     if (kernel_ms) *kernel_ms = ms;
+    if (hc.status & kStTimeout) return fail(FG_ERR_TIMEOUT, "sweep: an edge tile copy did not complete");
+    if (hc.status & kStOverflow) return fail(FG_ERR_OVERFLOW, "sweep: a candidate reached INT32_MAX");
     return FG_OK;
 }
 

@@ -134,13 +134,67 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Mutable arrays are read through L2 (ld.global.cg): other CTAs write them
-// during the kernel, so L1 copies could be stale.
+// Arrays that other CTAs write during the current round are read through L2
+// (ld.global.cg): an L1 copy could be stale.  Arrays written only before the
+// current round began -- the previous round's values and activity stamps of
+// the synchronous modes -- are read through L1 (ld.global.ca), where the hot
+// lines of skewed graphs stay SM-local: the team barrier that separates
+// rounds ends with an acquire at gpu scope on every CTA, which discards this
+// SM's L1 copies of lines written in earlier rounds.
 __device__ __forceinline__ int32_t ldcg(const int32_t *p) { return __ldcg(p); }
+__device__ __forceinline__ int32_t ldca(const int32_t *p) { return __ldca(p); }
 __device__ __forceinline__ void stcg(int32_t *p, int32_t v) { __stcg(p, v); }
 // atomic MIN whose result is not needed (a reduction: no round trip)
 __device__ __forceinline__ void red_min(int32_t *p, int32_t v) {
     asm volatile("red.relaxed.gpu.global.min.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ---------------------------------------------------------------- bulk copies (TMA)
+// One-dimensional bulk copies global -> shared memory, completed on an
+// mbarrier with a transaction count (PTX ISA: cp.async.bulk, mbarrier).
+// Both addresses must be 16-byte aligned and the size a multiple of 16.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// make initialised barriers visible to the async (bulk-copy) proxy
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// L2 policy for data read once per pass (the edge stream): evict it first so
+// that the value and stamp arrays stay resident in L2.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
 }
 
 // ---------------------------------------------------------------- team barrier

@@ -152,3 +152,28 @@ def sync_rounds_from_distances(n, src, dst, w, s, dist):
                 hops[v] = hops[u] + 1
                 q.append(v)
     return 1 + max(hops)
+
+
+def brute_force_hop_limited(n, src, dst, w, s, k):
+    """Minimum weight over simple paths from s with at most k edges (None = no
+    such path), by enumeration.  With w >= 0 a walk never beats its simple
+    sub-path, so this is what k double-buffered rounds from (s: 0, else
+    unreached) must hold (tiny n only)."""
+    adj = [[] for _ in range(n)]
+    for u, v, x in zip(src, dst, w):
+        adj[int(u)].append((int(v), int(x)))
+    best = [None] * n
+    best[s] = 0
+    stack = [(s, 0, 0, 1 << s)]
+    while stack:
+        u, dist, hops, seen = stack.pop()
+        if hops == k:
+            continue
+        for v, x in adj[u]:
+            if seen >> v & 1:
+                continue
+            nd = dist + x
+            if best[v] is None or nd < best[v]:
+                best[v] = nd
+            stack.append((v, nd, hops + 1, seen | (1 << v)))
+    return best

@@ -32,6 +32,13 @@ MUTANTS = {
                                    "if (next[src[e]] == INT64_MAX) continue;"),
                                   ("int64_t cand = cur[src[e]] + ((unit || !w) ? 1 : (int64_t)w[e]);",
                                    "int64_t cand = next[src[e]] + ((unit || !w) ? 1 : (int64_t)w[e]);")],
+    "sweep_reads_write_buffer": [("if (cur[src[e]] == UNREACHED) continue;",
+                                  "if (next[src[e]] == UNREACHED) continue;"),
+                                 ("int64_t cand = (int64_t)cur[src[e]] + (w ? (int64_t)w[e] : 1);",
+                                  "int64_t cand = (int64_t)next[src[e]] + (w ? (int64_t)w[e] : 1);")],
+    "sweep_drops_weight": [("int64_t cand = (int64_t)cur[src[e]] + (w ? (int64_t)w[e] : 1);",
+                            "int64_t cand = (int64_t)cur[src[e]] + 1;")],
+    "sweep_counts_writes": [("count += next[v] < before[v];", "count += next[v] <= before[v];")],
     "dijkstra_skips_zero_weight": [("if (cand < d[t]) {", "if (cand < d[t] && cand != it.key) {")],
 }
 
@@ -84,6 +91,12 @@ def run_pins(lib):
         r, _ = oracle.jacobi_rounds(g.n, g.src, g.dst, g.w, 0, lib=lib)
         assert r == 9
 
+    def sweep():
+        src, dst, w = [0, 1, 3], [1, 2, 2], [5, 7, 1]
+        cur = np.array([0, INF, INF, INF], np.int32)
+        rc, nxt, low = oracle.sweep(4, src, dst, w, cur, cur, lib=lib)
+        assert rc == oracle.OK and nxt.tolist() == [0, 5, INF, INF] and low == 1
+
     def invariants():
         g = gg.rmat(10, 8, seed=77)
         s = int(gg.sources(g, 1, seed=78)[0])
@@ -94,7 +107,7 @@ def run_pins(lib):
 
     for name, fn in [("floyd_warshall", fw), ("brute_force", brute), ("cycle", cycle),
                      ("cliques", cliques), ("overflow", overflow), ("rounds", rounds),
-                     ("invariants", invariants)]:
+                     ("sweep", sweep), ("invariants", invariants)]:
         check(name, fn)
     return failed
 

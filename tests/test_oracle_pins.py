@@ -7,7 +7,10 @@ invariants.  BFS (Alg. 3) by brute force, scipy unweighted shortest paths,
 closed forms (grid, directed cycle, complete graph) and invariants.  CC by
 scipy weak components, DFS component counts, disjoint cliques and the
 one-label-per-component invariants.  The Jacobi round count by path/star
-closed forms and by its definition through hop counts.
+closed forms and by its definition through hop counts.  The all-active round
+(one double-buffered relaxation from a given state) by a hand example, by
+hop-limited brute-force path enumeration after k rounds, and by iterating it
+to the Floyd-Warshall distances in the hop-count number of rounds.
 """
 import numpy as np
 import pytest
@@ -241,3 +244,68 @@ def test_jacobi_rounds_vs_definition(seed):
     _, ref = oracle.sssp(g.n, g.src, g.dst, g.w, 0)
     np.testing.assert_array_equal(dist, ref)
     assert r == pins.sync_rounds_from_distances(g.n, g.src, g.dst, g.w, 0, ref)
+
+
+# ---------------------------------------------------------------- one all-active round
+def _init_state(n, s):
+    cur = np.full(n, INF, np.int32)
+    cur[s] = 0
+    return cur
+
+
+def test_sweep_hand_example():
+    # 0 -5-> 1 -7-> 2, 3 -1-> 2 with vertex 3 unreached: one double-buffered
+    # round from (0: 0) reaches 1 only; a round that read its own writes
+    # would also reach 2.
+    src, dst, w = [0, 1, 3], [1, 2, 2], [5, 7, 1]
+    cur = _init_state(4, 0)
+    rc, nxt, low = oracle.sweep(4, src, dst, w, cur, cur)
+    assert rc == oracle.OK and nxt.tolist() == [0, 5, INF, INF] and low == 1
+    rc, nxt2, low = oracle.sweep(4, src, dst, w, nxt, nxt)
+    assert rc == oracle.OK and nxt2.tolist() == [0, 5, 12, INF] and low == 1
+    # next below cur is kept; only lower candidates are written
+    rc, nxt3, low = oracle.sweep(4, src, dst, w, nxt2, [0, 3, 20, 9])
+    assert nxt3.tolist() == [0, 3, 12, 9] and low == 1
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_sweep_rounds_vs_hop_limited_brute_force(seed):
+    rng = np.random.Generator(np.random.PCG64(400 + seed))
+    n = int(rng.integers(1, 9))
+    g = gg.random_small(n, int(rng.integers(0, 3 * n + 1)), seed=4000 + seed, wlo=0, whi=9)
+    s = int(rng.integers(0, n))
+    cur = _init_state(n, s)
+    for k in range(1, n + 1):
+        rc, cur, _ = oracle.sweep(n, g.src, g.dst, g.w, cur, cur)
+        assert rc == oracle.OK
+        exp = pins.brute_force_hop_limited(n, g.src.tolist(), g.dst.tolist(), g.w.tolist(), s, k)
+        assert cur.tolist() == [INF if x is None else x for x in exp], k
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_sweep_iterated_reaches_floyd_warshall(seed):
+    g = gg.random_small(40, 160, seed=4100 + seed, wlo=0, whi=20)
+    fw = pins.floyd_warshall(g.n, g.src, g.dst, g.w)
+    cur = _init_state(g.n, 0)
+    sweeps = 0
+    while True:
+        rc, nxt, low = oracle.sweep(g.n, g.src, g.dst, g.w, cur, cur)
+        assert rc == oracle.OK
+        sweeps += 1
+        assert low == int(np.count_nonzero(nxt < cur))
+        cur = nxt
+        if low == 0:
+            break
+    np.testing.assert_array_equal(cur, np.where(fw[0] >= pins.BIG, INF, fw[0]))
+    assert sweeps == pins.sync_rounds_from_distances(g.n, g.src, g.dst, g.w, 0, cur)
+
+
+def test_sweep_overflow_and_errors():
+    big = 2**31 - 1
+    # 0 -> 1 overflows (dropped, status OVERFLOW), 0 -> 2 is still applied
+    rc, nxt, low = oracle.sweep(3, [0, 0], [1, 2], [10, 1], [big - 5, INF, INF], [big - 5, INF, INF])
+    assert rc == oracle.OVERFLOW and nxt.tolist() == [big - 5, INF, big - 4] and low == 1
+    assert oracle.sweep(2, [0], [1], [-1], [0, INF], [0, INF])[0] == oracle.NEGATIVE_WEIGHT
+    assert oracle.sweep(2, [0], [2], [1], [0, INF], [0, INF])[0] == oracle.INVALID
+    rc, nxt, low = oracle.sweep(3, [], [], [], [0, INF, 4], [0, 7, 4])
+    assert rc == oracle.OK and nxt.tolist() == [0, 7, 4] and low == 0
