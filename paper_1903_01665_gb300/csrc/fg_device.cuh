@@ -206,12 +206,15 @@ struct AsyncOp {
         }
         return true;
     }
-    __device__ __forceinline__ int32_t probe(int32_t v) const { return ldcg(D + v); }
+    // Values only decrease, so an L1 copy (possibly stale, never below the
+    // current value) rejects most candidates without an L2 access; the few
+    // it lets through are checked again against L2 before the update.
+    __device__ __forceinline__ int32_t probe(int32_t v) const { return ldca(D + v); }
     // A candidate below the value just read lowers v or loses to an even
     // lower one; either way v has changed in this generation and is queued
     // (once, by the stamp) for the next.
     __device__ __forceinline__ bool commit(int32_t v, int32_t c, int32_t pv, Acc &a) const {
-        if (c < pv) {
+        if (c < pv && c < ldcg(D + v)) {
             red_min(D + v, c);
             a.updates++;
             return atomicExch(stamp + v, gen + 1) != gen + 1;
@@ -235,7 +238,9 @@ struct BfsAsyncOp {
         c = gen + 1;
         return true;
     }
-    __device__ __forceinline__ int32_t probe(int32_t v) const { return ldcg(L + v); }
+    // a level, once claimed, never changes: an L1 copy that shows it set is
+    // exact, one that shows INF may be stale and the CAS decides
+    __device__ __forceinline__ int32_t probe(int32_t v) const { return ldca(L + v); }
     __device__ __forceinline__ bool commit(int32_t v, int32_t c, int32_t pv, Acc &a) const {
         if (pv != kInf) return false;
         if (atomicCAS(L + v, kInf, c) == kInf) {
@@ -278,9 +283,12 @@ struct SweepOp {
         return true;
     }
     __device__ __forceinline__ int32_t probe(int32_t v) const { return ldca(next + v); }
+    // a write per candidate below the probed value: at least the number of
+    // lowered values, at most the number of edges
     __device__ __forceinline__ bool commit(int32_t v, int32_t c, int32_t pv, Acc &a) const {
         if (c < pv) {
-            if (atomicMin(next + v, c) > c) a.updates++;
+            red_min(next + v, c);
+            a.updates++;
         }
         return false;
     }
@@ -715,7 +723,6 @@ __device__ __forceinline__ void lb_expand(const Team &t, const uint32_t *__restr
     __shared__ uint32_t s_rb[kBlock];
     __shared__ int32_t s_val[kBlock];
     __shared__ int s_i0;
-    __shared__ uint32_t s_t1;
     const int G = t.size;
     // exclusive scan of the slice totals, redundantly in every CTA
     {
@@ -761,10 +768,13 @@ __device__ __forceinline__ void lb_expand(const Team &t, const uint32_t *__restr
         s_i0 = l;
     }
     __syncthreads();
+    // A window of up to kBlock items -- their global edge offsets, row starts
+    // and values -- is staged once and serves every 1024-edge sub-tile of
+    // the CTA's range that falls inside it.
     uint32_t t0 = (uint32_t)lo;
     while (t0 < (uint32_t)hi) {
-        int i0 = s_i0;
-        int cnt = min(kBlock, n_items - i0);
+        const int i0 = s_i0;
+        const int cnt = min(kBlock, n_items - i0);
         bool rq = false;
         int32_t u = 0;
         if ((int)threadIdx.x < cnt) {
@@ -779,80 +789,96 @@ __device__ __forceinline__ void lb_expand(const Team &t, const uint32_t *__restr
         push(rq, u, a);
         if (threadIdx.x == 0) s_goff[cnt] = (i0 + cnt < n_items) ? goff(i0 + cnt) : T;
         __syncthreads();
-        uint32_t t1 = min((uint32_t)hi, min(t0 + (uint32_t)(kBlock * kU), s_goff[cnt]));
-        uint32_t e[kU];
-        int32_t val[kU];
-        bool in[kU];
+        const uint32_t wend = min((uint32_t)hi, s_goff[cnt]);   // the window's edges end here
+        while (t0 < wend) {
+            const uint32_t t1 = min(wend, t0 + (uint32_t)(kBlock * kU));
+            uint32_t e[kU];
+            int32_t val[kU];
+            bool in[kU];
+            int l = 0;   // owners are non-decreasing in j: each search starts at the last one
 #pragma unroll
-        for (int j = 0; j < kU; j++) {
-            uint32_t x = t0 + j * kBlock + threadIdx.x;
-            in[j] = x < t1;
-            e[j] = 0;
-            val[j] = 0;
-            if (in[j]) {
-                int l = 0, r = cnt - 1;
-                while (l < r) {
-                    int mdl = (l + r + 1) >> 1;
-                    if (s_goff[mdl] <= x) l = mdl; else r = mdl - 1;
+            for (int j = 0; j < kU; j++) {
+                uint32_t x = t0 + j * kBlock + threadIdx.x;
+                in[j] = x < t1;
+                e[j] = 0;
+                val[j] = 0;
+                if (in[j]) {
+                    int r = cnt - 1;
+                    while (l < r) {
+                        int mdl = (l + r + 1) >> 1;
+                        if (s_goff[mdl] <= x) l = mdl; else r = mdl - 1;
+                    }
+                    e[j] = s_rb[l] + (x - s_goff[l]);
+                    val[j] = s_val[l];
+                    a.edges++;
                 }
-                e[j] = s_rb[l] + (x - s_goff[l]);
-                val[j] = s_val[l];
-                a.edges++;
             }
+            relax_batch(col, op, push, e, val, in, a);
+            t0 = t1;
         }
-        relax_batch(col, op, push, e, val, in, a);
         if (threadIdx.x == 0) {
-            // next tile starts at edge t1; find its item among the staged ones
-            int l = 0, r = cnt;   // s_goff[cnt] may equal t1 (then item i0 + cnt)
+            // the next window starts with the item holding edge t0
+            int l = 0, r = cnt;   // s_goff[cnt] may equal t0 (then item i0 + cnt)
             while (l < r) {
                 int mdl = (l + r + 1) >> 1;
-                if (s_goff[mdl] <= t1) l = mdl; else r = mdl - 1;
+                if (s_goff[mdl] <= t0) l = mdl; else r = mdl - 1;
             }
             s_i0 = i0 + l;
-            s_t1 = t1;
         }
-        __syncthreads();
-        t0 = s_t1;
         __syncthreads();
     }
 }
 
 // ================================================================ sparse edge-sync rounds
-// A round of the synchronous edge mode normally streams every edge's source.
-// When the previous round changed few vertices the round is "sparse": a
-// flag pass first marks the 1024-edge chunks whose sources include an active
-// vertex (from the activity words of 256-vertex groups), and only those
-// chunks are streamed.  The choice is made identically by every CTA.
+// A round of the synchronous edge mode normally streams every edge.  When the
+// previous round changed few vertices the round is "sparse": a flag pass
+// first stamps every 128-edge warp tile that holds an out-edge of an active
+// vertex, and only those tiles are streamed.  The choice is made identically
+// by every CTA.
 
-// Flag pass: one warp per 256-vertex group; if any vertex of the group is
-// active (activity word == act_val), flag the edge chunks holding the
-// group's out-edges with `round`.
-__device__ __forceinline__ void flag_edge_chunks(const Team &t, const uint32_t *__restrict__ row_off, const int32_t *actw,
-                                                 int32_t act_val, int32_t n, int32_t *eflag, int32_t round,
-                                                 Acc &a) {
+// Flag pass: a warp tests 128 consecutive vertices per step (128-bit loads of
+// the activity word); each active vertex stamps the warp tiles of its edge
+// range [row_off[v], row_off[v+1]) with `round`, a long range (more than 8
+// tiles) by the whole warp.
+__device__ __forceinline__ void flag_edge_tiles(const Team &t, const uint32_t *__restrict__ row_off, const int32_t *actw,
+                                                int32_t act_val, int32_t n, int32_t *eflag, int32_t round, Acc &a) {
     const unsigned lane = lane_id();
     const int64_t gw = (t.rank * (int64_t)kBlock + threadIdx.x) >> 5;
     const int64_t nw = (int64_t)t.size * kWarps;
-    const int64_t ngr = ((int64_t)n + kVGroup - 1) >> kVGroupLog;
-    for (int64_t gi = gw; gi < ngr; gi += nw) {
-        const int64_t vlo = gi << kVGroupLog, vhi = min((int64_t)n, vlo + kVGroup);
-        bool any = false;
+    for (int64_t v0 = gw * 128; v0 < n; v0 += nw * 128) {
+        const int64_t vb = v0 + 4 * lane;
+        bool act[4] = {false, false, false, false};
+        if (vb + 3 < n) {
+            const int4 w4 = __ldcg(reinterpret_cast<const int4 *>(actw + vb));
+            act[0] = w4.x == act_val; act[1] = w4.y == act_val; act[2] = w4.z == act_val; act[3] = w4.w == act_val;
+        } else {
 #pragma unroll
-        for (int h = 0; h < kVGroup / 128; h++) {
-            const int64_t v0 = vlo + 128 * h + 4 * lane;
-            if (v0 + 3 < vhi) {
-                int4 t = __ldcg(reinterpret_cast<const int4 *>(actw + v0));
-                any |= (t.x == act_val) | (t.y == act_val) | (t.z == act_val) | (t.w == act_val);
-            } else {
-                for (int j = 0; j < 4; j++)
-                    if (v0 + j < vhi) any |= ldcg(actw + v0 + j) == act_val;
+            for (int j = 0; j < 4; j++) act[j] = vb + j < n && ldcg(actw + vb + j) == act_val;
+        }
+        if (lane == 0) a.scanned += (uint64_t)min((int64_t)128, (int64_t)n - v0);
+        uint32_t big_t0 = 0, big_t1 = 0;
+        bool big = false;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if (!act[j]) continue;
+            const uint32_t rb = __ldg(row_off + vb + j), re = __ldg(row_off + vb + j + 1);
+            if (re <= rb) continue;
+            const uint32_t t0 = rb / kWTile, t1 = (re - 1) / kWTile;
+            if (t1 - t0 < 8) {
+                for (uint32_t k = t0; k <= t1; k++) stcg(eflag + k, round);
+            } else if (!big) {
+                big = true;
+                big_t0 = t0;
+                big_t1 = t1;
+            } else {   // a second long range of the same lane (rare): alone
+                for (uint32_t k = t0; k <= t1; k++) stcg(eflag + k, round);
             }
         }
-        if (lane == 0) a.scanned += vhi - vlo;
-        if (!__any_sync(0xffffffffu, any)) continue;
-        const uint32_t eb = __ldg(row_off + vlo), ee = __ldg(row_off + vhi);
-        if (ee > eb)
-            for (uint32_t k = (eb >> kEChunkLog) + lane; k <= (ee - 1) >> kEChunkLog; k += 32) stcg(eflag + k, round);
+        for (unsigned m = __ballot_sync(0xffffffffu, big); m; m &= m - 1) {
+            const int src = __ffs(m) - 1;
+            const uint32_t t0 = __shfl_sync(0xffffffffu, big_t0, src), t1 = __shfl_sync(0xffffffffu, big_t1, src);
+            for (uint32_t k = t0 + lane; k <= t1; k += 32) stcg(eflag + k, round);
+        }
     }
 }
 
@@ -874,9 +900,7 @@ __device__ __forceinline__ void flag_edge_chunks(const Team &t, const uint32_t *
 #ifndef FG_EDGE_STAGES
 #define FG_EDGE_STAGES 2
 #endif
-constexpr int kWTile = 128;             // edges per warp tile (4 per lane)
-constexpr int kWStages = FG_EDGE_STAGES;
-constexpr int kWTilesPerChunk = kEChunk / kWTile;
+constexpr int kWStages = FG_EDGE_STAGES;   // buffers per warp; a warp tile is kWTile = 128 edges (4 per lane)
 
 template <bool W>
 struct __align__(16) WarpStage {
@@ -1095,31 +1119,40 @@ __device__ __forceinline__ bool stream_all_edges(const Team &t, uint32_t &used, 
     return __syncthreads_and(ok);
 }
 
-// Sparse synchronous edge round: the 1024-edge chunks flagged by
-// flag_edge_chunks, dealt round-robin to the CTAs, 256 flags tested at once;
-// warp w of the CTA streams warp tile w of every flagged chunk.
+// Sparse synchronous edge round: each warp tests its share of the warp tiles
+// (tiles gw, gw + nw, ...) 128 at a time, lists the flagged ones in shared
+// memory and streams them.
 template <bool W, class OP>
 __device__ __forceinline__ bool stream_flagged_edges(const Team &t, uint32_t &used, const View &g,
                                                      const int32_t *eflag, int32_t round, const OP &op, Acc &a,
                                                      Ctrl *c, unsigned long long timeout_ns) {
-    __shared__ int32_t s_klist[kBlock];
-    __shared__ int s_kn;
+    __shared__ int32_t s_wl[kWarps][128];
     EdgeRings<W> &R = edge_rings<W>();
-    const int64_t nec = (g.m + kEChunk - 1) >> kEChunkLog;
-    const int64_t G = t.size;
     const int wid = threadIdx.x >> 5;
+    const unsigned lane = lane_id();
+    const int64_t ntiles = (g.m + kWTile - 1) / kWTile;
+    const int64_t gw = (int64_t)t.rank * kWarps + wid, nw = (int64_t)t.size * kWarps;
     bool ok = true;
-    for (int64_t base = t.rank; base < nec; base += G * kBlock) {
-        const int64_t k = base + (int64_t)threadIdx.x * G;
-        const bool act = k < nec && ldcg(eflag + k) == round;
-        const int na = block_compact(act, (int32_t)k, s_klist, &s_kn);
-        if (threadIdx.x == 0)
-            for (int i = 0; i < na; i++) a.scanned += (uint64_t)min((int64_t)kEChunk, g.m - ((int64_t)s_klist[i] << kEChunkLog));
-        ok = warp_stream(R.warp[wid], R.pol, used, na,
-                         [&](int i) { return (int64_t)s_klist[i] * kWTilesPerChunk + wid; }, g, op, a, c, timeout_ns);
-        if (!__syncthreads_and(ok)) return false;
+    for (int64_t k0 = 0; gw + k0 * nw < ntiles && ok; k0 += 128) {
+        int na = 0;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int64_t tile = gw + (k0 + 32 * j + lane) * nw;
+            const bool f = tile < ntiles && ldcg(eflag + tile) == round;
+            const unsigned bal = __ballot_sync(0xffffffffu, f);
+            if (f) s_wl[wid][na + __popc(bal & lanemask_lt())] = (int32_t)tile;
+            na += __popc(bal);
+        }
+        __syncwarp();
+        if (lane == 0)
+            for (int i = 0; i < na; i++) {
+                const int64_t e0 = (int64_t)s_wl[wid][i] * kWTile;
+                a.scanned += (uint64_t)min((int64_t)kWTile, g.m - e0);
+            }
+        ok = warp_stream(R.warp[wid], R.pol, used, na, [&](int i) { return (int64_t)s_wl[wid][i]; }, g, op, a, c,
+                         timeout_ns);
     }
-    return true;
+    return __syncthreads_and(ok);
 }
 
 // ================================================================ the kernel
@@ -1131,6 +1164,9 @@ __device__ __forceinline__ bool stream_flagged_edges(const Team &t, uint32_t &us
 #endif
 #ifndef FG_ASYNC_MIN_BLOCKS
 #define FG_ASYNC_MIN_BLOCKS 4
+#endif
+#ifndef FG_SPARSE_SHIFT
+#define FG_SPARSE_SHIFT 3
 #endif
 #ifndef FG_EDGE_SYNC_MIN_BLOCKS
 #define FG_EDGE_SYNC_MIN_BLOCKS 4
@@ -1187,7 +1223,7 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
         if (!SYNC && ALGO != kBFS) p.S0[v] = 0;
     }
     if (MODE == kEdgeSync)
-        for (int64_t k = tid; k < ((g.m + kEChunk - 1) >> kEChunkLog); k += nth) p.eflag[k] = 0;
+        for (int64_t k = tid; k < (g.m + kWTile - 1) / kWTile; k += nth) p.eflag[k] = 0;
 
     if (!SYNC && ALGO != kCC && tid == 0) {
         int32_t s = p.source;
@@ -1218,10 +1254,11 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
         int pass_ctr = 0;
         constexpr bool kW = (ALGO == kSSSP);   // the edge rings carry weights for SSSP only
         // edge-sync: a round is sparse if the previous one accepted fewer
-        // candidates than n/8 (round 1: only the source is active, except CC)
+        // candidates than n / 2^FG_SPARSE_SHIFT (round 1: only the source is
+        // active, except CC)
         auto sparse_round = [&](int r) -> bool {
             if (r == 1) return ALGO != kCC;
-            return (int64_t)__ldcg(&c->changed[(r - 1) % 3]) * 8 < (int64_t)n;
+            return ((int64_t)__ldcg(&c->changed[(r - 1) % 3]) << FG_SPARSE_SHIFT) < (int64_t)n;
         };
         for (int r = 1;; r++) {
             if (r > p.max_rounds) {
@@ -1237,7 +1274,7 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
                                     NoPush{}, a);
                     expand_low_dense(t, g.row_off, g.col, p.A, r - 1, n, op, a);
                 } else if (sparse_round(r)) {
-                    flag_edge_chunks(t, g.row_off, p.A, r - 1, n, p.eflag, r, a);
+                    flag_edge_tiles(t, g.row_off, p.A, r - 1, n, p.eflag, r, a);
                     if (!sync_()) break;
                     if (!stream_flagged_edges<kW>(t, ring_used, g, p.eflag, r, op, a, c, p.timeout_ns)) break;
                 } else {
@@ -1254,7 +1291,7 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
                                     NoPush{}, a);
                     expand_low_dense(t, g.row_off, g.col, scur, r, n, op, a);
                 } else if (sparse_round(r)) {
-                    flag_edge_chunks(t, g.row_off, scur, r, n, p.eflag, r, a);
+                    flag_edge_tiles(t, g.row_off, scur, r, n, p.eflag, r, a);
                     if (!sync_()) break;
                     if (!stream_flagged_edges<kW>(t, ring_used, g, p.eflag, r, op, a, c, p.timeout_ns)) break;
                 } else {

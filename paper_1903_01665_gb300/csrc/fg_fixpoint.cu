@@ -115,8 +115,8 @@ size_t query_workspace_bytes(const View &g, Algo algo, Mode mode) {
     const bool sync = (mode == kVertexSync || mode == kEdgeSync);
     size_t need = Workspace::need(1, sizeof(Ctrl)) + Workspace::need(n, 4);
     if (sync && algo != kBFS) need += 3 * Workspace::need(n, 4);
-    const int64_t nec = (g.m + kEChunk - 1) >> kEChunkLog;
-    if (mode == kEdgeSync) need += Workspace::need(nec, 4);
+    const int64_t nwt = (g.m + kWTile - 1) / kWTile;   // edge-sync: one flag per 128-edge warp tile
+    if (mode == kEdgeSync) need += Workspace::need(nwt, 4);
     if (!sync) {
         if (algo != kBFS) need += Workspace::need(n, 4);
         for (int k = 0; k < 3; k++) need += 2 * Workspace::need(wl_cap_of(g, mode, k), 4);
@@ -131,7 +131,7 @@ void carve_query_workspace(char *base, const View &g, Algo algo, Mode mode, Para
     ws.base = base;
     const int32_t n = g.n;
     const bool sync = (mode == kVertexSync || mode == kEdgeSync);
-    const int64_t nec = (g.m + kEChunk - 1) >> kEChunkLog;
+    const int64_t nwt = (g.m + kWTile - 1) / kWTile;
     p.g = g;
     p.ctrl = ws.take<Ctrl>(1);
     p.A = ws.take<int32_t>(n);
@@ -140,7 +140,7 @@ void carve_query_workspace(char *base, const View &g, Algo algo, Mode mode, Para
         p.S0 = ws.take<int32_t>(n);
         p.S1 = ws.take<int32_t>(n);
     }
-    if (mode == kEdgeSync) p.eflag = ws.take<int32_t>(nec);
+    if (mode == kEdgeSync) p.eflag = ws.take<int32_t>(nwt);
     if (!sync) {
         if (algo != kBFS) p.S0 = ws.take<int32_t>(n);
         for (int par = 0; par < 2; par++)

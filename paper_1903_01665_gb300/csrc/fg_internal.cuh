@@ -20,8 +20,7 @@ constexpr int kLowMax = 32;            // low bucket: 1 .. 31 out-edges (thread 
 constexpr int kMidMax = 1024;          // mid bucket: 32 .. 1023 (warp per vertex)
 constexpr int kChunk = 2048;           // high bucket: >= 1024, split in 2048-edge chunks (CTA each)
 constexpr int32_t kInf = FG_INF;
-constexpr int kVGroupLog = 8, kVGroup = 1 << kVGroupLog;    // edge-sync: vertices per activity group
-constexpr int kEChunkLog = 10, kEChunk = 1 << kEChunkLog;   // edge-sync: edges per streamed chunk
+constexpr int kWTile = 128;            // edge-sync: edges per warp tile (the streamed and flagged unit)
 
 // device status bits (Ctrl::status)
 constexpr int kStTimeout = 1;          // a grid barrier wait ran out
@@ -98,7 +97,7 @@ struct Params {
     int32_t wl_cap[3] = {};     // capacity per class (in int32 slots)
     uint32_t *lb_off = nullptr; // edge-async: per-item local offsets
     uint32_t *lb_blk = nullptr; // edge-async: per-CTA totals
-    int32_t *eflag = nullptr;   // edge-sync sparse rounds: round stamp per 1024-edge chunk
+    int32_t *eflag = nullptr;   // edge-sync sparse rounds: round stamp per 128-edge warp tile
     int32_t source = 0;
     int32_t max_rounds = 0;
     unsigned long long timeout_ns = 0;
