@@ -15,9 +15,20 @@
  *   FG_VERTEX_ASYNC data-driven (Sec. 3.3): a device worklist of vertices,
  *                   in-place atomic MIN, run until the worklist is empty;
  *   FG_EDGE_ASYNC   the same worklist expanded to its out-edges and relaxed
- *                   edge-parallel, in place.
+ *                   edge-parallel, in place;
  *
- * All four reach the same unique fixpoint, so their outputs are identical.
+ * and a fifth built on the paper's in-neighbour iterator (innbrs, Sec. 2):
+ *
+ *   FG_PULL         vertex-based, double-buffered, direction-optimising: a
+ *                   round in which many vertices changed pulls over the
+ *                   in-neighbours (SSSP/CC: each vertex takes the minimum of
+ *                   its in-neighbours' candidates, no atomics; BFS bottom-up:
+ *                   an unvisited vertex stops at its first in-neighbour on
+ *                   the frontier), the other rounds push as FG_VERTEX_SYNC.
+ *                   The transposed CSR it reads is built on the first pull
+ *                   query of a graph and kept with it (about 8 bytes per edge).
+ *
+ * All reach the same unique fixpoint, so their outputs are identical.
  *
  * Conventions for every call:
  *   - Ids, weights, distances, levels and labels are int32.  "Unreached" is
@@ -66,7 +77,8 @@ typedef enum {
     FG_VERTEX_ASYNC = 1,
     FG_EDGE_SYNC = 2,
     FG_EDGE_ASYNC = 3,
-    FG_AUTO = 4                 /* the mode fg_select_mode picks */
+    FG_AUTO = 4,                /* the mode fg_select_mode picks */
+    FG_PULL = 5
 } fg_mode;
 
 typedef enum { FG_ALGO_SSSP = 0, FG_ALGO_BFS = 1, FG_ALGO_CC = 2 } fg_algo;
@@ -170,6 +182,8 @@ typedef struct {
                                    the query's stream) */
     int32_t barriers;           /* grid barriers the kernel passed (= trace entries written,
                                    up to the cap) */
+    int32_t pull_rounds;        /* FG_PULL: rounds that pulled over the in-neighbours */
+    int64_t edges_pulled;       /* FG_PULL: in-edges read by those rounds */
 } fg_stats;
 
 /*
@@ -319,10 +333,12 @@ fg_status fg_server_drain(fg_server *s, int32_t timeout_ms);
 fg_status fg_server_destroy(fg_server *s);
 
 /*
- * Autotuner: times the four modes on this graph (one query each from src,
- * ignored for CC), writes their device times in ms to times_ms[4] (may be
- * NULL) and the fastest mode to *best, and caches it on the handle:
- * fg_select_mode (and FG_AUTO) return the cached choice from then on.
+ * Autotuner: times the candidate modes on this graph (one query each from
+ * src, ignored for CC) -- the four paper modes, and FG_PULL for BFS, whose
+ * bottom-up levels lower the total work -- writes their device times in ms to
+ * times_ms[6] indexed by mode (0 for a mode not timed, and for FG_AUTO;
+ * times_ms may be NULL) and the fastest mode to *best, and caches it on the
+ * handle: fg_select_mode (and FG_AUTO) return the cached choice from then on.
  */
 fg_status fg_autotune(const fg_graph *g, fg_algo algo, int32_t src, fg_mode *best, float *times_ms);
 

@@ -32,7 +32,8 @@ FG_VERTEX_ASYNC = 1
 FG_EDGE_SYNC = 2
 FG_EDGE_ASYNC = 3
 FG_AUTO = 4
-MODES = {"vertex_sync": 0, "vertex_async": 1, "edge_sync": 2, "edge_async": 3, "auto": 4}
+FG_PULL = 5
+MODES = {"vertex_sync": 0, "vertex_async": 1, "edge_sync": 2, "edge_async": 3, "auto": 4, "pull": 5}
 MODE_NAMES = {v: k for k, v in MODES.items()}
 # algorithms
 FG_ALGO_SSSP = 0
@@ -53,7 +54,7 @@ class fg_stats(ctypes.Structure):
                 ("grid_blocks", ctypes.c_int32), ("vertices_processed", ctypes.c_int64),
                 ("edges_relaxed", ctypes.c_int64), ("updates", ctypes.c_int64),
                 ("pushes", ctypes.c_int64), ("scanned", ctypes.c_int64), ("kernel_ms", ctypes.c_float),
-                ("barriers", ctypes.c_int32)]
+                ("barriers", ctypes.c_int32), ("pull_rounds", ctypes.c_int32), ("edges_pulled", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -283,9 +284,9 @@ def fg_run_batch(queries, stream=None, use_cuda_graph=False, wait_timeout_ms=0):
 
 
 def fg_autotune(g, algo, src=0):
-    """Returns (status, best mode, [ms per mode])."""
+    """Returns (status, best mode, [ms per mode, indexed by mode; index FG_AUTO unused])."""
     best = ctypes.c_int(-1)
-    times = (ctypes.c_float * 4)()
+    times = (ctypes.c_float * 6)()
     st = load().fg_autotune(g, int(algo), int(src), ctypes.byref(best), times)
     return st, best.value, list(times)
 

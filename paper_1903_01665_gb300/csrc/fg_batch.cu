@@ -51,20 +51,24 @@ __global__ void __launch_bounds__(kBlock, min_blocks<MODE>()) batch_kernel(Batch
 
 using BatchFn = void (*)(BatchArgs);
 
+// kind = algo * 8 + mode
 BatchFn batch_kernel_for(int kind) {
     switch (kind) {
-        case kSSSP * 4 + kVertexSync: return batch_kernel<kSSSP, kVertexSync>;
-        case kSSSP * 4 + kVertexAsync: return batch_kernel<kSSSP, kVertexAsync>;
-        case kSSSP * 4 + kEdgeSync: return batch_kernel<kSSSP, kEdgeSync>;
-        case kSSSP * 4 + kEdgeAsync: return batch_kernel<kSSSP, kEdgeAsync>;
-        case kBFS * 4 + kVertexSync: return batch_kernel<kBFS, kVertexSync>;
-        case kBFS * 4 + kVertexAsync: return batch_kernel<kBFS, kVertexAsync>;
-        case kBFS * 4 + kEdgeSync: return batch_kernel<kBFS, kEdgeSync>;
-        case kBFS * 4 + kEdgeAsync: return batch_kernel<kBFS, kEdgeAsync>;
-        case kCC * 4 + kVertexSync: return batch_kernel<kCC, kVertexSync>;
-        case kCC * 4 + kVertexAsync: return batch_kernel<kCC, kVertexAsync>;
-        case kCC * 4 + kEdgeSync: return batch_kernel<kCC, kEdgeSync>;
-        case kCC * 4 + kEdgeAsync: return batch_kernel<kCC, kEdgeAsync>;
+        case kSSSP * 8 + kVertexSync: return batch_kernel<kSSSP, kVertexSync>;
+        case kSSSP * 8 + kVertexAsync: return batch_kernel<kSSSP, kVertexAsync>;
+        case kSSSP * 8 + kEdgeSync: return batch_kernel<kSSSP, kEdgeSync>;
+        case kSSSP * 8 + kEdgeAsync: return batch_kernel<kSSSP, kEdgeAsync>;
+        case kBFS * 8 + kVertexSync: return batch_kernel<kBFS, kVertexSync>;
+        case kBFS * 8 + kVertexAsync: return batch_kernel<kBFS, kVertexAsync>;
+        case kBFS * 8 + kEdgeSync: return batch_kernel<kBFS, kEdgeSync>;
+        case kBFS * 8 + kEdgeAsync: return batch_kernel<kBFS, kEdgeAsync>;
+        case kCC * 8 + kVertexSync: return batch_kernel<kCC, kVertexSync>;
+        case kCC * 8 + kVertexAsync: return batch_kernel<kCC, kVertexAsync>;
+        case kCC * 8 + kEdgeSync: return batch_kernel<kCC, kEdgeSync>;
+        case kCC * 8 + kEdgeAsync: return batch_kernel<kCC, kEdgeAsync>;
+        case kSSSP * 8 + kPull: return batch_kernel<kSSSP, kPull>;
+        case kBFS * 8 + kPull: return batch_kernel<kBFS, kPull>;
+        case kCC * 8 + kPull: return batch_kernel<kCC, kPull>;
     }
     return nullptr;
 }
@@ -128,8 +132,12 @@ fg_status batch_launch(const fg_query *qs, int32_t nq, const fg_batch_options *o
         }
         mode[i] = (Mode)m;
         view[i] = (q.algo == FG_ALGO_CC) ? &q.g->s : &q.g->g;
-        KindPlan &kp = kinds[q.algo * 4 + (int)m];
-        kp.kind = q.algo * 4 + (int)m;
+        if (m == FG_PULL && q.algo != FG_ALGO_CC) {
+            fg_status s = ensure_transpose(q.g);
+            if (s != FG_OK) return s;
+        }
+        KindPlan &kp = kinds[q.algo * 8 + (int)m];
+        kp.kind = q.algo * 8 + (int)m;
         kp.queries.push_back(i);
         double w = work_of(q.algo, *view[i]);
         kp.work += w;
@@ -229,6 +237,7 @@ fg_status batch_launch(const fg_query *qs, int32_t nq, const fg_batch_options *o
         qw.off += query_workspace_bytes(*view[i], (Algo)qs[i].algo, mode[i]);
         Params p;
         carve_query_workspace(w, *view[i], (Algo)qs[i].algo, mode[i], p);
+        if (mode[i] == kPull) p.tv = (qs[i].algo == FG_ALGO_CC) ? qs[i].g->s : qs[i].g->t;
         p.ctrl = job.d_ctrls + i;
         p.source = qs[i].algo == FG_ALGO_CC ? 0 : qs[i].src;
         p.max_rounds = view[i]->n > INT32_MAX - 2 ? INT32_MAX : view[i]->n + 2;
@@ -408,6 +417,8 @@ fg_status batch_finish(BatchJob &job, fg_status *status_out, fg_stats *stats_out
             s.pushes = (int64_t)hc.st_pushes;
             s.scanned = (int64_t)hc.st_scanned;
             s.barriers = hc.barriers;
+            s.pull_rounds = hc.pull_rounds;
+            s.edges_pulled = (int64_t)hc.st_pulled;
         }
     }
     if (job.status != FG_OK && status_out)

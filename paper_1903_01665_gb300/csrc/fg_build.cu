@@ -80,6 +80,17 @@ __global__ void k_scatter_coo(int64_t m, const int32_t *__restrict__ s, const in
     }
 }
 
+// Transposed CSR: every edge u->v stored at v's in-edge list as (u, w).
+__global__ void k_scatter_transpose(int64_t m, const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                                    const int32_t *__restrict__ w, uint32_t *cursor, int32_t *tcol, int32_t *tw) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t pos = atomicAdd(&cursor[dst[e]], 1u);
+        tcol[pos] = src[e];
+        tw[pos] = w[e];
+    }
+}
+
 __global__ void k_offsets_to_u32(int32_t n, const int64_t *__restrict__ ro, uint32_t *out) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v <= n;
          v += (int64_t)gridDim.x * blockDim.x)
@@ -524,6 +535,46 @@ fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const i
     I.n_high_chunks = v.n_high_chunks;
     I.n_isolated = s.n_zero;
     *out = g;
+    return FG_OK;
+}
+
+// The transposed view of the directed graph (in-neighbours with their
+// weights, bucketed by in-degree), built once on the first pull query and
+// kept with the graph.  Thread-safe: callers hold no lock.
+fg_status ensure_transpose(const fg_graph *cg) {
+    fg_graph *g = const_cast<fg_graph *>(cg);
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (g->t_ready) return FG_OK;
+    const View &v = g->g;
+    const int32_t n = v.n;
+    const int64_t m = v.m;
+    Builder b{g, (cudaStream_t)0};
+    uint32_t *tro = b.alloc_graph<uint32_t>((int64_t)n + 1);
+    int32_t *tcol = b.alloc_graph<int32_t>(m);
+    int32_t *tw = b.alloc_graph<int32_t>(m);
+    uint32_t *cnt = b.alloc_tmp<uint32_t>(n);
+    uint32_t *cursor = b.alloc_tmp<uint32_t>((int64_t)n + 1);
+    if (b.status == FG_OK) {
+        b.check(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(uint32_t), b.st), "memset");
+        if (m > 0) { k_histogram<<<grid_for(m), kBlock, 0, b.st>>>(m, v.col, cnt); count_launch(); }
+        b.check(exclusive_scan(cnt, tro, n, b.st), "scan");
+        b.check(cudaMemcpyAsync(cursor, tro, ((size_t)n + 1) * sizeof(uint32_t), cudaMemcpyDeviceToDevice, b.st), "copy");
+        if (m > 0) { k_scatter_transpose<<<grid_for(m), kBlock, 0, b.st>>>(m, v.src, v.col, v.w, cursor, tcol, tw); count_launch(); }
+        b.check(cudaGetLastError(), "transpose");
+    }
+    if (cnt) cudaFreeAsync(cnt, b.st);
+    if (cursor) cudaFreeAsync(cursor, b.st);
+    View t;
+    t.n = n;
+    t.m = m;
+    t.row_off = tro;
+    t.col = tcol;
+    t.w = tw;
+    if (b.status == FG_OK) make_buckets(b, t);
+    b.check(cudaStreamSynchronize(b.st), "transpose build");
+    if (b.status != FG_OK) return fail(b.status, b.msg);
+    g->t = t;
+    g->t_ready = true;
     return FG_OK;
 }
 

@@ -76,7 +76,7 @@ using namespace fg;
 namespace {
 
 fg_status check_mode(fg_mode m) {
-    if (m < FG_VERTEX_SYNC || m > FG_AUTO) return fail(FG_ERR_INVALID_ARG, "invalid mode");
+    if (m < FG_VERTEX_SYNC || m > FG_PULL) return fail(FG_ERR_INVALID_ARG, "invalid mode");
     return FG_OK;
 }
 
@@ -246,25 +246,31 @@ fg_status fg_autotune(const fg_graph *g, fg_algo algo, int32_t src, fg_mode *bes
     int32_t *out = nullptr;
     cudaError_t e = cudaMalloc(&out, (size_t)g->info.n * sizeof(int32_t));
     if (e != cudaSuccess) return cuda_fail(e, "autotune workspace");
-    float t[4];
+    // FG_PULL is a candidate for BFS only: its bottom-up levels stop each
+    // vertex at the first parent and so lower the total work, whereas SSSP
+    // and CC pull rounds read every in-edge -- no faster alone, and slower
+    // where queries share the device (a batch pays for total work)
+    float t[6] = {0, 0, 0, 0, 0, 0};
+    const int modes[5] = {kVertexSync, kVertexAsync, kEdgeSync, kEdgeAsync, kPull};
+    const int nmodes = algo == FG_ALGO_BFS ? 5 : 4;
     fg_status s = FG_OK;
-    for (int m = 0; m < 4 && s == FG_OK; m++) {
+    for (int i = 0; i < nmodes && s == FG_OK; i++) {
         fg_stats st{};
-        s = run_query(g, (Algo)algo, (Mode)m, src, out, nullptr, &st);
-        t[m] = st.kernel_ms;
+        s = run_query(g, (Algo)algo, (Mode)modes[i], src, out, nullptr, &st);
+        t[modes[i]] = st.kernel_ms;
     }
     cudaFree(out);
     if (s != FG_OK) return s;
     int bm = 0;
-    for (int m = 1; m < 4; m++)
-        if (t[m] < t[bm]) bm = m;
+    for (int i = 1; i < nmodes; i++)
+        if (t[modes[i]] < t[bm]) bm = modes[i];
     {
         std::lock_guard<std::mutex> lk(g->mu);
         g->tuned_mode[algo] = bm;
     }
     *best = (fg_mode)bm;
     if (times_ms)
-        for (int m = 0; m < 4; m++) times_ms[m] = t[m];
+        for (int m = 0; m < 6; m++) times_ms[m] = t[m];
     return FG_OK;
 }
 
@@ -278,7 +284,7 @@ fg_status fg_run_batch(const fg_query *queries, int32_t nq, const fg_batch_optio
         if (!q.g) return fail(FG_ERR_INVALID_ARG, where + "graph is NULL");
         if (!q.out) return fail(FG_ERR_INVALID_ARG, where + "output buffer is NULL");
         if (q.algo < FG_ALGO_SSSP || q.algo > FG_ALGO_CC) return fail(FG_ERR_INVALID_ARG, where + "invalid algorithm");
-        if (q.mode < FG_VERTEX_SYNC || q.mode > FG_AUTO) return fail(FG_ERR_INVALID_ARG, where + "invalid mode");
+        if (q.mode < FG_VERTEX_SYNC || q.mode > FG_PULL) return fail(FG_ERR_INVALID_ARG, where + "invalid mode");
         if (q.algo != FG_ALGO_CC && (q.src < 0 || q.src >= q.g->info.n))
             return fail(FG_ERR_INVALID_ARG, where + "source vertex outside [0, n)");
     }

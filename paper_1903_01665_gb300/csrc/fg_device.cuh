@@ -35,10 +35,29 @@ namespace {
 
 
 struct Acc {
-    unsigned long long edges = 0, verts = 0, updates = 0, pushes = 0, scanned = 0;
+    unsigned long long edges = 0, verts = 0, updates = 0, pushes = 0, scanned = 0, pulled = 0;
     int changed = 0;
     int overflow = 0;
 };
+
+__device__ __forceinline__ int32_t warp_min(int32_t x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+// minimum over the CTA, returned to every thread
+__device__ __forceinline__ int32_t block_min(int32_t x) {
+    __shared__ int32_t sh[kWarps];
+    x = warp_min(x);
+    if (lane_id() == 0) sh[threadIdx.x >> 5] = x;
+    __syncthreads();
+    int32_t r = sh[0];
+#pragma unroll
+    for (int i = 1; i < kWarps; i++) r = min(r, sh[i]);
+    __syncthreads();
+    return r;
+}
 
 template <typename T>
 __device__ __forceinline__ T block_sum(T x) {
@@ -829,6 +848,209 @@ __device__ __forceinline__ void lb_expand(const Team &t, const uint32_t *__restr
     }
 }
 
+// ================================================================ pull rounds
+// The in-neighbour iterator (innbrs): a pull round visits every vertex with
+// in-edges over the transposed CSR, bucketed by in-degree like the push side
+// (low: a warp's 32 vertices with their in-edges spread over its lanes and
+// combined by shared-memory atomics; mid: a warp per vertex; high: a CTA per
+// 2048-edge chunk).  An op reduces its in-edges' candidates by minimum:
+//   skip(v)          -- nothing to pull for v (BFS: already visited)
+//   weight(e)        -- in-edge e's weight (loaded with the in-neighbour id)
+//   cand(u, wv, a)   -- the candidate of an in-edge from u of weight wv (kInf: none)
+//   finish(v, m, a)  -- the only writer of v applies the minimum m
+//   finish_part(v, m, first, a) -- one of several chunks of v applies its m
+//   kEarly           -- a candidate of 0 ends v's scan (BFS: a parent found)
+
+// SSSP / CC pull round r: next[v] = min(cur[v], min over in-edges (u, w) of
+// cur[u] + w) -- Alg. 1's MIN gathered at the target, so no atomics except
+// where a hub's chunks meet.  cur is the previous round's and is read through
+// L1.  next may hold an older (larger) value: a single writer overwrites it,
+// and the chunk holding a hub's first in-edge includes cur[v] in its MIN.
+template <int ALGO>
+struct PullMinOp {
+    const int32_t *__restrict__ w;   // in-edge weights (SSSP)
+    const int32_t *cur;
+    int32_t *next;
+    int32_t *snext;
+    int32_t r;
+    static constexpr bool kEarly = false;
+
+    static constexpr bool kWeights = (ALGO == kSSSP);
+
+    __device__ __forceinline__ bool skip(int32_t) const { return false; }
+    __device__ __forceinline__ int32_t weight(uint32_t e) const { return kWeights ? __ldg(w + e) : 0; }
+    __device__ __forceinline__ int32_t cand(int32_t u, int32_t wv, Acc &a) const {
+        const int32_t x = ldca(cur + u);
+        if (ALGO != kSSSP || x == kInf) return x;
+        const uint32_t y = (uint32_t)x + (uint32_t)wv;
+        if (y >= (uint32_t)kInf) {
+            a.overflow = 1;
+            return kInf;
+        }
+        return (int32_t)y;
+    }
+    __device__ __forceinline__ void finish(int32_t v, int32_t m, Acc &a) const {
+        const int32_t c = ldca(cur + v);
+        stcg(next + v, min(c, m));
+        if (m < c) {
+            stcg(snext + v, r + 1);
+            a.changed++;
+            a.updates++;
+        }
+    }
+    __device__ __forceinline__ void finish_part(int32_t v, int32_t m, bool first, Acc &a) const {
+        const int32_t c = ldca(cur + v);
+        if (first) red_min(next + v, min(c, m));
+        else if (m < c) red_min(next + v, m);
+        if (m < c) {
+            stcg(snext + v, r + 1);
+            a.changed++;
+            a.updates++;
+        }
+    }
+};
+
+// BFS bottom-up step (level lev): an unvisited vertex joins level lev+1 when
+// some in-neighbour is at level lev; its scan stops at the first one.
+struct BfsPullOp {
+    int32_t *L;
+    int32_t lev;
+    static constexpr bool kEarly = true;
+    static constexpr bool kWeights = false;
+
+    __device__ __forceinline__ bool skip(int32_t v) const { return ldcg(L + v) != kInf; }
+    __device__ __forceinline__ int32_t weight(uint32_t) const { return 0; }
+    // an in-neighbour's level was set in an earlier round (L1 is safe)
+    __device__ __forceinline__ int32_t cand(int32_t u, int32_t, Acc &) const { return ldca(L + u) == lev ? 0 : kInf; }
+    __device__ __forceinline__ void finish(int32_t v, int32_t m, Acc &a) const {
+        if (m == 0) {
+            stcg(L + v, lev + 1);
+            a.changed++;
+            a.updates++;
+        }
+    }
+    __device__ __forceinline__ void finish_part(int32_t v, int32_t m, bool, Acc &a) const {
+        if (m == 0 && atomicCAS(L + v, kInf, lev + 1) == kInf) {
+            a.changed++;
+            a.updates++;
+        }
+    }
+};
+
+template <class OP>
+__device__ __forceinline__ void pull_vertices(const Team &t, const View &tv, const OP &op, Acc &a) {
+    __shared__ int32_t s_min[kWarps][32];
+    __shared__ int s_skip;
+    const unsigned lane = lane_id();
+    const int wid = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)t.rank * kWarps + wid, nw = (int64_t)t.size * kWarps;
+
+    // high in-degree: a CTA per 2048-edge chunk
+    for (int64_t ci = t.rank; ci < tv.n_high_chunks; ci += t.size) {
+        const int2 hc = __ldg(tv.high + ci);
+        const int32_t v = hc.x;
+        if (threadIdx.x == 0) s_skip = op.skip(v);
+        __syncthreads();
+        const bool skip = s_skip;
+        __syncthreads();
+        if (skip) continue;
+        const uint32_t rb = __ldg(tv.row_off + v), e0 = (uint32_t)hc.y;
+        const uint32_t e1 = min(__ldg(tv.row_off + v + 1), e0 + (uint32_t)kChunk);
+        int32_t m = kInf;
+        for (uint32_t eb = e0 + threadIdx.x; eb < e1; eb += kBlock * kU) {
+            int32_t u[kU], wv[kU];
+#pragma unroll
+            for (int j = 0; j < kU; j++) {
+                const bool in = eb + j * kBlock < e1;
+                u[j] = in ? __ldg(tv.col + eb + j * kBlock) : -1;
+                wv[j] = in ? op.weight(eb + j * kBlock) : 0;
+            }
+#pragma unroll
+            for (int j = 0; j < kU; j++)
+                if (u[j] >= 0) m = min(m, op.cand(u[j], wv[j], a));
+        }
+        if (threadIdx.x == 0) a.pulled += e1 - e0;
+        m = block_min(m);
+        if (threadIdx.x == 0) op.finish_part(v, m, e0 == rb, a);
+    }
+
+    // mid in-degree: a warp per vertex
+    for (int64_t i = gw; i < tv.n_mid; i += nw) {
+        const int32_t v = __ldg(tv.mid + i);
+        if (__shfl_sync(0xffffffffu, lane == 0 ? (int)op.skip(v) : 0, 0)) continue;
+        const uint32_t rb = __ldg(tv.row_off + v), re = __ldg(tv.row_off + v + 1);
+        int32_t m = kInf;
+        uint32_t seen = 0;
+        for (uint32_t eb = rb + lane; eb < re; eb += 32 * kU) {
+            int32_t u[kU], wv[kU];
+#pragma unroll
+            for (int j = 0; j < kU; j++) {
+                const bool in = eb + 32 * j < re;
+                u[j] = in ? __ldg(tv.col + eb + 32 * j) : -1;
+                wv[j] = in ? op.weight(eb + 32 * j) : 0;
+            }
+#pragma unroll
+            for (int j = 0; j < kU; j++)
+                if (u[j] >= 0) m = min(m, op.cand(u[j], wv[j], a));
+            seen += 32 * kU;
+            if (OP::kEarly && __any_sync(0xffffffffu, m == 0)) break;
+        }
+        if (lane == 0) a.pulled += min(seen, re - rb);
+        m = warp_min(m);
+        if (lane == 0) op.finish(v, m, a);
+    }
+
+    // low in-degree: a warp's 32 vertices, their in-edges spread over the lanes
+    const int64_t nl = tv.n_low;
+    for (int64_t i0 = gw * 32; i0 < nl; i0 += nw * 32) {
+        const int64_t i = i0 + lane;
+        int32_t v = -1;
+        uint32_t rb = 0, d = 0;
+        if (i < nl) {
+            v = __ldg(tv.low + i);
+            if (!op.skip(v)) {
+                rb = __ldg(tv.row_off + v);
+                d = __ldg(tv.row_off + v + 1) - rb;
+            }
+        }
+        s_min[wid][lane] = kInf;
+        __syncwarp();
+        const uint32_t incl = warp_inclusive_scan(d);
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        const uint32_t excl = incl - d;
+        if (lane == 0) a.pulled += total;
+        for (uint32_t k0 = 0; k0 < total; k0 += 32 * kU) {
+            int32_t u[kU], wv[kU], own[kU];
+            uint32_t e[kU];
+#pragma unroll
+            for (int j = 0; j < kU; j++) {
+                const uint32_t k = k0 + 32 * j + lane;
+                int owner = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const uint32_t pv = __shfl_sync(0xffffffffu, incl, owner + step - 1);
+                    if (pv <= k) owner += step;
+                }
+                const uint32_t ob = __shfl_sync(0xffffffffu, rb, owner);
+                const uint32_t oe = __shfl_sync(0xffffffffu, excl, owner);
+                own[j] = owner;
+                e[j] = ob + (k - oe);
+                u[j] = k < total ? __ldg(tv.col + e[j]) : -1;
+                wv[j] = k < total ? op.weight(e[j]) : 0;
+            }
+#pragma unroll
+            for (int j = 0; j < kU; j++)
+                if (u[j] >= 0) {
+                    const int32_t cnd = op.cand(u[j], wv[j], a);
+                    if (cnd != kInf) atomicMin(&s_min[wid][own[j]], cnd);
+                }
+        }
+        __syncwarp();
+        if (d > 0) op.finish(v, s_min[wid][lane], a);
+        __syncwarp();
+    }
+}
+
 // ================================================================ sparse edge-sync rounds
 // A round of the synchronous edge mode normally streams every edge.  When the
 // previous round changed few vertices the round is "sparse": a flag pass
@@ -1165,8 +1387,20 @@ __device__ __forceinline__ bool stream_flagged_edges(const Team &t, uint32_t &us
 #ifndef FG_ASYNC_MIN_BLOCKS
 #define FG_ASYNC_MIN_BLOCKS 4
 #endif
+#ifndef FG_PULL_SHIFT_BFS
+#define FG_PULL_SHIFT_BFS 2
+#endif
+#ifndef FG_PULL_SHIFT_CC
+#define FG_PULL_SHIFT_CC 4
+#endif
+#ifndef FG_PULL_SHIFT_SSSP
+#define FG_PULL_SHIFT_SSSP 0
+#endif
 #ifndef FG_SPARSE_SHIFT
-#define FG_SPARSE_SHIFT 3
+#define FG_SPARSE_SHIFT 0
+#endif
+#ifndef FG_PULL_MIN_BLOCKS
+#define FG_PULL_MIN_BLOCKS 4
 #endif
 #ifndef FG_EDGE_SYNC_MIN_BLOCKS
 #define FG_EDGE_SYNC_MIN_BLOCKS 4
@@ -1174,7 +1408,8 @@ __device__ __forceinline__ bool stream_flagged_edges(const Team &t, uint32_t &us
 template <int MODE>
 constexpr int min_blocks() {
     return MODE == kVertexSync ? FG_SYNC_MIN_BLOCKS
-                               : (MODE == kEdgeSync ? FG_EDGE_SYNC_MIN_BLOCKS : FG_ASYNC_MIN_BLOCKS);
+                               : (MODE == kEdgeSync ? FG_EDGE_SYNC_MIN_BLOCKS
+                                                    : (MODE == kPull ? FG_PULL_MIN_BLOCKS : FG_ASYNC_MIN_BLOCKS));
 }
 
 // The whole query -- init, rounds, convergence -- run by one team of CTAs
@@ -1191,7 +1426,7 @@ __device__ __forceinline__ void fixpoint_prologue(uint32_t &ring_used) {
 
 template <int ALGO, int MODE>
 __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, uint32_t &ring_used) {
-    constexpr bool SYNC = (MODE == kVertexSync || MODE == kEdgeSync);
+    constexpr bool SYNC = (MODE == kVertexSync || MODE == kEdgeSync || MODE == kPull);
     Ctrl *c = p.ctrl;
     const View &g = p.g;
     const int32_t n = g.n;
@@ -1256,6 +1491,16 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
         // edge-sync: a round is sparse if the previous one accepted fewer
         // candidates than n / 2^FG_SPARSE_SHIFT (round 1: only the source is
         // active, except CC)
+        // pull mode: a round pulls if the previous one changed more than
+        // n / 2^shift vertices (round 1: only CC has every vertex active).
+        // A pull round reads every in-edge, a push round only the active
+        // vertices' out-edges; BFS pulls with an early exit per vertex.
+        constexpr int kPullShift = ALGO == kBFS ? FG_PULL_SHIFT_BFS : (ALGO == kCC ? FG_PULL_SHIFT_CC : FG_PULL_SHIFT_SSSP);
+        auto pull_round = [&](int r) -> bool {
+            if (r == 1) return ALGO == kCC;
+            const int64_t ch = __ldcg(&c->changed[(r - 1) % 3]);
+            return kPullShift >= 0 ? (ch << kPullShift) > (int64_t)n : (ch >> -kPullShift) > (int64_t)n;
+        };
         auto sparse_round = [&](int r) -> bool {
             if (r == 1) return ALGO != kCC;
             return ((int64_t)__ldcg(&c->changed[(r - 1) % 3]) << FG_SPARSE_SHIFT) < (int64_t)n;
@@ -1267,9 +1512,13 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
             }
             if (tid == 0) c->changed[(r + 1) % 3] = 0;
             rounds = r;
+            const bool pull = (MODE == kPull) && pull_round(r);
+            if (pull && tid == 0) c->pull_rounds++;
             if constexpr (ALGO == kBFS) {
                 BfsSyncOp op{p.A, r - 1};
-                if constexpr (MODE == kVertexSync) {
+                if (pull) {
+                    pull_vertices(t, p.tv, BfsPullOp{p.A, r - 1}, a);
+                } else if constexpr (MODE == kVertexSync || MODE == kPull) {
                     expand_vertices(t, g.row_off, g.col, g.low, 0, g.mid, g.n_mid, g.high, g.n_high_chunks, op,
                                     NoPush{}, a);
                     expand_low_dense(t, g.row_off, g.col, p.A, r - 1, n, op, a);
@@ -1286,7 +1535,9 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
                 const int32_t *scur = (r & 1) ? p.S1 : p.S0;
                 int32_t *snext = (r & 1) ? p.S0 : p.S1;
                 SyncOp<ALGO> op{g.w, cur, next, scur, snext, r};
-                if constexpr (MODE == kVertexSync) {
+                if (pull) {
+                    pull_vertices(t, p.tv, PullMinOp<ALGO>{p.tv.w, cur, next, snext, r}, a);
+                } else if constexpr (MODE == kVertexSync || MODE == kPull) {
                     expand_vertices(t, g.row_off, g.col, g.low, 0, g.mid, g.n_mid, g.high, g.n_high_chunks, op,
                                     NoPush{}, a);
                     expand_low_dense(t, g.row_off, g.col, scur, r, n, op, a);
@@ -1420,7 +1671,7 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
 
     // ---- statistics
     unsigned long long ev = block_sum(a.verts), ee = block_sum(a.edges), eu = block_sum(a.updates),
-                       ep = block_sum(a.pushes), es = block_sum(a.scanned);
+                       ep = block_sum(a.pushes), es = block_sum(a.scanned), el = block_sum(a.pulled);
     int of = block_sum(a.overflow);
     if (threadIdx.x == 0) {
         if (ev) atomicAdd(&c->st_vertices, ev);
@@ -1428,6 +1679,7 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
         if (eu) atomicAdd(&c->st_updates, eu);
         if (ep) atomicAdd(&c->st_pushes, ep);
         if (es) atomicAdd(&c->st_scanned, es);
+        if (el) atomicAdd(&c->st_pulled, el);
         if (of) atomicOr(&c->status, kStOverflow);
     }
     if (tid == 0) {

@@ -61,6 +61,7 @@ KernelFn kernel_for(Algo algo, Mode mode) {
     FG_K(kSSSP, kVertexSync) FG_K(kSSSP, kVertexAsync) FG_K(kSSSP, kEdgeSync) FG_K(kSSSP, kEdgeAsync)
     FG_K(kBFS, kVertexSync) FG_K(kBFS, kVertexAsync) FG_K(kBFS, kEdgeSync) FG_K(kBFS, kEdgeAsync)
     FG_K(kCC, kVertexSync) FG_K(kCC, kVertexAsync) FG_K(kCC, kEdgeSync) FG_K(kCC, kEdgeAsync)
+    FG_K(kSSSP, kPull) FG_K(kBFS, kPull) FG_K(kCC, kPull)
 #undef FG_K
     return nullptr;
 }
@@ -112,7 +113,7 @@ int64_t wl_cap_of(const View &g, Mode mode, int k) {
 // worklists, prefix arrays, chunk flags), each piece 256-byte aligned.
 size_t query_workspace_bytes(const View &g, Algo algo, Mode mode) {
     const int32_t n = g.n;
-    const bool sync = (mode == kVertexSync || mode == kEdgeSync);
+    const bool sync = (mode == kVertexSync || mode == kEdgeSync || mode == kPull);
     size_t need = Workspace::need(1, sizeof(Ctrl)) + Workspace::need(n, 4);
     if (sync && algo != kBFS) need += 3 * Workspace::need(n, 4);
     const int64_t nwt = (g.m + kWTile - 1) / kWTile;   // edge-sync: one flag per 128-edge warp tile
@@ -130,7 +131,7 @@ void carve_query_workspace(char *base, const View &g, Algo algo, Mode mode, Para
     Workspace ws;
     ws.base = base;
     const int32_t n = g.n;
-    const bool sync = (mode == kVertexSync || mode == kEdgeSync);
+    const bool sync = (mode == kVertexSync || mode == kEdgeSync || mode == kPull);
     const int64_t nwt = (g.m + kWTile - 1) / kWTile;
     p.g = g;
     p.ctrl = ws.take<Ctrl>(1);
@@ -165,6 +166,10 @@ fg_status run_query(const fg_graph *G, Algo algo, Mode mode, int32_t source, int
     if (!dp.coop) return fail(FG_ERR_CUDA, "device does not support cooperative launches");
     KernelFn fn = kernel_for(algo, mode);
     if (!fn) return fail(FG_ERR_INVALID_ARG, "invalid algorithm or mode");
+    if (mode == kPull && algo != kCC) {
+        fg_status ts = ensure_transpose(G);
+        if (ts != FG_OK) return ts;
+    }
 
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, kBlock, 0);
@@ -180,6 +185,7 @@ fg_status run_query(const fg_graph *G, Algo algo, Mode mode, int32_t source, int
     if (e != cudaSuccess) return cuda_fail(e, "query workspace");
     Params p;
     carve_query_workspace(wsbase, g, algo, mode, p);
+    if (mode == kPull) p.tv = (algo == kCC) ? G->s : G->t;
     struct {
         char *base;
     } ws{wsbase};
@@ -273,6 +279,8 @@ fg_status run_query(const fg_graph *G, Algo algo, Mode mode, int32_t source, int
         stats->pushes = (int64_t)hc.st_pushes;
         stats->scanned = (int64_t)hc.st_scanned;
         stats->barriers = hc.barriers;
+        stats->pull_rounds = hc.pull_rounds;
+        stats->edges_pulled = (int64_t)hc.st_pulled;
         stats->kernel_ms = ms;
     }
     if (status != FG_OK) return fail(status, msg);

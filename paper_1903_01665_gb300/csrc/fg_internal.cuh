@@ -53,8 +53,10 @@ struct fg_graph {
     int device = 0;
     fg::View g;      // directed
     fg::View s;      // symmetrised
+    fg::View t;      // transposed (in-neighbours), built on the first pull query
+    bool t_ready = false;
     fg_graph_info_t info{};
-    void *allocs[32] = {};
+    void *allocs[48] = {};
     int n_allocs = 0;
     // lazily computed diameter estimate and autotuned modes for fg_select_mode
     mutable std::mutex mu;
@@ -77,18 +79,21 @@ struct Ctrl {
     int jchanged[3];            // per-pass pointer-jumping change counters
     int wl_size[3][4];          // async: worklist sizes per generation slot and class
     unsigned long long st_vertices, st_edges, st_updates, st_pushes, st_scanned;
+    unsigned long long st_pulled;   // pull mode: in-edges read by pull rounds
     int barriers;
     int done;                   // the fixpoint was reached
+    int pull_rounds;            // pull mode: rounds that pulled
 };
 
 enum Algo { kSSSP = 0, kBFS = 1, kCC = 2 };
-enum Mode { kVertexSync = 0, kVertexAsync = 1, kEdgeSync = 2, kEdgeAsync = 3 };
+enum Mode { kVertexSync = 0, kVertexAsync = 1, kEdgeSync = 2, kEdgeAsync = 3, kPull = 5 };
 
 // worklist classes (vertex-async): low, mid, high chunks; edge-async uses class 0 only
 enum { kWlLow = 0, kWlMid = 1, kWlHigh = 2 };
 
 struct Params {
     View g;
+    View tv;                    // pull mode: the transposed view (in-neighbours; CC: the symmetrised one)
     int32_t *A = nullptr;       // values (dist / level / label); the result for async
     int32_t *B = nullptr;       // second buffer of the sync modes
     int32_t *S0 = nullptr;      // activity stamps (sync: read in odd/even rounds)
@@ -338,6 +343,9 @@ struct Workspace {
 struct Params;
 size_t query_workspace_bytes(const View &g, Algo algo, Mode mode);
 void carve_query_workspace(char *base, const View &g, Algo algo, Mode mode, Params &p);
+
+// the transposed view for pull queries (fg_build.cu)
+fg_status ensure_transpose(const fg_graph *g);
 
 // queries (fg_fixpoint.cu)
 fg_status run_query(const fg_graph *g, Algo algo, Mode mode, int32_t source, int32_t *out,

@@ -52,6 +52,7 @@ int main(void) {
   P(fg_stats, mode); P(fg_stats, rounds); P(fg_stats, jump_passes); P(fg_stats, grid_blocks);
   P(fg_stats, vertices_processed); P(fg_stats, edges_relaxed); P(fg_stats, updates);
   P(fg_stats, pushes); P(fg_stats, scanned); P(fg_stats, kernel_ms);
+  P(fg_stats, pull_rounds); P(fg_stats, edges_pulled);
   P(fg_graph_info_t, n); P(fg_graph_info_t, m); P(fg_graph_info_t, m_sym);
   P(fg_graph_info_t, max_out_degree); P(fg_graph_info_t, n_zero_out); P(fg_graph_info_t, n_low);
   P(fg_graph_info_t, n_mid); P(fg_graph_info_t, n_high); P(fg_graph_info_t, n_high_chunks);

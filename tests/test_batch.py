@@ -39,7 +39,7 @@ def test_batch_matches_oracle(use_graph):
             srcs = [int(x) for x in gg.sources(g, 3, seed=100 + gi)]
             for k, s in enumerate(srcs):
                 for algo in (0, 1, 2):
-                    mode = int(rng.integers(0, 4))
+                    mode = int(rng.choice([0, 1, 2, 3, 5]))
                     if (k + algo) % 2:
                         out = torch.full((g.n,), -5, dtype=torch.int32, device="cuda")
                     else:
@@ -64,7 +64,10 @@ def test_batch_auto_after_autotune_and_overflow_status():
         s = int(gg.sources(g, 1, seed=3)[0])
         for algo in (0, 1, 2):
             st, best, times = fg.fg_autotune(h, algo, s)
-            assert st == fg.FG_OK and best in (0, 1, 2, 3) and all(t > 0 for t in times)
+            tried = (0, 1, 2, 3, 5) if algo == fg.FG_ALGO_BFS else (0, 1, 2, 3)
+            assert st == fg.FG_OK and best in tried and all(times[m] > 0 for m in tried)
+            assert times[fg.FG_AUTO] == 0 and times[best] == min(times[m] for m in tried)
+            assert all(times[m] == 0 for m in range(6) if m not in tried)
             st, m = fg.fg_select_mode(h, algo)
             assert m == best
         outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in range(3)]
