@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 import graphgen as gg  # noqa: E402
 
 METRIC = "SSSP/BFS GTEPS & HBM-roofline %; served p50/p99 latency vs one-at-a-time"
-MODE_NAMES = {0: "vertex_sync", 1: "vertex_async", 2: "edge_sync", 3: "edge_async", 5: "pull"}
+MODE_NAMES = {0: "vertex_sync", 1: "vertex_async", 2: "edge_sync", 3: "edge_async", 5: "pull", 6: "bucket"}
 ALGO_NAMES = ["sssp", "bfs", "cc"]
 
 # DRAM bytes per launch from one ncu capture (dram__bytes_read.sum +
@@ -277,6 +277,46 @@ def run_extra_modes(r, per_kernel: dict, modes, reps: int = 2) -> dict:
     finally:
         fg.check(fg.fg_graph_destroy(h))
     return out
+
+
+def run_grid_bucket(device, reps: int = 2) -> dict:
+    """The bucketed SSSP (near-far) where it is meant to help: the 4096^2
+    road-like grid, SSSP from two seeded sources, against the paper's
+    vertex-sync and vertex-async modes (device time, edges relaxed, exact
+    agreement of the three results)."""
+    import torch
+    import paper_1903_01665_gb300 as fg
+    g = gg.grid(4096)
+    srcs = [int(x) for x in gg.sources(g, 2)]
+    st, h = fg.fg_graph_create_coo(g.n, torch.from_numpy(g.src).to(device), torch.from_numpy(g.dst).to(device),
+                                   torch.from_numpy(g.w).to(device))
+    fg.check(st)
+    outs = [torch.empty(g.n, dtype=torch.int32, device=device) for _ in range(3)]
+    res = {}
+    exact = True
+    try:
+        for k, (name, mode) in enumerate((("vertex_sync", fg.FG_VERTEX_SYNC), ("vertex_async", fg.FG_VERTEX_ASYNC),
+                                          ("bucket", fg.FG_BUCKET))):
+            ms, edges, gens = [], [], []
+            for s_ in srcs:
+                for rep in range(reps + 1):
+                    st, stats = fg.fg_run(h, 0, s_, outs[k], mode)
+                    fg.check(st)
+                    if rep:
+                        ms.append(stats.kernel_ms)
+                        edges.append(stats.edges_relaxed)
+                        gens.append(stats.rounds)
+                if mode == fg.FG_BUCKET:
+                    fg.check(fg.fg_run(h, 0, s_, outs[0], fg.FG_VERTEX_SYNC)[0])
+                    fg.check(fg.fg_run(h, 0, s_, outs[1], fg.FG_VERTEX_ASYNC)[0])
+                    exact &= bool(torch.equal(outs[0], outs[2]) and torch.equal(outs[1], outs[2]))
+            res[name] = {"avg_ms": round(float(np.mean(ms)), 3), "edges_relaxed": int(np.mean(edges)),
+                         "generations": int(np.mean(gens))}
+    finally:
+        fg.check(fg.fg_graph_destroy(h))
+    res["bit_exact"] = exact
+    res["workload"] = "grid-4096 (16,777,216 V, ~65.8 M E, w U[1,10000]), SSSP from 2 seeded sources"
+    return res
 
 
 def run_batched(device, reps: int = 3) -> dict:
@@ -580,7 +620,7 @@ def run_ours(args):
                "d2h_bytes_per_step": 4 * r.g.n * len(r.queries), "steps": k2}
 
     sweep = None if args.no_sweep else run_sweep_roofline(r, peaks[0])
-    extra = run_extra_modes(r, per_kernel, [fg.FG_PULL])
+    extra = run_extra_modes(r, per_kernel, [fg.FG_PULL, fg.FG_BUCKET])
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -589,6 +629,7 @@ def run_ours(args):
     batched = serving = None
     del r
     torch.cuda.empty_cache()
+    grid_bucket = None if args.no_grid_bucket else run_grid_bucket(device)
     if not args.no_batched:
         batched = run_batched(device)
     if not args.no_serving:
@@ -603,7 +644,8 @@ def run_ours(args):
                            "teps_edges_per_step": units // max(args.steps, 1),
                            "l2": "inputs larger than L2 (graph ~1.9-2.2 GB built per step)",
                            "parallelism": f"replicas x{ws}"},
-                "roofline": roofline, "sweep_roofline": sweep, "extra_modes": extra, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "roofline": roofline, "sweep_roofline": sweep, "extra_modes": extra, "grid_bucket": grid_bucket,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "per_kernel": per_mode, "batched": batched, "serving": serving}
         print(json.dumps(line), flush=True)
     if pg:
@@ -730,6 +772,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sweep", action="store_true", help="skip the all-active sweep roofline test")
+    ap.add_argument("--no-grid-bucket", action="store_true", help="skip the bucketed-SSSP grid comparison")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload comparison")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving comparison")
     ap.add_argument("--serving-full", action="store_true",

@@ -26,7 +26,17 @@
  *                   an unvisited vertex stops at its first in-neighbour on
  *                   the frontier), the other rounds push as FG_VERTEX_SYNC.
  *                   The transposed CSR it reads is built on the first pull
- *                   query of a graph and kept with it (about 8 bytes per edge).
+ *                   query of a graph and kept with it (about 8 bytes per edge);
+ *
+ * and a sixth for high-diameter graphs:
+ *
+ *   FG_BUCKET       FG_VERTEX_ASYNC with the worklist split by distance
+ *                   (near-far, a two-bucket form of delta-stepping): SSSP
+ *                   vertices whose new distance is below a threshold T are
+ *                   processed first; the others wait in a far list, and when
+ *                   the near worklist runs empty T moves to the far list's
+ *                   smallest distance + delta and the far list is split.
+ *                   BFS and CC run as FG_VERTEX_ASYNC.
  *
  * All reach the same unique fixpoint, so their outputs are identical.
  *
@@ -78,7 +88,8 @@ typedef enum {
     FG_EDGE_SYNC = 2,
     FG_EDGE_ASYNC = 3,
     FG_AUTO = 4,                /* the mode fg_select_mode picks */
-    FG_PULL = 5
+    FG_PULL = 5,
+    FG_BUCKET = 6
 } fg_mode;
 
 typedef enum { FG_ALGO_SSSP = 0, FG_ALGO_BFS = 1, FG_ALGO_CC = 2 } fg_algo;
@@ -164,12 +175,15 @@ typedef struct {
                                    mid-round or pointer-jumping barrier), at most
                                    round_trace_cap entries; NULL = no tracing */
     int32_t round_trace_cap;
+    int32_t delta;              /* FG_BUCKET: bucket width (0 = 8 x the mean edge weight x the
+                                   mean out-degree) */
 } fg_options;
 
 typedef struct {
     int32_t mode;               /* mode that ran (FG_AUTO resolved) */
     int32_t rounds;             /* sync rounds or async worklist generations, final
-                                   no-change round included */
+                                   no-change round included (FG_BUCKET: far-list splits
+                                   included; max_rounds counts the other generations) */
     int32_t jump_passes;        /* CC pointer-jumping passes */
     int32_t grid_blocks;        /* persistent CTAs launched */
     int64_t vertices_processed; /* active vertices expanded, summed over rounds */

@@ -33,7 +33,8 @@ FG_EDGE_SYNC = 2
 FG_EDGE_ASYNC = 3
 FG_AUTO = 4
 FG_PULL = 5
-MODES = {"vertex_sync": 0, "vertex_async": 1, "edge_sync": 2, "edge_async": 3, "auto": 4, "pull": 5}
+FG_BUCKET = 6
+MODES = {"vertex_sync": 0, "vertex_async": 1, "edge_sync": 2, "edge_async": 3, "auto": 4, "pull": 5, "bucket": 6}
 MODE_NAMES = {v: k for k, v in MODES.items()}
 # algorithms
 FG_ALGO_SSSP = 0
@@ -46,7 +47,7 @@ class fg_options(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("max_rounds", ctypes.c_int32),
                 ("wait_timeout_ms", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("inject_missing_arrival", ctypes.c_int32), ("round_trace", ctypes.c_void_p),
-                ("round_trace_cap", ctypes.c_int32)]
+                ("round_trace_cap", ctypes.c_int32), ("delta", ctypes.c_int32)]
 
 
 class fg_stats(ctypes.Structure):
@@ -242,14 +243,14 @@ def fg_select_mode(g, algo):
 
 
 def fg_run(g, algo, src, out, mode, stream=None, max_rounds=0, wait_timeout_ms=0, blocks_per_sm=0,
-           inject_missing_arrival=0, round_trace=None):
+           inject_missing_arrival=0, round_trace=None, delta=0):
     """Returns (status, fg_stats).  stream: a torch.cuda.Stream, a raw handle, or None."""
     _check_dtype(out, "int32")
     if stream is not None and hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
     opt = fg_options(stream, int(max_rounds), int(wait_timeout_ms), int(blocks_per_sm),
                      int(inject_missing_arrival), _ptr(round_trace),
-                     int(round_trace.shape[0]) if round_trace is not None else 0)
+                     int(round_trace.shape[0]) if round_trace is not None else 0, int(delta))
     stats = fg_stats()
     st = load().fg_run(g, int(algo), int(src), _ptr(out), int(mode), ctypes.byref(opt), ctypes.byref(stats))
     return st, stats

@@ -69,6 +69,9 @@ BatchFn batch_kernel_for(int kind) {
         case kSSSP * 8 + kPull: return batch_kernel<kSSSP, kPull>;
         case kBFS * 8 + kPull: return batch_kernel<kBFS, kPull>;
         case kCC * 8 + kPull: return batch_kernel<kCC, kPull>;
+        case kSSSP * 8 + kBucket: return batch_kernel<kSSSP, kBucket>;
+        case kBFS * 8 + kBucket: return batch_kernel<kBFS, kBucket>;
+        case kCC * 8 + kBucket: return batch_kernel<kCC, kBucket>;
     }
     return nullptr;
 }
@@ -238,6 +241,7 @@ fg_status batch_launch(const fg_query *qs, int32_t nq, const fg_batch_options *o
         Params p;
         carve_query_workspace(w, *view[i], (Algo)qs[i].algo, mode[i], p);
         if (mode[i] == kPull) p.tv = (qs[i].algo == FG_ALGO_CC) ? qs[i].g->s : qs[i].g->t;
+        p.delta = default_delta(qs[i].g);
         p.ctrl = job.d_ctrls + i;
         p.source = qs[i].algo == FG_ALGO_CC ? 0 : qs[i].src;
         p.max_rounds = view[i]->n > INT32_MAX - 2 ? INT32_MAX : view[i]->n + 2;

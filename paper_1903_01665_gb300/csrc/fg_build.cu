@@ -80,6 +80,15 @@ __global__ void k_scatter_coo(int64_t m, const int32_t *__restrict__ s, const in
     }
 }
 
+// Sum of the edge weights (for the bucket mode's default width).
+__global__ void k_weight_sum(int64_t m, const int32_t *__restrict__ w, unsigned long long *sum) {
+    unsigned long long x = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        x += (unsigned)w[e];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(sum, x);
+}
+
 // Transposed CSR: every edge u->v stored at v's in-edge list as (u, w).
 __global__ void k_scatter_transpose(int64_t m, const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
                                     const int32_t *__restrict__ w, uint32_t *cursor, int32_t *tcol, int32_t *tw) {
@@ -522,6 +531,23 @@ fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const i
         for (int i = 0; i < g->n_allocs; i++) cudaFree(g->allocs[i]);
         delete g;
         return fail(st, msg);
+    }
+    if (m > 0) {
+        unsigned long long *d_sum = nullptr, h_sum = 0;
+        cudaError_t e = cudaMalloc(&d_sum, sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMemset(d_sum, 0, sizeof(unsigned long long));
+        if (e == cudaSuccess) {
+            k_weight_sum<<<grid_for(m), kBlock>>>(m, v.w, d_sum);
+            count_launch();
+            e = cudaMemcpy(&h_sum, d_sum, sizeof(h_sum), cudaMemcpyDeviceToHost);
+        }
+        if (d_sum) cudaFree(d_sum);
+        if (e != cudaSuccess) {
+            for (int i = 0; i < g->n_allocs; i++) cudaFree(g->allocs[i]);
+            delete g;
+            return cuda_fail(e, "weight sum");
+        }
+        g->w_mean = (double)h_sum / (double)m;
     }
     fg_graph_info_t &I = g->info;
     I.n = n;

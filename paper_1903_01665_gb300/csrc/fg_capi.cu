@@ -76,7 +76,7 @@ using namespace fg;
 namespace {
 
 fg_status check_mode(fg_mode m) {
-    if (m < FG_VERTEX_SYNC || m > FG_PULL) return fail(FG_ERR_INVALID_ARG, "invalid mode");
+    if (m < FG_VERTEX_SYNC || m > FG_BUCKET) return fail(FG_ERR_INVALID_ARG, "invalid mode");
     return FG_OK;
 }
 
@@ -100,7 +100,7 @@ fg_status query(const fg_graph *g, fg_algo algo, int32_t src, int32_t *out, fg_m
     if (s != FG_OK) return s;
     if (algo != FG_ALGO_CC && (src < 0 || src >= g->info.n))
         return fail(FG_ERR_INVALID_ARG, "source vertex outside [0, n)");
-    if (opt && (opt->max_rounds < 0 || opt->wait_timeout_ms < 0 || opt->blocks_per_sm < 0))
+    if (opt && (opt->max_rounds < 0 || opt->wait_timeout_ms < 0 || opt->blocks_per_sm < 0 || opt->delta < 0))
         return fail(FG_ERR_INVALID_ARG, "negative option");
     int dev;
     if (!ensure_device(&dev)) return fail(FG_ERR_CUDA, "no CUDA device");
@@ -284,7 +284,7 @@ fg_status fg_run_batch(const fg_query *queries, int32_t nq, const fg_batch_optio
         if (!q.g) return fail(FG_ERR_INVALID_ARG, where + "graph is NULL");
         if (!q.out) return fail(FG_ERR_INVALID_ARG, where + "output buffer is NULL");
         if (q.algo < FG_ALGO_SSSP || q.algo > FG_ALGO_CC) return fail(FG_ERR_INVALID_ARG, where + "invalid algorithm");
-        if (q.mode < FG_VERTEX_SYNC || q.mode > FG_PULL) return fail(FG_ERR_INVALID_ARG, where + "invalid mode");
+        if (q.mode < FG_VERTEX_SYNC || q.mode > FG_BUCKET) return fail(FG_ERR_INVALID_ARG, where + "invalid mode");
         if (q.algo != FG_ALGO_CC && (q.src < 0 || q.src >= q.g->info.n))
             return fail(FG_ERR_INVALID_ARG, where + "source vertex outside [0, n)");
     }

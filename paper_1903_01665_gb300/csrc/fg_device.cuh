@@ -242,6 +242,38 @@ struct AsyncOp {
     }
 };
 
+// Bucketed SSSP (near-far): as AsyncOp, but a target whose new distance is
+// not below the threshold T goes to the far list of the current epoch (once
+// per epoch, by far_mark) instead of the next generation's worklist.
+struct BucketOp : AsyncOp<kSSSP> {
+    int32_t T;
+    int32_t epoch;
+    int32_t *far;
+    int32_t *far_mark;
+    int *far_size;
+    int32_t far_cap;
+    Ctrl *ctrl;
+
+    __device__ __forceinline__ bool commit(int32_t v, int32_t c, int32_t pv, Acc &a) const {
+        if (c < pv && c < ldcg(D + v)) {
+            red_min(D + v, c);
+            a.updates++;
+            if (c < T) return atomicExch(stamp + v, gen + 1) != gen + 1;
+            if (atomicExch(far_mark + v, epoch) != epoch) {
+                // warp-aggregated append of the lanes that got here together
+                const unsigned am = __activemask();
+                const int leader = __ffs(am) - 1;
+                int base = 0;
+                if ((int)lane_id() == leader) base = atomicAdd(far_size, __popc(am));
+                base = __shfl_sync(am, base, leader) + __popc(am & lanemask_lt());
+                if (base < far_cap) far[base] = v;
+                else atomicOr(&ctrl->status, kStWorklist);
+            }
+        }
+        return false;
+    }
+};
+
 // Asynchronous BFS: frontier queue; a vertex is claimed once by CAS from INF.
 struct BfsAsyncOp {
     int32_t *L;
@@ -1406,7 +1438,7 @@ __device__ __forceinline__ bool stream_flagged_edges(const Team &t, uint32_t &us
 #define FG_EDGE_SYNC_MIN_BLOCKS 4
 #endif
 template <int MODE>
-constexpr int min_blocks() {
+constexpr int min_blocks() {  // kBucket: as the other worklist modes
     return MODE == kVertexSync ? FG_SYNC_MIN_BLOCKS
                                : (MODE == kEdgeSync ? FG_EDGE_SYNC_MIN_BLOCKS
                                                     : (MODE == kPull ? FG_PULL_MIN_BLOCKS : FG_ASYNC_MIN_BLOCKS));
@@ -1456,7 +1488,10 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
             p.S0[v] = 0;
         }
         if (!SYNC && ALGO != kBFS) p.S0[v] = 0;
+        if (MODE == kBucket && ALGO == kSSSP) p.far_mark[v] = 0;
     }
+    if (MODE == kBucket && tid == 0)
+        for (int k = 0; k < 3; k++) c->far_min[k] = kInf;
     if (MODE == kEdgeSync)
         for (int64_t k = tid; k < (g.m + kWTile - 1) / kWTile; k += nth) p.eflag[k] = 0;
 
@@ -1607,6 +1642,11 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
         }
         __syncwarp();
         WarpBuf *wb = s_buf[threadIdx.x >> 5];
+        // bucket mode: the near threshold and the far list's epoch (epochs
+        // start at 1 so that the zeroed far_mark means "in no far list")
+        int32_t T = (MODE == kBucket && ALGO == kSSSP) ? p.delta : kInf;
+        int epoch = 1;
+        int work_gens = 0;
         for (int gen = 0;; gen++) {
             const int in_slot = gen % 3, out_slot = (gen + 1) % 3;
             const bool initial_cc = (ALGO == kCC && gen == 0);
@@ -1619,28 +1659,86 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
                     n_in[kWlLow] = g.n_low; n_in[kWlMid] = g.n_mid; n_in[kWlHigh] = g.n_high_chunks;
                 }
             }
-            if (n_in[0] + n_in[1] + n_in[2] == 0) {
+            const bool empty = n_in[0] + n_in[1] + n_in[2] == 0;
+            const bool split = empty && MODE == kBucket && ALGO == kSSSP && __ldcg(&c->far_size[epoch % 3]) > 0;
+            if (empty && !split) {
                 done = true;
                 break;
             }
-            if (gen >= p.max_rounds) {
+            // the cap counts worklist generations; a far-list split always
+            // moves at least the far list's nearest vertex, so splits end
+            if (!split && work_gens >= p.max_rounds) {
                 if (tid == 0) atomicOr(&c->status, kStRoundCap);
                 break;
             }
+            if (!split) work_gens++;
             rounds = gen + 1;
             if (tid == 0)
                 for (int k = 0; k < 3; k++) c->wl_size[(gen + 2) % 3][k] = 0;
             const int pi = gen & 1, po = pi ^ 1;
             int *osize = c->wl_size[out_slot];
-            if (MODE == kVertexAsync) {
+            if (split) {
+                // The near worklist ran empty: the threshold moves to the far
+                // list's smallest distance + delta, and the far list is split
+                // into the next generation's worklist (distance below the
+                // new threshold) and the next epoch's far list.
+                const int32_t *far_in = p.far[epoch & 1];
+                int32_t *far_out = p.far[(epoch + 1) & 1];
+                const int fn = __ldcg(&c->far_size[epoch % 3]);
+                if (tid == 0) {
+                    c->far_size[(epoch + 2) % 3] = 0;
+                    c->far_min[(epoch + 2) % 3] = kInf;
+                    c->splits++;
+                }
+                int32_t fm = kInf;
+                for (int64_t i = tid; i < fn; i += nth) fm = min(fm, ldcg(p.A + ldcg(far_in + i)));
+                fm = block_min(fm);
+                if (threadIdx.x == 0 && fm < kInf) atomicMin(&c->far_min[epoch % 3], fm);
+                if (!sync_()) break;
+                const int32_t fmin = __ldcg(&c->far_min[epoch % 3]);
+                T = fmin >= kInf - p.delta ? kInf : fmin + p.delta;
+                ClassPush push{g.row_off, g.vclass, p.wl[po][kWlLow], p.wl[po][kWlMid],
+                               reinterpret_cast<int2 *>(p.wl[po][kWlHigh]), osize,
+                               p.wl_cap[kWlLow], p.wl_cap[kWlMid], p.wl_cap[kWlHigh] / 2, &wb[0], &wb[1], c};
+                for (int64_t i0 = tid - lane_id(); i0 < fn; i0 += nth) {   // warp-uniform trip count
+                    const int64_t i = i0 + lane_id();
+                    bool near = false;
+                    int32_t v = 0;
+                    if (i < fn) {
+                        v = ldcg(far_in + i);
+                        if (ldcg(p.A + v) < T) {
+                            near = atomicExch(p.S0 + v, gen + 1) != gen + 1;
+                        } else if (atomicExch(p.far_mark + v, epoch + 1) != epoch + 1) {
+                            const unsigned am = __activemask();
+                            const int leader = __ffs(am) - 1;
+                            int base = 0;
+                            if ((int)lane_id() == leader) base = atomicAdd(&c->far_size[(epoch + 1) % 3], __popc(am));
+                            base = __shfl_sync(am, base, leader) + __popc(am & lanemask_lt());
+                            if (base < p.far_cap) far_out[base] = v;
+                            else atomicOr(&c->status, kStWorklist);
+                        }
+                    }
+                    __syncwarp();
+                    push(near, v, a);
+                }
+                push.flush();
+                epoch++;
+            } else if (MODE == kVertexAsync || MODE == kBucket) {
                 const int32_t *low = initial_cc ? g.low : p.wl[pi][kWlLow];
                 const int32_t *mid = initial_cc ? g.mid : p.wl[pi][kWlMid];
                 const int2 *high = initial_cc ? g.high : reinterpret_cast<const int2 *>(p.wl[pi][kWlHigh]);
                 ClassPush push{g.row_off, g.vclass, p.wl[po][kWlLow], p.wl[po][kWlMid],
                                reinterpret_cast<int2 *>(p.wl[po][kWlHigh]), osize,
                                p.wl_cap[kWlLow], p.wl_cap[kWlMid], p.wl_cap[kWlHigh] / 2, &wb[0], &wb[1], c};
-                if (ALGO == kBFS) {
+                if constexpr (ALGO == kBFS) {
                     BfsAsyncOp op{p.A, gen};
+                    expand_vertices(t, g.row_off, g.col, low, n_in[kWlLow], mid, n_in[kWlMid], high, n_in[kWlHigh],
+                                    op, push, a);
+                } else if constexpr (MODE == kBucket && ALGO == kSSSP) {
+                    BucketOp op;
+                    op.w = g.w; op.D = p.A; op.stamp = p.S0; op.gen = gen;
+                    op.T = T; op.epoch = epoch; op.far = p.far[epoch & 1]; op.far_mark = p.far_mark;
+                    op.far_size = &c->far_size[epoch % 3]; op.far_cap = p.far_cap; op.ctrl = c;
                     expand_vertices(t, g.row_off, g.col, low, n_in[kWlLow], mid, n_in[kWlMid], high, n_in[kWlHigh],
                                     op, push, a);
                 } else {

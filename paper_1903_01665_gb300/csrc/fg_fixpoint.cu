@@ -62,6 +62,7 @@ KernelFn kernel_for(Algo algo, Mode mode) {
     FG_K(kBFS, kVertexSync) FG_K(kBFS, kVertexAsync) FG_K(kBFS, kEdgeSync) FG_K(kBFS, kEdgeAsync)
     FG_K(kCC, kVertexSync) FG_K(kCC, kVertexAsync) FG_K(kCC, kEdgeSync) FG_K(kCC, kEdgeAsync)
     FG_K(kSSSP, kPull) FG_K(kBFS, kPull) FG_K(kCC, kPull)
+    FG_K(kSSSP, kBucket) FG_K(kBFS, kBucket) FG_K(kCC, kBucket)
 #undef FG_K
     return nullptr;
 }
@@ -99,7 +100,7 @@ void overflow_check_launch(const View &g, const int32_t *D, int *flag, cudaStrea
 
 namespace {
 int64_t wl_cap_of(const View &g, Mode mode, int k) {
-    if (mode == kVertexAsync) {
+    if (mode == kVertexAsync || mode == kBucket) {
         if (k == kWlLow) return std::max(g.n_low, 1);
         if (k == kWlMid) return std::max(g.n_mid, 1);
         return 2 * (int64_t)std::max(g.n_high_chunks, 1);
@@ -122,6 +123,7 @@ size_t query_workspace_bytes(const View &g, Algo algo, Mode mode) {
         if (algo != kBFS) need += Workspace::need(n, 4);
         for (int k = 0; k < 3; k++) need += 2 * Workspace::need(wl_cap_of(g, mode, k), 4);
         if (mode == kEdgeAsync) need += Workspace::need(wl_cap_of(g, mode, 0), 4) + Workspace::need(kMaxGrid, 4);
+        if (mode == kBucket && algo == kSSSP) need += 3 * Workspace::need(n, 4);
     }
     return need;
 }
@@ -151,7 +153,23 @@ void carve_query_workspace(char *base, const View &g, Algo algo, Mode mode, Para
             p.lb_off = ws.take<uint32_t>(wl_cap_of(g, mode, 0));
             p.lb_blk = ws.take<uint32_t>(kMaxGrid);
         }
+        if (mode == kBucket && algo == kSSSP) {
+            p.far[0] = ws.take<int32_t>(n);
+            p.far[1] = ws.take<int32_t>(n);
+            p.far_mark = ws.take<int32_t>(n);
+            p.far_cap = n;
+        }
     }
+}
+
+// bucket mode: 8 x the mean edge weight x the mean out-degree unless the
+// caller sets it.  A narrower bucket relaxes fewer edges but needs more
+// generations, each a grid barrier: on the 4096^2 road-like grid 1/4 of the
+// mean weight relaxes each edge about once yet runs 10x more generations.
+int32_t default_delta(const fg_graph *G) {
+    const double deg = G->info.n > 0 ? (double)G->info.m / (double)G->info.n : 1.0;
+    const double d = 8.0 * G->w_mean * std::max(1.0, deg);
+    return d >= (double)(kInf / 2) ? kInf / 2 : std::max(1, (int32_t)(d + 0.5));
 }
 
 fg_status run_query(const fg_graph *G, Algo algo, Mode mode, int32_t source, int32_t *out,
@@ -186,6 +204,7 @@ fg_status run_query(const fg_graph *G, Algo algo, Mode mode, int32_t source, int
     Params p;
     carve_query_workspace(wsbase, g, algo, mode, p);
     if (mode == kPull) p.tv = (algo == kCC) ? G->s : G->t;
+    p.delta = (opt && opt->delta > 0) ? opt->delta : default_delta(G);
     struct {
         char *base;
     } ws{wsbase};

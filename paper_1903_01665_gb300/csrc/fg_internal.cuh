@@ -61,6 +61,7 @@ struct fg_graph {
     // lazily computed diameter estimate and autotuned modes for fg_select_mode
     mutable std::mutex mu;
     mutable int32_t diam_est = -1;
+    double w_mean = 1.0;        // mean edge weight (bucket mode's default width)
     mutable int32_t tuned_mode[3] = {-1, -1, -1};
 };
 
@@ -83,10 +84,13 @@ struct Ctrl {
     int barriers;
     int done;                   // the fixpoint was reached
     int pull_rounds;            // pull mode: rounds that pulled
+    int far_size[3];            // bucket mode: far-list sizes, rotating by epoch
+    int far_min[3];             // bucket mode: smallest distance in each epoch's far list
+    int splits;                 // bucket mode: far-list splits (threshold moves)
 };
 
 enum Algo { kSSSP = 0, kBFS = 1, kCC = 2 };
-enum Mode { kVertexSync = 0, kVertexAsync = 1, kEdgeSync = 2, kEdgeAsync = 3, kPull = 5 };
+enum Mode { kVertexSync = 0, kVertexAsync = 1, kEdgeSync = 2, kEdgeAsync = 3, kPull = 5, kBucket = 6 };
 
 // worklist classes (vertex-async): low, mid, high chunks; edge-async uses class 0 only
 enum { kWlLow = 0, kWlMid = 1, kWlHigh = 2 };
@@ -103,6 +107,10 @@ struct Params {
     uint32_t *lb_off = nullptr; // edge-async: per-item local offsets
     uint32_t *lb_blk = nullptr; // edge-async: per-CTA totals
     int32_t *eflag = nullptr;   // edge-sync sparse rounds: round stamp per 128-edge warp tile
+    int32_t *far[2] = {};       // bucket mode: far lists by epoch parity
+    int32_t *far_mark = nullptr; // bucket mode: epoch in whose far list a vertex is
+    int32_t far_cap = 0;
+    int32_t delta = 0;          // bucket mode: bucket width
     int32_t source = 0;
     int32_t max_rounds = 0;
     unsigned long long timeout_ns = 0;
@@ -348,6 +356,7 @@ void carve_query_workspace(char *base, const View &g, Algo algo, Mode mode, Para
 fg_status ensure_transpose(const fg_graph *g);
 
 // queries (fg_fixpoint.cu)
+int32_t default_delta(const fg_graph *G);
 fg_status run_query(const fg_graph *g, Algo algo, Mode mode, int32_t source, int32_t *out,
                     const fg_options *opt, fg_stats *stats);
 fg_status run_sweep(const fg_graph *g, Mode mode, const int32_t *cur, int32_t *next,

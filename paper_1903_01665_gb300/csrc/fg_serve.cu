@@ -242,7 +242,7 @@ fg_status fg_server_submit(fg_server *s, const fg_query *q, uint64_t *ticket) {
     if (!s || !q) return fail(FG_ERR_INVALID_ARG, "NULL argument");
     if (!q->g || !q->out) return fail(FG_ERR_INVALID_ARG, "graph or output is NULL");
     if (q->algo < FG_ALGO_SSSP || q->algo > FG_ALGO_CC) return fail(FG_ERR_INVALID_ARG, "invalid algorithm");
-    if (q->mode < FG_VERTEX_SYNC || q->mode > FG_PULL) return fail(FG_ERR_INVALID_ARG, "invalid mode");
+    if (q->mode < FG_VERTEX_SYNC || q->mode > FG_BUCKET) return fail(FG_ERR_INVALID_ARG, "invalid mode");
     if (q->algo != FG_ALGO_CC && (q->src < 0 || q->src >= q->g->info.n))
         return fail(FG_ERR_INVALID_ARG, "source vertex outside [0, n)");
     if (q->g->device != s->device) return fail(FG_ERR_INVALID_ARG, "graph lives on another device");

@@ -7,8 +7,8 @@ import numpy as np
 
 import paper_1903_01665_gb300 as fg
 
-MODES = [fg.FG_VERTEX_SYNC, fg.FG_VERTEX_ASYNC, fg.FG_EDGE_SYNC, fg.FG_EDGE_ASYNC, fg.FG_PULL]
-MODE_IDS = ["vertex_sync", "vertex_async", "edge_sync", "edge_async", "pull"]
+MODES = [fg.FG_VERTEX_SYNC, fg.FG_VERTEX_ASYNC, fg.FG_EDGE_SYNC, fg.FG_EDGE_ASYNC, fg.FG_PULL, fg.FG_BUCKET]
+MODE_IDS = ["vertex_sync", "vertex_async", "edge_sync", "edge_async", "pull", "bucket"]
 ALGOS = {"sssp": fg.FG_ALGO_SSSP, "bfs": fg.FG_ALGO_BFS, "cc": fg.FG_ALGO_CC}
 
 

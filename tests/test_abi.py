@@ -48,7 +48,7 @@ int main(void) {
   printf("fg_options %zu\nfg_stats %zu\nfg_graph_info_t %zu\n", sizeof(fg_options), sizeof(fg_stats), sizeof(fg_graph_info_t));
   P(fg_options, stream); P(fg_options, max_rounds); P(fg_options, wait_timeout_ms);
   P(fg_options, blocks_per_sm); P(fg_options, inject_missing_arrival); P(fg_options, round_trace);
-  P(fg_options, round_trace_cap); P(fg_stats, barriers);
+  P(fg_options, round_trace_cap); P(fg_options, delta); P(fg_stats, barriers);
   P(fg_stats, mode); P(fg_stats, rounds); P(fg_stats, jump_passes); P(fg_stats, grid_blocks);
   P(fg_stats, vertices_processed); P(fg_stats, edges_relaxed); P(fg_stats, updates);
   P(fg_stats, pushes); P(fg_stats, scanned); P(fg_stats, kernel_ms);

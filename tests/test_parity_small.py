@@ -12,6 +12,7 @@ import pytest
 
 import graphgen as gg
 import oracle
+import paper_1903_01665_gb300 as fg
 from tests import pins
 from tests.gpu_util import ALGOS, MODE_IDS, MODES, graph_handle, run
 from tests.test_golden import HAND, parse_fixture
@@ -185,3 +186,16 @@ def test_invariants_on_results():
             pins.check_bfs_invariants(g.n, g.src, g.dst, 5, lv)
             lab, _ = run(h, g.n, ALGOS["cc"], 0, mode)
             pins.check_cc_invariants(g.n, g.src, g.dst, lab)
+
+
+@pytest.mark.parametrize("delta", [1, 7, 500, 2**30])
+def test_bucket_mode_any_width(delta):
+    """The bucketed SSSP reaches the same fixpoint whatever the bucket width:
+    1 (one distance per bucket), small, and one bucket holding everything."""
+    for g in (gg.grid(96, seed=31), gg.rmat(12, seed=32), gg.random_small(300, 2500, seed=33, wlo=0, whi=20)):
+        s = int(gg.sources(g, 1, seed=34)[0])
+        _, d = oracle.sssp(g.n, g.src, g.dst, g.w, s)
+        with graph_handle(g) as h:
+            got, st = run(h, g.n, ALGOS["sssp"], s, fg.FG_BUCKET, delta=delta)
+            np.testing.assert_array_equal(got, d)
+            assert st.mode == fg.FG_BUCKET
