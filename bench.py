@@ -426,7 +426,7 @@ def run_serving(device, full: bool = False, rates=(100, 1000, 10000), n_req: int
             row = {"rate_per_s": rate}
             for kind in ("batched", "one_at_a_time"):
                 if kind == "batched":
-                    st, srv = fg.fg_server_create(hbm_budget_bytes=16 << 30, max_inflight=4, max_wave=64)
+                    st, srv = fg.fg_server_create(hbm_budget_bytes=16 << 30, max_inflight=2, max_wave=64)
                 else:
                     st, srv = fg.fg_server_create(one_at_a_time=True)
                 fg.check(st)
@@ -620,7 +620,7 @@ def run_ours(args):
                "d2h_bytes_per_step": 4 * r.g.n * len(r.queries), "steps": k2}
 
     sweep = None if args.no_sweep else run_sweep_roofline(r, peaks[0])
-    extra = run_extra_modes(r, per_kernel, [fg.FG_PULL, fg.FG_BUCKET])
+    extra = None if args.no_extra else run_extra_modes(r, per_kernel, [fg.FG_PULL, fg.FG_BUCKET])
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -772,6 +772,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sweep", action="store_true", help="skip the all-active sweep roofline test")
+    ap.add_argument("--no-extra", action="store_true", help="skip the pull/bucket comparison on the workload")
     ap.add_argument("--no-grid-bucket", action="store_true", help="skip the bucketed-SSSP grid comparison")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload comparison")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving comparison")

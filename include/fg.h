@@ -307,10 +307,11 @@ fg_status fg_run_batch(const fg_query *queries, int32_t nq, const fg_batch_optio
  * the batched path).  Requests are queued by fg_server_submit from any host
  * thread; a native worker admits them in waves -- whenever one of
  * max_inflight wave slots is free and the device memory of the in-flight
- * queries' state stays within hbm_budget_bytes, up to max_wave requests from
- * the head of the queue are launched together on the slot's stream -- so
- * waves overlap on the device and new requests start as soon as a slot and
- * memory free up.  one_at_a_time = 1 serves the queue strictly in order, one
+ * queries' state stays within hbm_budget_bytes, the oldest pending request
+ * and later ones of the same kind (graph, algorithm, mode), up to max_wave,
+ * are launched together on the slot's stream -- so waves overlap on the
+ * device and new requests start as soon as a slot and memory free up.
+ * Requests on large graphs (exclusive_edges) run alone on the whole device.  one_at_a_time = 1 serves the queue strictly in order, one
  * request at a time, with the plain per-query kernel (the baseline).
  * A request's work is ordered after all work enqueued on the legacy default
  * stream before it was submitted (so outputs prepared there are safe); it
@@ -323,10 +324,16 @@ typedef struct fg_server fg_server;
 
 typedef struct {
     int64_t hbm_budget_bytes;   /* in-flight query state limit; 0 = 8 GiB */
-    int32_t max_inflight;       /* concurrent waves; 0 = 4 */
+    int32_t max_inflight;       /* concurrent waves; 0 = 2 */
     int32_t max_wave;           /* requests per wave at most; 0 = 64 */
     int32_t one_at_a_time;      /* nonzero: the one-query-at-a-time baseline */
     int32_t wait_timeout_ms;    /* bound on any device-side wait; 0 = 1000 ms */
+    int64_t exclusive_edges;    /* a request on a graph with at least this many edges (the
+                                   symmetrised count for CC) runs alone on the whole device
+                                   once the waves before it finish, with the plain per-query
+                                   kernel: such a query already fills the GPU, and sharing
+                                   SMs with other queries costs it L1 hits; 0 = 2^25,
+                                   < 0 = never */
 } fg_server_options;
 
 typedef struct {

@@ -93,7 +93,7 @@ class fg_batch_stats(ctypes.Structure):
 class fg_server_options(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
                 ("max_wave", ctypes.c_int32), ("one_at_a_time", ctypes.c_int32),
-                ("wait_timeout_ms", ctypes.c_int32)]
+                ("wait_timeout_ms", ctypes.c_int32), ("exclusive_edges", ctypes.c_int64)]
 
 
 class fg_completion(ctypes.Structure):
@@ -292,10 +292,11 @@ def fg_autotune(g, algo, src=0):
     return st, best.value, list(times)
 
 
-def fg_server_create(hbm_budget_bytes=0, max_inflight=0, max_wave=0, one_at_a_time=False, wait_timeout_ms=0):
+def fg_server_create(hbm_budget_bytes=0, max_inflight=0, max_wave=0, one_at_a_time=False, wait_timeout_ms=0,
+                     exclusive_edges=0):
     """Returns (status, server handle)."""
     o = fg_server_options(int(hbm_budget_bytes), int(max_inflight), int(max_wave), 1 if one_at_a_time else 0,
-                          int(wait_timeout_ms))
+                          int(wait_timeout_ms), int(exclusive_edges))
     h = _VP()
     st = load().fg_server_create(ctypes.byref(o), ctypes.byref(h))
     return st, (h.value if st == FG_OK else None)

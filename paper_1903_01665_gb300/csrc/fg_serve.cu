@@ -3,11 +3,17 @@
 // Requests (SSSP / BFS / CC on resident graphs) are submitted from any host
 // thread and queued.  A native worker thread admits them in waves: whenever a
 // wave slot is free and the HBM budget of the in-flight waves' query state
-// allows, the pending requests at the head of the queue (up to max_wave) are
-// launched as one batch on the slot's stream (fg_batch.cu), so waves overlap
-// on the device and requests arriving while others run start as soon as a
-// slot and memory free up.  Completion = the wave's results are in the
-// callers' outputs; latency is measured from submission to completion.
+// allows, the oldest pending request and the later ones of the same kind
+// (graph, algorithm, mode; up to max_wave) are launched as one batch on the
+// slot's stream (fg_batch.cu), so waves overlap on the device and requests
+// arriving while others run start as soon as a slot and memory free up.
+// Completion = the wave's results are in the callers' outputs; latency is
+// measured from submission to completion.
+//
+// A request on a large graph (exclusive_edges) is not batched: it runs alone
+// on the whole device with the plain per-query kernel as soon as the waves
+// admitted before it have finished (the queue stays first come, first
+// served).
 //
 // In one-at-a-time mode the worker serves the queue strictly one request at
 // a time with the plain per-query kernel (the baseline).
@@ -35,6 +41,7 @@ struct fg_server {
         fg_query q;
         Clock::time_point t_submit;
         size_t bytes;
+        bool exclusive;           // runs alone on the whole device
     };
     struct Wave {
         fg::BatchJob job;
@@ -136,18 +143,34 @@ void worker_main(fg_server *s) {
         }
         // admit new waves while a slot and the HBM budget allow
         while (!s->pending.empty() && (int)s->inflight.size() < max_inflight) {
+            if (s->pending.front().exclusive) {
+                if (!s->inflight.empty()) break;   // after the waves before it
+                serve_one_at_a_time(s, lk);
+                continue;
+            }
             int slot = 0;
             while (s->slot_busy[slot]) slot++;
+            // A wave holds requests of one kind (graph, algorithm, mode): the
+            // oldest pending request and the later ones of its kind.  Mixed
+            // waves finish with their slowest kind while the CTAs of the
+            // others idle, and mix hot sets in each SM's L1.
             std::unique_ptr<fg_server::Wave> w(new fg_server::Wave());
             size_t bytes = 0;
-            while (!s->pending.empty() && (int)w->reqs.size() < max_wave) {
-                const fg_server::Req &r = s->pending.front();
+            const fg_query head = s->pending.front().q;
+            size_t window = std::min(s->pending.size(), (size_t)max_wave * 8);   // requests scanned
+            for (size_t i = 0; i < window && i < s->pending.size() && (int)w->reqs.size() < max_wave;) {
+                const fg_server::Req &r = s->pending[i];
+                if (r.exclusive || r.q.g != head.g || r.q.algo != head.algo || r.q.mode != head.mode) {
+                    i++;
+                    continue;
+                }
                 const bool fits = s->bytes_inflight + bytes + r.bytes <= (size_t)s->opt.hbm_budget_bytes;
                 const bool alone = s->inflight.empty() && w->reqs.empty();   // always make progress
                 if (!fits && !alone) break;
                 bytes += r.bytes;
                 w->reqs.push_back(r);
-                s->pending.pop_front();
+                s->pending.erase(s->pending.begin() + (long)i);
+                window--;   // the scan window shrinks with the queue; i now names the next request
             }
             if (w->reqs.empty()) break;
             w->bytes = bytes;
@@ -203,7 +226,11 @@ fg_status fg_server_create(const fg_server_options *opt, fg_server **out) {
     if (o.hbm_budget_bytes < 0 || o.max_inflight < 0 || o.max_wave < 0 || o.wait_timeout_ms < 0)
         return fail(FG_ERR_INVALID_ARG, "negative option");
     if (o.hbm_budget_bytes == 0) o.hbm_budget_bytes = (int64_t)8 << 30;
-    if (o.max_inflight == 0) o.max_inflight = 4;
+    if (o.exclusive_edges == 0) o.exclusive_edges = (int64_t)1 << 25;
+    // two waves in flight: a new wave starts while one runs; more made the
+    // waves' kernels crowd each other's SMs (L1, CTA budget) and cost
+    // throughput on the R-MAT 20-22 + grid mix
+    if (o.max_inflight == 0) o.max_inflight = 2;
     if (o.max_wave == 0) o.max_wave = 64;
     if (o.one_at_a_time) o.max_inflight = 1;
     int dev = -1;
@@ -253,7 +280,9 @@ fg_status fg_server_submit(fg_server *s, const fg_query *q, uint64_t *ticket) {
         if (st != FG_OK) return st;
     }
     qq.mode = (int32_t)m;
-    fg_server::Req r{0, qq, Clock::now(), request_bytes(qq, (Mode)m)};
+    const int64_t edges = (qq.algo == FG_ALGO_CC) ? qq.g->s.m : qq.g->g.m;
+    const bool exclusive = s->opt.exclusive_edges > 0 && edges >= s->opt.exclusive_edges;
+    fg_server::Req r{0, qq, Clock::now(), request_bytes(qq, (Mode)m), exclusive};
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->stop) return fail(FG_ERR_INVALID_ARG, "server is shutting down");

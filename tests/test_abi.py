@@ -64,7 +64,7 @@ int main(void) {
   P(fg_batch_stats, kernel_ms); P(fg_batch_stats, launches); P(fg_batch_stats, teams); P(fg_batch_stats, ctas);
   printf("fg_server_options %zu\nfg_completion %zu\n", sizeof(fg_server_options), sizeof(fg_completion));
   P(fg_server_options, hbm_budget_bytes); P(fg_server_options, max_inflight); P(fg_server_options, max_wave);
-  P(fg_server_options, one_at_a_time); P(fg_server_options, wait_timeout_ms);
+  P(fg_server_options, one_at_a_time); P(fg_server_options, wait_timeout_ms); P(fg_server_options, exclusive_edges);
   P(fg_completion, ticket); P(fg_completion, status); P(fg_completion, wave_size); P(fg_completion, latency_ms);
   return 0;
 }

@@ -76,6 +76,29 @@ def test_results_in_the_mix_equal_results_alone(setup):
     assert all(c[3] > 0 for c in comps)
 
 
+def test_large_graphs_run_alone_and_match(setup):
+    """Requests on graphs with at least exclusive_edges edges run alone (wave
+    size 1) on the whole device between the waves; every result is the same
+    as alone."""
+    graphs, handles = setup
+    reqs = _requests(graphs, 120, seed=8)
+    cut = graphs[1].m   # rmat-15 and larger run alone
+    outs, comps = _serve(handles, graphs, reqs, max_inflight=3, max_wave=16, exclusive_edges=cut)
+    want = _alone(graphs, handles, reqs)
+    for (gi, algo, s), out in zip(reqs, outs):
+        np.testing.assert_array_equal(out.cpu().numpy(), want[(gi, algo, s)])
+    ticket_to_req = {}
+    by_ticket = {c[0]: c for c in comps}
+    first = min(by_ticket)
+    for i, (gi, algo, s) in enumerate(reqs):
+        ticket_to_req[first + i] = (gi, algo)
+    for t, c in by_ticket.items():
+        gi, algo = ticket_to_req[t]
+        edges = 2 * graphs[gi].m if algo == 2 else graphs[gi].m
+        if edges >= cut:
+            assert c[2] == 1, "a large-graph request must run alone"
+
+
 def test_tiny_budget_serves_one_per_wave(setup):
     graphs, handles = setup
     reqs = _requests(graphs, 40, seed=6)
