@@ -45,9 +45,9 @@ ALGO_NAMES = ["sssp", "bfs", "cc"]
 # is unchanged (sha256 over fg_internal.cuh, fg_device.cuh and fg_fixpoint.cu
 # at capture time).
 NCU_TRAFFIC: dict = {
-    # profiles/sssp_edge_sync_rmat22.md: one launch, first bench source, R-MAT 22
-    "fixpoint_kernel<sssp,edge_sync>": {"bytes_per_launch": 6907746560 + 466209280,
-                                        "src_sha": "b504cc75616bdffc"},
+    # profiles/sssp_edge_async_rmat22.md: one launch, first seeded source, R-MAT 22
+    "fixpoint_kernel<sssp,edge_async>": {"bytes_per_launch": 3972096768 + 256009728,
+                                         "src_sha": "1ad1f532eccc1140"},
 }
 
 

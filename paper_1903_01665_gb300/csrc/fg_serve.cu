@@ -148,6 +148,12 @@ void worker_main(fg_server *s) {
                 serve_one_at_a_time(s, lk);
                 continue;
             }
+            // a lone request on an idle device: the plain per-query kernel
+            // (a batch of one costs its planning and staging for nothing)
+            if (s->pending.size() == 1 && s->inflight.empty()) {
+                serve_one_at_a_time(s, lk);
+                continue;
+            }
             int slot = 0;
             while (s->slot_busy[slot]) slot++;
             // A wave holds requests of one kind (graph, algorithm, mode): the
