@@ -435,24 +435,84 @@ struct ClassPush {
     }
 };
 
-// edge-async: one list of vertices with >= 1 out-edge
-struct ListPush {
+// edge-async: the worklist with each item's global edge offset.  A warp's
+// staged block of items reserves its slots and its edges in one 64-bit
+// atomicAdd on (edges << 32 | items), so the next generation's load balance
+// needs no separate prefix pass over the worklist.
+struct LbPush {
+    const uint32_t *__restrict__ row_off;
     const uint8_t *__restrict__ vclass;
     int32_t *list;
-    int *size;
+    uint32_t *off;
+    unsigned long long *pack;
     int32_t cap;
     WarpBuf *buf;
     Ctrl *c;
 
+    __device__ __forceinline__ void flush_block(int cnt) const {
+        __syncwarp();
+        const unsigned lane = lane_id();
+        constexpr int kPer = kPushBuf / 32;   // contiguous items per lane
+        uint32_t deg[kPer], sum = 0;
+#pragma unroll
+        for (int k = 0; k < kPer; k++) {
+            const int i = (int)lane * kPer + k;
+            deg[k] = 0;
+            if (i < cnt) {
+                const int32_t v = buf->item[i];
+                deg[k] = __ldg(row_off + v + 1) - __ldg(row_off + v);
+            }
+            sum += deg[k];
+        }
+        const uint32_t incl = warp_inclusive_scan(sum);
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(pack, ((unsigned long long)total << 32) | (unsigned)cnt);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const uint32_t ibase = (uint32_t)base, ebase = (uint32_t)(base >> 32);
+        uint32_t run = ebase + incl - sum;
+#pragma unroll
+        for (int k = 0; k < kPer; k++) {
+            const int i = (int)lane * kPer + k;
+            if (i < cnt) {
+                const uint32_t pos = ibase + (uint32_t)i;
+                if (pos < (uint32_t)cap) {
+                    list[pos] = buf->item[i];
+                    off[pos] = run;
+                } else {
+                    atomicOr(&c->status, kStWorklist);
+                }
+            }
+            run += deg[k];
+        }
+        __syncwarp();
+    }
     __device__ __forceinline__ void operator()(bool want, int32_t v, Acc &a) const {
         bool ok = false;
         if (want) {
             ok = __ldg(vclass + v) != 0;
             if (ok) a.pushes++;
         }
-        buffered_append(ok, v, buf, list, size, cap, c);
+        const unsigned bal = __ballot_sync(0xffffffffu, ok);
+        if (bal == 0) return;
+        const int n = __popc(bal);
+        int cnt = buf->count;
+        if (cnt + n > kPushBuf) {
+            flush_block(cnt);
+            cnt = 0;
+        }
+        if (ok) buf->item[cnt + __popc(bal & lanemask_lt())] = v;
+        __syncwarp();
+        if (lane_id() == 0) buf->count = cnt + n;
+        __syncwarp();
     }
-    __device__ __forceinline__ void flush() const { buffered_flush(buf, list, size, cap, c); }
+    __device__ __forceinline__ void flush() const {
+        const int cnt = buf->count;
+        if (cnt > 0) flush_block(cnt);
+        __syncwarp();
+        if (lane_id() == 0) buf->count = 0;
+        __syncwarp();
+    }
 };
 
 // ================================================================ batched relaxation
@@ -724,91 +784,25 @@ __device__ __forceinline__ void expand_vertices(const Team &t, const uint32_t *_
 }
 
 // Load-balanced expansion of a vertex worklist to its out-edges (edge-async).
-// Phase 1 (before the caller's grid barrier): each CTA takes a contiguous
-// slice of the worklist and writes the exclusive prefix sum of its items'
-// degrees (lb_off) and its slice total (lb_blk).
-__device__ __forceinline__ void lb_prefix(const Team &t, const uint32_t *__restrict__ row_off, const int32_t *items, int n_items,
-                                          uint32_t *lb_off, uint32_t *lb_blk) {
-    __shared__ uint32_t s_tot;
-    __shared__ uint32_t warp_tot[kWarps];
-    int S = (n_items + t.size - 1) / t.size;
-    int lo = min(n_items, (int)t.rank * S), hi = min(n_items, lo + S);
-    uint32_t run = 0;
-    for (int t0 = lo; t0 < hi; t0 += kBlock) {
-        int i = t0 + threadIdx.x;
-        uint32_t d = 0;
-        if (i < hi) {
-            int32_t u = ldcg(items + i);
-            d = __ldg(row_off + u + 1) - __ldg(row_off + u);
-        }
-        uint32_t inc = warp_inclusive_scan(d);
-        int wid = threadIdx.x >> 5;
-        if (lane_id() == 31) warp_tot[wid] = inc;
-        __syncthreads();
-        if (wid == 0) {
-            uint32_t t = lane_id() < (unsigned)kWarps ? warp_tot[lane_id()] : 0u;
-            uint32_t ti = warp_inclusive_scan(t);
-            if (lane_id() < (unsigned)kWarps) warp_tot[lane_id()] = ti - t;
-            if (lane_id() == kWarps - 1) s_tot = ti;
-        }
-        __syncthreads();
-        if (i < hi) lb_off[i] = run + warp_tot[wid] + inc - d;
-        run += s_tot;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) lb_blk[t.rank] = run;
-}
-
-constexpr int kMaxGrid = 152 * 8;   // persistent CTAs (lb prefix table size)
-
-// Phase 2 (after the barrier): the edge space [0, T) is split evenly over the
-// CTAs; each CTA walks its range in tiles, staging up to kBlock items'
-// offsets, row starts and values in shared memory, and every thread finds the
-// owner of its edges by binary search in shared memory.
-template <class OP, class PUSH>
+// goff(i) is item i's global edge offset (non-decreasing in i) and T the
+// worklist's edge total.  The edge space [0, T) is split evenly over the
+// CTAs; each CTA finds the item holding its first edge by binary search,
+// stages a window of up to kBlock items' offsets, row starts and values in
+// shared memory, and relaxes the window's edges in 1024-edge sub-tiles: each
+// thread takes four consecutive edges, finds the first one's owner by binary
+// search in the window and walks on from there.
+template <class GOFF, class OP, class PUSH>
 __device__ __forceinline__ void lb_expand(const Team &t, const uint32_t *__restrict__ row_off, const int32_t *__restrict__ col,
-                                          const int32_t *items, int n_items, const uint32_t *lb_off,
-                                          const uint32_t *lb_blk, const OP &op, const PUSH &push, Acc &a) {
-    __shared__ uint32_t sP[kMaxGrid + 1];
+                                          const int32_t *items, int n_items, const GOFF &goff, uint32_t T,
+                                          const OP &op, const PUSH &push, Acc &a) {
     __shared__ uint32_t s_goff[kBlock + 1];
     __shared__ uint32_t s_rb[kBlock];
     __shared__ int32_t s_val[kBlock];
     __shared__ int s_i0;
     const int G = t.size;
-    // exclusive scan of the slice totals, redundantly in every CTA
-    {
-        __shared__ uint32_t warp_tot[kWarps];
-        __shared__ uint32_t carry;
-        if (threadIdx.x == 0) carry = 0;
-        __syncthreads();
-        for (int t0 = 0; t0 < G; t0 += kBlock) {
-            int i = t0 + threadIdx.x;
-            uint32_t x = i < G ? ldcg((const int32_t *)lb_blk + i) : 0u;
-            uint32_t inc = warp_inclusive_scan(x);
-            int wid = threadIdx.x >> 5;
-            if (lane_id() == 31) warp_tot[wid] = inc;
-            __syncthreads();
-            if (wid == 0) {
-                uint32_t t = lane_id() < (unsigned)kWarps ? warp_tot[lane_id()] : 0u;
-                uint32_t ti = warp_inclusive_scan(t);
-                if (lane_id() < (unsigned)kWarps) warp_tot[lane_id()] = ti - t;
-            }
-            __syncthreads();
-            if (i < G) sP[i] = carry + warp_tot[wid] + inc - x;
-            __syncthreads();
-            if (threadIdx.x == kBlock - 1) carry += warp_tot[wid] + inc;
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) sP[G] = carry;
-        __syncthreads();
-    }
-    const uint32_t T = sP[G];
-    if (T == 0) return;
-    const int S = (n_items + G - 1) / G;
+    if (T == 0 || n_items == 0) return;
     const uint64_t lo = (uint64_t)T * t.rank / G, hi = (uint64_t)T * (t.rank + 1) / G;
     if (lo >= hi) return;
-    // global offset of item i
-    auto goff = [&](int i) -> uint32_t { return sP[i / S] + (uint32_t)ldcg((const int32_t *)lb_off + i); };
     if (threadIdx.x == 0) {
         // item containing edge lo: last item with goff <= lo
         int l = 0, r = n_items - 1;
@@ -819,9 +813,6 @@ __device__ __forceinline__ void lb_expand(const Team &t, const uint32_t *__restr
         s_i0 = l;
     }
     __syncthreads();
-    // A window of up to kBlock items -- their global edge offsets, row starts
-    // and values -- is staged once and serves every 1024-edge sub-tile of
-    // the CTA's range that falls inside it.
     uint32_t t0 = (uint32_t)lo;
     while (t0 < (uint32_t)hi) {
         const int i0 = s_i0;
@@ -843,22 +834,26 @@ __device__ __forceinline__ void lb_expand(const Team &t, const uint32_t *__restr
         const uint32_t wend = min((uint32_t)hi, s_goff[cnt]);   // the window's edges end here
         while (t0 < wend) {
             const uint32_t t1 = min(wend, t0 + (uint32_t)(kBlock * kU));
+            const uint32_t x0 = t0 + kU * threadIdx.x;
             uint32_t e[kU];
             int32_t val[kU];
             bool in[kU];
-            int l = 0;   // owners are non-decreasing in j: each search starts at the last one
+            int l = 0;
+            if (x0 < t1) {
+                int r = cnt - 1;
+                while (l < r) {
+                    int mdl = (l + r + 1) >> 1;
+                    if (s_goff[mdl] <= x0) l = mdl; else r = mdl - 1;
+                }
+            }
 #pragma unroll
             for (int j = 0; j < kU; j++) {
-                uint32_t x = t0 + j * kBlock + threadIdx.x;
+                const uint32_t x = x0 + j;
                 in[j] = x < t1;
                 e[j] = 0;
                 val[j] = 0;
                 if (in[j]) {
-                    int r = cnt - 1;
-                    while (l < r) {
-                        int mdl = (l + r + 1) >> 1;
-                        if (s_goff[mdl] <= x) l = mdl; else r = mdl - 1;
-                    }
+                    while (l + 1 < cnt && s_goff[l + 1] <= x) l++;   // owners are consecutive
                     e[j] = s_rb[l] + (x - s_goff[l]);
                     val[j] = s_val[l];
                     a.edges++;
@@ -1501,7 +1496,8 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
         if (d > 0) {
             if (MODE == kEdgeAsync) {
                 p.wl[0][0][0] = s;
-                c->wl_size[0][0] = 1;
+                p.lb_off[0][0] = 0;
+                c->wl_pack[0] = ((unsigned long long)d << 32) | 1u;
             } else if (d < (uint32_t)kLowMax) {
                 p.wl[0][kWlLow][0] = s;
                 c->wl_size[0][kWlLow] = 1;
@@ -1652,6 +1648,9 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
             const bool initial_cc = (ALGO == kCC && gen == 0);
             int n_in[3];
             for (int k = 0; k < 3; k++) n_in[k] = __ldcg(&c->wl_size[in_slot][k]);
+            // edge-async: items and their edge total come packed in one word
+            const unsigned long long pk = MODE == kEdgeAsync ? __ldcg(&c->wl_pack[in_slot]) : 0ull;
+            if (MODE == kEdgeAsync) n_in[0] = (int)(uint32_t)pk;
             if (initial_cc) {
                 if (MODE == kEdgeAsync) {
                     n_in[0] = g.n_nz; n_in[1] = n_in[2] = 0;
@@ -1673,8 +1672,10 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
             }
             if (!split) work_gens++;
             rounds = gen + 1;
-            if (tid == 0)
+            if (tid == 0) {
                 for (int k = 0; k < 3; k++) c->wl_size[(gen + 2) % 3][k] = 0;
+                c->wl_pack[(gen + 2) % 3] = 0;
+            }
             const int pi = gen & 1, po = pi ^ 1;
             int *osize = c->wl_size[out_slot];
             if (split) {
@@ -1749,16 +1750,21 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
                 push.flush();
             } else {
                 const int32_t *items = initial_cc ? g.nz : p.wl[pi][0];
-                lb_prefix(t, g.row_off, items, n_in[0], p.lb_off, p.lb_blk);
-                if (!sync_()) break;
-                ListPush push{g.vclass, p.wl[po][0], &osize[0], p.wl_cap[0], &wb[0], c};
-                a.verts += 0;
+                const uint32_t *ioff = p.lb_off[pi];
+                const uint32_t T = initial_cc ? (uint32_t)g.m : (uint32_t)(pk >> 32);
+                // global edge offset of item i (CC's first generation: all
+                // vertices with out-edges, whose offsets are their row starts)
+                auto goff = [&](int i) -> uint32_t {
+                    return initial_cc ? __ldg(g.row_off + __ldg(g.nz + i)) : (uint32_t)ldcg((const int32_t *)ioff + i);
+                };
+                LbPush push{g.row_off, g.vclass, p.wl[po][0], p.lb_off[po], &c->wl_pack[out_slot], p.wl_cap[0],
+                            &wb[0], c};
                 if (ALGO == kBFS) {
                     BfsAsyncOp op{p.A, gen};
-                    lb_expand(t, g.row_off, g.col, items, n_in[0], p.lb_off, p.lb_blk, op, push, a);
+                    lb_expand(t, g.row_off, g.col, items, n_in[0], goff, T, op, push, a);
                 } else {
                     AsyncOp<ALGO> op{g.w, p.A, p.S0, gen};
-                    lb_expand(t, g.row_off, g.col, items, n_in[0], p.lb_off, p.lb_blk, op, push, a);
+                    lb_expand(t, g.row_off, g.col, items, n_in[0], goff, T, op, push, a);
                 }
                 push.flush();
                 if (tid == 0) a.verts += (unsigned long long)n_in[0];

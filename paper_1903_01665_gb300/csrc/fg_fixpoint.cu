@@ -122,7 +122,7 @@ size_t query_workspace_bytes(const View &g, Algo algo, Mode mode) {
     if (!sync) {
         if (algo != kBFS) need += Workspace::need(n, 4);
         for (int k = 0; k < 3; k++) need += 2 * Workspace::need(wl_cap_of(g, mode, k), 4);
-        if (mode == kEdgeAsync) need += Workspace::need(wl_cap_of(g, mode, 0), 4) + Workspace::need(kMaxGrid, 4);
+        if (mode == kEdgeAsync) need += 2 * Workspace::need(wl_cap_of(g, mode, 0), 4);
         if (mode == kBucket && algo == kSSSP) need += 3 * Workspace::need(n, 4);
     }
     return need;
@@ -150,8 +150,8 @@ void carve_query_workspace(char *base, const View &g, Algo algo, Mode mode, Para
             for (int k = 0; k < 3; k++) p.wl[par][k] = ws.take<int32_t>(wl_cap_of(g, mode, k));
         for (int k = 0; k < 3; k++) p.wl_cap[k] = (int32_t)wl_cap_of(g, mode, k);
         if (mode == kEdgeAsync) {
-            p.lb_off = ws.take<uint32_t>(wl_cap_of(g, mode, 0));
-            p.lb_blk = ws.take<uint32_t>(kMaxGrid);
+            p.lb_off[0] = ws.take<uint32_t>(wl_cap_of(g, mode, 0));
+            p.lb_off[1] = ws.take<uint32_t>(wl_cap_of(g, mode, 0));
         }
         if (mode == kBucket && algo == kSSSP) {
             p.far[0] = ws.take<int32_t>(n);

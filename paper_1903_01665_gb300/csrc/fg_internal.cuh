@@ -20,6 +20,7 @@ constexpr int kLowMax = 32;            // low bucket: 1 .. 31 out-edges (thread 
 constexpr int kMidMax = 1024;          // mid bucket: 32 .. 1023 (warp per vertex)
 constexpr int kChunk = 2048;           // high bucket: >= 1024, split in 2048-edge chunks (CTA each)
 constexpr int32_t kInf = FG_INF;
+constexpr int kMaxGrid = 152 * 8;      // persistent CTAs of one launch at most
 constexpr int kWTile = 128;            // edge-sync: edges per warp tile (the streamed and flagged unit)
 
 // device status bits (Ctrl::status)
@@ -79,6 +80,7 @@ struct Ctrl {
     int changed[3];             // per-round change counters, rotating slots
     int jchanged[3];            // per-pass pointer-jumping change counters
     int wl_size[3][4];          // async: worklist sizes per generation slot and class
+    unsigned long long wl_pack[3];   // edge-async: (edges << 32 | items) per generation slot
     unsigned long long st_vertices, st_edges, st_updates, st_pushes, st_scanned;
     unsigned long long st_pulled;   // pull mode: in-edges read by pull rounds
     int barriers;
@@ -104,8 +106,7 @@ struct Params {
     int32_t *S1 = nullptr;      //   async: S0 = push stamp (dedup)
     int32_t *wl[2][3] = {};     // async worklists [in/out parity][class]; high as int2 pairs
     int32_t wl_cap[3] = {};     // capacity per class (in int32 slots)
-    uint32_t *lb_off = nullptr; // edge-async: per-item local offsets
-    uint32_t *lb_blk = nullptr; // edge-async: per-CTA totals
+    uint32_t *lb_off[2] = {};   // edge-async: global edge offset of each worklist item, by parity
     int32_t *eflag = nullptr;   // edge-sync sparse rounds: round stamp per 128-edge warp tile
     int32_t *far[2] = {};       // bucket mode: far lists by epoch parity
     int32_t *far_mark = nullptr; // bucket mode: epoch in whose far list a vertex is
