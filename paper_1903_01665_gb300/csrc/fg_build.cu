@@ -67,16 +67,16 @@ __global__ void k_histogram(int64_t m, const int32_t *__restrict__ keys, uint32_
         atomicAdd(&cnt[keys[e]], 1u);
 }
 
+// (the source array of the result is filled afterwards from the row
+// offsets, with sequential writes, by k_src_from_rows)
 __global__ void k_scatter_coo(int64_t m, const int32_t *__restrict__ s, const int32_t *__restrict__ d,
-                              const int32_t *__restrict__ w, uint32_t *cursor, int32_t *col,
-                              int32_t *wout, int32_t *srcout) {
+                              const int32_t *__restrict__ w, uint32_t *cursor, int32_t *col, int32_t *wout) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
         int32_t u = s[e];
         uint32_t pos = atomicAdd(&cursor[u], 1u);
         col[pos] = d[e];
         wout[pos] = w ? w[e] : 1;
-        srcout[pos] = u;
     }
 }
 
@@ -129,17 +129,25 @@ __global__ void k_sym_degree(int32_t n, const uint32_t *__restrict__ ro, uint32_
         deg[v] += ro[v + 1] - ro[v];
 }
 
+// Symmetrised adjacency of u: its out-edges first, in CSR order (their
+// positions follow from the offsets, written coalesced), then its in-edges
+// (placed by an atomic cursor that starts after the out-edges).
+__global__ void k_sym_cursor(int32_t n, const uint32_t *__restrict__ sro, const uint32_t *__restrict__ ro,
+                             uint32_t *cursor) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        cursor[v] = sro[v] + (ro[v + 1] - ro[v]);
+}
+
 __global__ void k_scatter_sym(int64_t m, const int32_t *__restrict__ src, const int32_t *__restrict__ col,
-                              uint32_t *cursor, int32_t *scol, int32_t *ssrc) {
+                              const uint32_t *__restrict__ ro, const uint32_t *__restrict__ sro, uint32_t *cursor,
+                              int32_t *scol) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
-        int32_t u = src[e], v = col[e];
-        uint32_t p = atomicAdd(&cursor[u], 1u);
-        scol[p] = v;
-        ssrc[p] = u;
-        uint32_t q = atomicAdd(&cursor[v], 1u);
+        const int32_t u = src[e], v = col[e];
+        scol[sro[u] + ((uint32_t)e - ro[u])] = v;
+        const uint32_t q = atomicAdd(&cursor[v], 1u);
         scol[q] = u;
-        ssrc[q] = v;
     }
 }
 
@@ -476,7 +484,12 @@ fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const i
                 if (m > 0) { k_histogram<<<grid_for(m), kBlock, 0, b.st>>>(m, d_src, cnt); count_launch(); }
                 b.check(exclusive_scan(cnt, ro, n, b.st), "scan");
                 b.check(cudaMemcpyAsync(cursor, ro, ((size_t)n + 1) * sizeof(uint32_t), cudaMemcpyDeviceToDevice, b.st), "copy");
-                if (m > 0) { k_scatter_coo<<<grid_for(m), kBlock, 0, b.st>>>(m, d_src, d_dst, d_w, cursor, col, wt, esrc); count_launch(); }
+                if (m > 0) {
+                    k_scatter_coo<<<grid_for(m), kBlock, 0, b.st>>>(m, d_src, d_dst, d_w, cursor, col, wt);
+                    count_launch();
+                    k_src_from_rows<<<grid_for((int64_t)n * 32), kBlock, 0, b.st>>>(n, ro, esrc);
+                    count_launch();
+                }
                 b.check(cudaGetLastError(), "scatter");
             }
             if (cnt) cudaFreeAsync(cnt, b.st);
@@ -506,8 +519,14 @@ fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const i
             k_sym_degree<<<grid_for(n), kBlock, 0, b.st>>>(n, ro, deg);
             count_launch();
             b.check(exclusive_scan(deg, sro, n, b.st), "scan");
-            b.check(cudaMemcpyAsync(cursor, sro, ((size_t)n + 1) * sizeof(uint32_t), cudaMemcpyDeviceToDevice, b.st), "copy");
-            if (m > 0) { k_scatter_sym<<<grid_for(m), kBlock, 0, b.st>>>(m, esrc, col, cursor, scol, ssrc); count_launch(); }
+            k_sym_cursor<<<grid_for(n), kBlock, 0, b.st>>>(n, sro, ro, cursor);
+            count_launch();
+            if (m > 0) {
+                k_scatter_sym<<<grid_for(m), kBlock, 0, b.st>>>(m, esrc, col, ro, sro, cursor, scol);
+                count_launch();
+                k_src_from_rows<<<grid_for((int64_t)n * 32), kBlock, 0, b.st>>>(n, sro, ssrc);
+                count_launch();
+            }
             b.check(cudaGetLastError(), "symmetrise");
         }
         if (deg) cudaFreeAsync(deg, b.st);

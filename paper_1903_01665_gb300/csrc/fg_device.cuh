@@ -1405,14 +1405,17 @@ __device__ __forceinline__ bool stream_flagged_edges(const Team &t, uint32_t &us
 }
 
 // ================================================================ the kernel
-// Resident CTAs per SM the register budget is sized for: the synchronous
-// modes gain from more warps in flight; the worklist modes do not; the
-// edge-sync kernels keep their tile state in 64 registers (four CTAs).
+// Resident CTAs per SM the register budget is sized for.  The vertex-sync,
+// pull and worklist kernels gain from more warps in flight (their gathers are
+// latency-bound: 6 CTAs at 40 registers beat 4 at 64 by 10-30 % on R-MAT 22
+// despite a few spilled registers); the edge-sync kernels keep their tile
+// state in 64 registers (four CTAs; five at 48 registers spilled and ran 40 %
+// slower).
 #ifndef FG_SYNC_MIN_BLOCKS
 #define FG_SYNC_MIN_BLOCKS 6
 #endif
 #ifndef FG_ASYNC_MIN_BLOCKS
-#define FG_ASYNC_MIN_BLOCKS 4
+#define FG_ASYNC_MIN_BLOCKS 6
 #endif
 #ifndef FG_PULL_SHIFT_BFS
 #define FG_PULL_SHIFT_BFS 2
@@ -1426,17 +1429,24 @@ __device__ __forceinline__ bool stream_flagged_edges(const Team &t, uint32_t &us
 #ifndef FG_SPARSE_SHIFT
 #define FG_SPARSE_SHIFT 0
 #endif
+// the bucketed mode runs many generations with small worklists: fewer CTAs
+// pay less per barrier (4 CTAs: 10.6 ms on the 4096^2 grid, 6: 11.9 ms)
+#ifndef FG_BUCKET_MIN_BLOCKS
+#define FG_BUCKET_MIN_BLOCKS 4
+#endif
 #ifndef FG_PULL_MIN_BLOCKS
-#define FG_PULL_MIN_BLOCKS 4
+#define FG_PULL_MIN_BLOCKS 6
 #endif
 #ifndef FG_EDGE_SYNC_MIN_BLOCKS
 #define FG_EDGE_SYNC_MIN_BLOCKS 4
 #endif
 template <int MODE>
-constexpr int min_blocks() {  // kBucket: as the other worklist modes
+constexpr int min_blocks() {
     return MODE == kVertexSync ? FG_SYNC_MIN_BLOCKS
-                               : (MODE == kEdgeSync ? FG_EDGE_SYNC_MIN_BLOCKS
-                                                    : (MODE == kPull ? FG_PULL_MIN_BLOCKS : FG_ASYNC_MIN_BLOCKS));
+         : MODE == kEdgeSync   ? FG_EDGE_SYNC_MIN_BLOCKS
+         : MODE == kPull       ? FG_PULL_MIN_BLOCKS
+         : MODE == kBucket     ? FG_BUCKET_MIN_BLOCKS
+                               : FG_ASYNC_MIN_BLOCKS;
 }
 
 // The whole query -- init, rounds, convergence -- run by one team of CTAs
