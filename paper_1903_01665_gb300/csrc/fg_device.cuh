@@ -162,8 +162,11 @@ struct BfsSyncOp {
         c = lev + 1;
         return true;
     }
-    // a source's level was set in an earlier round (L1 is safe); the probe
-    // reads levels written during this round, through L2
+    // A source's level was set in an earlier round, so L1 is exact for it.
+    // The probe may also go through L1: a stale copy can only show INF for a
+    // vertex another thread set to lev+1 in this round, and then the store
+    // below writes that same level again (the counters count it twice; the
+    // result and the no-change test are unaffected).
     __device__ __forceinline__ void load_act(int32_t u, int32_t &s, int32_t &v) const {
         v = ldca(L + u);
         s = v;
@@ -173,7 +176,7 @@ struct BfsSyncOp {
         c = lev + 1;
         return true;
     }
-    __device__ __forceinline__ int32_t probe(int32_t v) const { return ldcg(L + v); }
+    __device__ __forceinline__ int32_t probe(int32_t v) const { return ldca(L + v); }
     __device__ __forceinline__ bool commit(int32_t v, int32_t c, int32_t pv, Acc &a) const {
         if (pv > c) {
             stcg(L + v, c);
