@@ -45,9 +45,11 @@ ALGO_NAMES = ["sssp", "bfs", "cc"]
 # is unchanged (sha256 over fg_internal.cuh, fg_device.cuh and fg_fixpoint.cu
 # at capture time).
 NCU_TRAFFIC: dict = {
-    # profiles/sssp_edge_async_rmat22.md: one launch, first seeded source, R-MAT 22
-    "fixpoint_kernel<sssp,edge_async>": {"bytes_per_launch": 3972096768 + 256009728,
-                                         "src_sha": "1ad1f532eccc1140"},
+    # profiles/sssp_edge_rmat22.md: one launch each, first seeded source, R-MAT 22
+    "fixpoint_kernel<sssp,edge_async>": {"bytes_per_launch": 3358194176 + 286504704,
+                                         "src_sha": "47407d26e0ed02c6"},
+    "fixpoint_kernel<sssp,edge_sync>": {"bytes_per_launch": 5332451328 + 202576896,
+                                        "src_sha": "47407d26e0ed02c6"},
 }
 
 
