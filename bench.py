@@ -14,6 +14,12 @@ C ABI with pinned host buffers (graph upload and result downloads inside the
 timed region).  Under torchrun, every rank runs an independent replica
 (the method shards by independent queries; no data-path collective).
 
+Besides the step, the JSON line carries: the all-active sweep roofline test
+(``sweep_roofline``), the pull and bucket modes against the best paper mode
+on the same queries (``extra_modes``), the bucketed SSSP on the 4096^2 grid
+(``grid_bucket``), the batched workload (``batched``) and the serving
+comparison (``serving``); each can be skipped with its ``--no-...`` flag.
+
 ``--impl reference`` times the CPU oracle (single thread) on a bounded sample
 of the same workload instead.
 """

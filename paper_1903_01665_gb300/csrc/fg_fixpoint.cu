@@ -111,7 +111,8 @@ int64_t wl_cap_of(const View &g, Mode mode, int k) {
 }  // namespace
 
 // Bytes of one query's device state (control block, value buffers, stamps,
-// worklists, prefix arrays, chunk flags), each piece 256-byte aligned.
+// worklists, edge offsets, warp-tile flags, far lists), each piece 256-byte
+// aligned.
 size_t query_workspace_bytes(const View &g, Algo algo, Mode mode) {
     const int32_t n = g.n;
     const bool sync = (mode == kVertexSync || mode == kEdgeSync || mode == kPull);
