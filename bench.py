@@ -51,11 +51,11 @@ ALGO_NAMES = ["sssp", "bfs", "cc"]
 # is unchanged (sha256 over fg_internal.cuh, fg_device.cuh and fg_fixpoint.cu
 # at capture time).
 NCU_TRAFFIC: dict = {
-    # profiles/sssp_edge_rmat22.md: one launch each, first seeded source, R-MAT 22
-    "fixpoint_kernel<sssp,edge_async>": {"bytes_per_launch": 3358194176 + 286504704,
-                                         "src_sha": "47407d26e0ed02c6"},
-    "fixpoint_kernel<sssp,edge_sync>": {"bytes_per_launch": 5332451328 + 202576896,
-                                        "src_sha": "47407d26e0ed02c6"},
+    # profiles/sssp_rmat22_traffic.md: one launch each, first seeded source, R-MAT 22
+    "fixpoint_kernel<sssp,vertex_sync>": {"bytes_per_launch": 4246044160 + 544795136, "src_sha": "7d1b82cd8b16b14d"},
+    "fixpoint_kernel<sssp,vertex_async>": {"bytes_per_launch": 3288791296 + 227156480, "src_sha": "7d1b82cd8b16b14d"},
+    "fixpoint_kernel<sssp,edge_sync>": {"bytes_per_launch": 5306321408 + 203094016, "src_sha": "7d1b82cd8b16b14d"},
+    "fixpoint_kernel<sssp,edge_async>": {"bytes_per_launch": 3393273088 + 293337088, "src_sha": "7d1b82cd8b16b14d"},
 }
 
 

@@ -97,6 +97,7 @@ struct SyncOp {
     const int32_t *scur;
     int32_t *snext;
     int32_t r;
+    bool two;          // apply the second filter (running minimum) in this round
 
     // cur and scur are the previous round's: not written during the round
     __device__ __forceinline__ bool active(int32_t u, int32_t &val, bool &) const {
@@ -145,10 +146,29 @@ struct SyncOp {
         }
         return false;
     }
+    // Second filter: a candidate below cur[v] is checked against next[v],
+    // the running minimum of this round (read through L2), and only one that
+    // beats it is applied.  next[v] below cur[v] means an earlier candidate
+    // went below cur[v] and marked v, so only the first one writes the mark.
+    // (R-MAT 22 CC's all-active first round: most of its 67 M MINs skipped.)
+    // It pays where many candidates meet at one target (dense rounds of
+    // skewed graphs); a round after few changes skips the extra load.
+    static constexpr bool kNextProbe = true;
+    __device__ __forceinline__ int32_t probe_next(int32_t v) const { return two ? ldcg(next + v) : kInf; }
+    __device__ __forceinline__ bool commit2(int32_t v, int32_t c, int32_t pv, int32_t nv, Acc &a) const {
+        if (c < pv && c < nv) {
+            red_min(next + v, c);
+            if (nv >= pv) stcg(snext + v, r + 1);
+            a.changed++;
+            a.updates++;
+        }
+        return false;
+    }
 };
 
 // Level-synchronous BFS (Alg. 3): in place, filter dist == lev.
 struct BfsSyncOp {
+    static constexpr bool kNextProbe = false;
     int32_t *L;
     int32_t lev;
 
@@ -190,6 +210,7 @@ struct BfsSyncOp {
 // Asynchronous SSSP / CC: in place, push on decrease, dedup by generation stamp.
 template <int ALGO>
 struct AsyncOp {
+    static constexpr bool kNextProbe = false;
     const int32_t *__restrict__ w;
     int32_t *D;
     int32_t *stamp;
@@ -281,6 +302,7 @@ struct BucketOp : AsyncOp<kSSSP> {
 
 // Asynchronous BFS: frontier queue; a vertex is claimed once by CAS from INF.
 struct BfsAsyncOp {
+    static constexpr bool kNextProbe = false;
     int32_t *L;
     int32_t gen;
     static constexpr bool kRefreshWindow = false;
@@ -310,6 +332,7 @@ struct BfsAsyncOp {
 
 // One full sweep with every vertex active (roofline measurement).
 struct SweepOp {
+    static constexpr bool kNextProbe = false;
     const int32_t *__restrict__ w;
     const int32_t *cur;
     int32_t *next;
@@ -546,8 +569,16 @@ __device__ __forceinline__ void relax_batch(const int32_t *__restrict__ col, con
 #pragma unroll
     for (int j = 0; j < N; j++) pv[j] = ok[j] ? op.probe(v[j]) : 0;
     bool want[N];
+    if constexpr (OP::kNextProbe) {
+        int32_t nv[N];
 #pragma unroll
-    for (int j = 0; j < N; j++) want[j] = ok[j] && op.commit(v[j], c[j], pv[j], a);
+        for (int j = 0; j < N; j++) nv[j] = (ok[j] && c[j] < pv[j]) ? op.probe_next(v[j]) : 0;
+#pragma unroll
+        for (int j = 0; j < N; j++) want[j] = ok[j] && op.commit2(v[j], c[j], pv[j], nv[j], a);
+    } else {
+#pragma unroll
+        for (int j = 0; j < N; j++) want[j] = ok[j] && op.commit(v[j], c[j], pv[j], a);
+    }
 #pragma unroll
     for (int j = 0; j < N; j++) push(want[j], v[j], a);
 }
@@ -1314,9 +1345,18 @@ __device__ __forceinline__ void quad_apply(const OP &op, const Quad &q, Acc &a) 
     int32_t pv[4];
 #pragma unroll
     for (int j = 0; j < 4; j++) pv[j] = q.ok[j] ? op.probe(q.vs[j]) : 0;
+    if constexpr (OP::kNextProbe) {
+        int32_t nv[4];
 #pragma unroll
-    for (int j = 0; j < 4; j++)
-        if (q.ok[j]) op.commit(q.vs[j], q.c[j], pv[j], a);
+        for (int j = 0; j < 4; j++) nv[j] = (q.ok[j] && q.c[j] < pv[j]) ? op.probe_next(q.vs[j]) : 0;
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            if (q.ok[j]) op.commit2(q.vs[j], q.c[j], pv[j], nv[j], a);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            if (q.ok[j]) op.commit(q.vs[j], q.c[j], pv[j], a);
+    }
 }
 
 // A warp streams `count` warp tiles, the k-th being tile_of(k), through its
@@ -1443,6 +1483,13 @@ __device__ __forceinline__ bool stream_flagged_edges(const Team &t, uint32_t &us
 #endif
 #ifndef FG_PULL_SHIFT_SSSP
 #define FG_PULL_SHIFT_SSSP 0
+#endif
+// sync modes: the running-minimum filter is used in CC's all-active first
+// round and in a round whose previous round changed more than
+// n / 2^FG_NEXT_PROBE_SHIFT vertices (R-MAT 22: CC 3.1 -> 2.0 ms; SSSP's
+// rounds gained nothing measurable from it)
+#ifndef FG_NEXT_PROBE_SHIFT
+#define FG_NEXT_PROBE_SHIFT 0
 #endif
 #ifndef FG_SPARSE_SHIFT
 #define FG_SPARSE_SHIFT 0
@@ -1593,7 +1640,10 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
                 int32_t *next = (r & 1) ? p.B : p.A;
                 const int32_t *scur = (r & 1) ? p.S1 : p.S0;
                 int32_t *snext = (r & 1) ? p.S0 : p.S1;
-                SyncOp<ALGO> op{g.w, cur, next, scur, snext, r};
+                const bool dense_prev =
+                    r == 1 ? ALGO == kCC
+                           : ((int64_t)__ldcg(&c->changed[(r - 1) % 3]) << FG_NEXT_PROBE_SHIFT) > (int64_t)n;
+                SyncOp<ALGO> op{g.w, cur, next, scur, snext, r, dense_prev};
                 if (pull) {
                     pull_vertices(t, p.tv, PullMinOp<ALGO>{p.tv.w, cur, next, snext, r}, a);
                 } else if constexpr (MODE == kVertexSync || MODE == kPull) {
