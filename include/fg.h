@@ -154,8 +154,11 @@ fg_status fg_cc(const fg_graph *g, int32_t *label_out, fg_mode mode);
 /*
  * The runtime form of the paper's compile-time choice of vertex/edge and
  * sync/async code (Sec. 2 "flexible processing", Sec. 4.3): picks a mode for
- * this graph and algorithm from its degree skew and an estimate of its
- * diameter (one BFS, run and cached on first use).
+ * this graph and algorithm -- the autotuner's measured choice if fg_autotune
+ * ran for it, else a rule on an estimate of the diameter (one BFS, run and
+ * cached on first use): on shallow graphs FG_PULL for BFS and FG_VERTEX_ASYNC
+ * for SSSP and CC, on deep ones (eccentricity estimate > 64) FG_VERTEX_ASYNC
+ * for BFS, FG_BUCKET for SSSP and FG_VERTEX_SYNC for CC.
  */
 fg_status fg_select_mode(const fg_graph *g, fg_algo algo, fg_mode *out);
 

@@ -227,12 +227,16 @@ fg_status fg_select_mode(const fg_graph *g, fg_algo algo, fg_mode *out) {
         g->diam_est = diam;
     }
     // Measured on GB300 (R-MAT 22 and the 4096^2 grid): with degree buckets
-    // the vertex modes lead on skewed and uniform graphs alike; the worklist
-    // wins BFS everywhere, and SSSP/CC on shallow graphs, while on deep
-    // graphs the synchronous sweep's lower per-round cost wins SSSP and CC.
+    // the vertex modes lead on skewed and uniform graphs alike.  On shallow
+    // graphs the worklist wins SSSP and CC, and the direction-optimising pull
+    // wins BFS (its bottom-up levels stop at the first parent); on deep
+    // graphs the worklist wins BFS, the bucketed worklist SSSP (far fewer
+    // relaxations) and the synchronous sweep's lower per-round cost CC.
     const bool deep = diam > 64;
-    fg_mode m = FG_VERTEX_ASYNC;
-    if (algo != FG_ALGO_BFS && deep) m = FG_VERTEX_SYNC;
+    fg_mode m;
+    if (algo == FG_ALGO_BFS) m = deep ? FG_VERTEX_ASYNC : FG_PULL;
+    else if (algo == FG_ALGO_SSSP) m = deep ? FG_BUCKET : FG_VERTEX_ASYNC;
+    else m = deep ? FG_VERTEX_SYNC : FG_VERTEX_ASYNC;
     *out = m;
     return FG_OK;
 }

@@ -170,10 +170,10 @@ def test_select_mode_runs_and_auto_matches():
     with graph_handle(g) as h:
         for algo in (0, 1, 2):
             st, m = fg.fg_select_mode(h, algo)
-            assert st == fg.FG_OK and m in (0, 1, 2, 3, 5)
+            assert st == fg.FG_OK and m in (0, 1, 2, 3, 5, 6)
         got, st = run(h, g.n, ALGOS["sssp"], 0, fg.FG_AUTO)
         np.testing.assert_array_equal(got, d)
-        assert st.mode in (0, 1, 2, 3, 5)
+        assert st.mode in (0, 1, 2, 3, 5, 6)
 
 
 def test_invariants_on_results():
