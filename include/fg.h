@@ -178,7 +178,7 @@ typedef struct {
                                    mid-round or pointer-jumping barrier), at most
                                    round_trace_cap entries; NULL = no tracing */
     int32_t round_trace_cap;
-    int32_t delta;              /* FG_BUCKET: bucket width (0 = 8 x the mean edge weight x the
+    int32_t delta;              /* FG_BUCKET: bucket width (0 = 5 x the mean edge weight x the
                                    mean out-degree) */
 } fg_options;
 

@@ -1770,7 +1770,12 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
                 // The near worklist ran empty: the threshold moves to the far
                 // list's smallest distance + delta, and the far list is split
                 // into the next generation's worklist (distance below the
-                // new threshold) and the next epoch's far list.
+                // new threshold) and the next epoch's far list.  An entry
+                // whose distance is now below the old threshold is stale: it
+                // was lowered under that threshold later, queued as near
+                // then and expanded with its current distance, so it is
+                // dropped and does not hold the new threshold down.
+                const int32_t T_old = T;
                 const int32_t *far_in = p.far[epoch & 1];
                 int32_t *far_out = p.far[(epoch + 1) & 1];
                 const int fn = __ldcg(&c->far_size[epoch % 3]);
@@ -1780,7 +1785,10 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
                     c->splits++;
                 }
                 int32_t fm = kInf;
-                for (int64_t i = tid; i < fn; i += nth) fm = min(fm, ldcg(p.A + ldcg(far_in + i)));
+                for (int64_t i = tid; i < fn; i += nth) {
+                    const int32_t d = ldcg(p.A + ldcg(far_in + i));
+                    if (d >= T_old) fm = min(fm, d);
+                }
                 fm = block_min(fm);
                 if (threadIdx.x == 0 && fm < kInf) atomicMin(&c->far_min[epoch % 3], fm);
                 if (!sync_()) break;
@@ -1795,7 +1803,10 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
                     int32_t v = 0;
                     if (i < fn) {
                         v = ldcg(far_in + i);
-                        if (ldcg(p.A + v) < T) {
+                        const int32_t d = ldcg(p.A + v);
+                        if (d < T_old) {
+                            // stale: expanded in an earlier generation
+                        } else if (d < T) {
                             near = atomicExch(p.S0 + v, gen + 1) != gen + 1;
                         } else if (atomicExch(p.far_mark + v, epoch + 1) != epoch + 1) {
                             const unsigned am = __activemask();
