@@ -105,8 +105,9 @@ def queries_for(workload: str, srcs):
 def algorithmic_bytes(algo: int, mode: int, st: dict, info: dict) -> float:
     """Bytes the variant must move for one query, from its device counters.
 
-    S activity words scanned (sync modes: vertex stamps or levels, and for
-    edge-sync the edge sources streamed), Va expanded vertices, Ea relaxed
+    S activity words scanned (sync modes: vertex stamps or levels; edge-sync
+    and the dense generations of edge-async: the edge sources streamed), Va
+    expanded vertices (edge-async: worklist items expanded), Ea relaxed
     edges, U accepted candidates, P worklist appends, n vertices.  Ids,
     values and offsets are 4 bytes; per edge: col (+ w for SSSP) + the
     target's value.
@@ -126,6 +127,8 @@ def algorithmic_bytes(algo: int, mode: int, st: dict, info: dict) -> float:
             item += 16           # degree prefix: item, offsets, prefix write
         upd = 8 if algo == 1 else 12
         b = Va * item + Ea * per_edge + U * upd + P * 8
+        if mode == 3:
+            b += 4 * S           # dense generations: the streamed edge sources
     if algo == 2:
         b += st["jump_passes"] * n * 8
     return float(b)

@@ -15,7 +15,10 @@
  *   FG_VERTEX_ASYNC data-driven (Sec. 3.3): a device worklist of vertices,
  *                   in-place atomic MIN, run until the worklist is empty;
  *   FG_EDGE_ASYNC   the same worklist expanded to its out-edges and relaxed
- *                   edge-parallel, in place;
+ *                   edge-parallel, in place; a generation whose worklist holds
+ *                   a quarter of the edges or more (BFS: half) streams the
+ *                   whole edge list instead, relaxing the edges whose source
+ *                   is queued;
  *
  * and a fifth built on the paper's in-neighbour iterator (innbrs, Sec. 2):
  *
@@ -189,12 +192,16 @@ typedef struct {
                                    included; max_rounds counts the other generations) */
     int32_t jump_passes;        /* CC pointer-jumping passes */
     int32_t grid_blocks;        /* persistent CTAs launched */
-    int64_t vertices_processed; /* active vertices expanded, summed over rounds */
+    int64_t vertices_processed; /* active vertices expanded, summed over rounds
+                                   (FG_EDGE_ASYNC: worklist items expanded; its dense
+                                   generations stream the edge list and count none) */
     int64_t edges_relaxed;      /* edges whose source was active, summed over rounds */
     int64_t updates;            /* successful MIN updates */
     int64_t pushes;             /* worklist appends (async modes) */
     int64_t scanned;            /* activity words read by the sync modes' scans (vertex ids,
-                                   or edge sources streamed by edge-sync), summed over rounds */
+                                   or edge sources streamed by edge-sync), and the edge
+                                   sources streamed by FG_EDGE_ASYNC's dense generations,
+                                   summed over rounds */
     float kernel_ms;            /* device time of the fixpoint kernel (CUDA events on
                                    the query's stream) */
     int32_t barriers;           /* grid barriers the kernel passed (= trace entries written,

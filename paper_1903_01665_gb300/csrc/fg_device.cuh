@@ -1472,6 +1472,184 @@ __device__ __forceinline__ bool stream_flagged_edges(const Team &t, uint32_t &us
     return __syncthreads_and(ok);
 }
 
+// ================================================================ dense edge-async generations
+// When a generation's worklist covers a large share of all edges, the
+// edge-async mode streams the whole edge list (source-sorted COO) instead of
+// expanding the worklist: the topology-driven form of the edge variant for
+// dense generations, the data-driven form for sparse ones (Sec. 3.3 names
+// both).  A source is in generation g's worklist iff its stamp is g: it was
+// stamped g when it was queued during g - 1, and during g a stamp only moves
+// on to g + 1 (the vertex is then in g + 1's worklist and is expanded there),
+// so an L1 copy of a stamp, fresh since the barrier, can only err towards
+// skipping a source that g + 1 expands anyway.  Each lane reads four
+// consecutive edges with 16-byte streaming loads.
+#ifndef FG_EA_DENSE_PCT
+#define FG_EA_DENSE_PCT 25
+#endif
+// worklist edges, % of m, from which a generation streams.  BFS only from
+// half: its frontier relaxes each edge once at most, and a quarter cost 10 %
+// on R-MAT 22.
+template <int ALGO>
+__host__ __device__ constexpr int ea_dense_pct() { return ALGO == kBFS ? 2 * FG_EA_DENSE_PCT : FG_EA_DENSE_PCT; }
+
+template <int ALGO>
+struct AsyncStreamOp : AsyncOp<ALGO> {
+    __device__ __forceinline__ void load_act(int32_t u, int32_t &st, int32_t &vl) const {
+        st = ldca(this->stamp + u);
+        vl = ldcg(this->D + u);
+    }
+    // SSSP also expands the sources lowered during this generation (stamp
+    // g + 1): relaxing with a current distance is always valid, it carries
+    // the new distance on at once, and a source of the worklist that was
+    // lowered after its first edges keeps its remaining edges in this
+    // generation.  CC keeps to the worklist: with the pointer jumps below,
+    // the wider test ran slower on R-MAT 22 and the 4096^2 grid.
+    static constexpr bool kAlsoLowered = (ALGO == kSSSP);
+    __device__ __forceinline__ bool is_act(int32_t st, int32_t vl) const {
+        return (kAlsoLowered ? st >= this->gen : st == this->gen) && vl != kInf;
+    }
+    // CC: the worklist expansion's pointer jumping (active()); the others
+    // use the value as read
+    static constexpr bool kJumps = (ALGO == kCC);
+    __device__ __forceinline__ int32_t jump(int32_t u, int32_t vl, bool &rq) const {
+        if (kJumps) {
+            int32_t v = vl;
+            this->active(u, v, rq);
+            return v;
+        }
+        return vl;
+    }
+    __device__ __forceinline__ bool cand_w(int32_t vl, int32_t w, int32_t &c, Acc &a) const {
+        if (ALGO == kSSSP) {
+            const uint32_t x = (uint32_t)vl + (uint32_t)w;
+            if (x >= (uint32_t)kInf) {
+                a.overflow = 1;
+                return false;
+            }
+            c = (int32_t)x;
+        } else {
+            c = vl;
+        }
+        return true;
+    }
+};
+
+// BFS: the sources of generation g are the vertices at level g (levels are
+// claimed once, by CAS, with the next generation's number)
+struct BfsStreamOp : BfsAsyncOp {
+    __device__ __forceinline__ void load_act(int32_t u, int32_t &st, int32_t &vl) const {
+        st = ldca(this->L + u);
+        vl = this->gen;
+    }
+    __device__ __forceinline__ bool is_act(int32_t st, int32_t) const { return st == this->gen; }
+    static constexpr bool kJumps = false;
+    __device__ __forceinline__ int32_t jump(int32_t, int32_t vl, bool &) const { return vl; }
+    __device__ __forceinline__ bool cand_w(int32_t, int32_t, int32_t &c, Acc &) const {
+        c = this->gen + 1;
+        return true;
+    }
+};
+
+// A lane's four consecutive edges of a warp tile, as loaded.
+struct RawQuad {
+    int32_t us[4], vs[4], ws[4];
+    int nv;
+};
+
+template <bool W>
+__device__ __forceinline__ void raw_load(const View &g, int64_t e0, RawQuad &r) {
+    const int64_t e = e0 + 4 * (int64_t)lane_id();
+    r.nv = (int)max((int64_t)0, min((int64_t)4, g.m - e));
+#pragma unroll
+    for (int j = 0; j < 4; j++) r.us[j] = r.vs[j] = r.ws[j] = 0;
+    if (r.nv == 4) {   // e is a multiple of 4 and the arrays are 16-byte aligned
+        const int4 s4 = __ldcs(reinterpret_cast<const int4 *>(g.src + e));
+        const int4 c4 = __ldcs(reinterpret_cast<const int4 *>(g.col + e));
+        r.us[0] = s4.x; r.us[1] = s4.y; r.us[2] = s4.z; r.us[3] = s4.w;
+        r.vs[0] = c4.x; r.vs[1] = c4.y; r.vs[2] = c4.z; r.vs[3] = c4.w;
+        if (W) {
+            const int4 w4 = __ldcs(reinterpret_cast<const int4 *>(g.w + e));
+            r.ws[0] = w4.x; r.ws[1] = w4.y; r.ws[2] = w4.z; r.ws[3] = w4.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            if (j < r.nv) {
+                r.us[j] = __ldg(g.src + e + j);
+                r.vs[j] = __ldg(g.col + e + j);
+                if (W) r.ws[j] = __ldg(g.w + e + j);
+            }
+    }
+}
+
+// Dense edge-async generation: warp tiles dealt round-robin to the team's
+// warps; targets lowered are queued for the next generation by `push`.  CC
+// first shortens each active source's label by pointer jumping, as the
+// worklist expansion does, and queues the source again if that lowered it;
+// this happens once per source, by the lane holding its first edge (the
+// edge before it has another source), and the lanes holding its other edges
+// use the label as read.
+// Measured and rejected: loading the next tile ahead of the current tile's
+// probes (it spilled registers at the worklist kernels' budget and ran 20 %
+// slower), and a contiguous range of tiles per warp instead of the
+// round-robin deal (the active tiles of skewed graphs cluster; SSSP on
+// R-MAT 22 ran 20 % slower, CC on the grid 2x).
+template <bool W, class OP, class PUSH>
+__device__ __forceinline__ void stream_edges_async(const Team &t, const View &g, const OP &op, const PUSH &push,
+                                                   Acc &a) {
+    const int64_t ntiles = (g.m + kWTile - 1) / kWTile;
+    const int64_t gw = (int64_t)t.rank * kWarps + (threadIdx.x >> 5), nw = (int64_t)t.size * kWarps;
+    if (t.rank == 0 && threadIdx.x == 0) a.scanned += (uint64_t)g.m;
+    for (int64_t tile = gw; tile < ntiles; tile += nw) {   // warp-uniform
+        RawQuad r;
+        raw_load<W>(g, tile * kWTile, r);
+        int32_t before = 0;   // source of the edge before the lane's first
+        if constexpr (OP::kJumps) {
+            before = __shfl_up_sync(0xffffffffu, r.us[3], 1);
+            if (lane_id() == 0) before = tile > 0 ? __ldg(g.src + tile * kWTile - 1) : -1;
+        }
+        Quad q;
+        bool fresh[4], act[4], rq[4];
+        int32_t st[4], vl[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            fresh[j] = j < r.nv && (j == 0 || r.us[j] != r.us[j - 1]);
+            st[j] = 0;
+            vl[j] = 0;
+            rq[j] = false;
+            if (fresh[j]) op.load_act(r.us[j], st[j], vl[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if (j >= r.nv) {
+                act[j] = false;
+            } else if (fresh[j]) {
+                act[j] = op.is_act(st[j], vl[j]);
+                if (OP::kJumps && act[j] && (j > 0 || r.us[0] != before)) vl[j] = op.jump(r.us[j], vl[j], rq[j]);
+            } else {
+                act[j] = act[j - 1];
+                vl[j] = vl[j - 1];
+            }
+            q.vs[j] = r.vs[j];
+            q.c[j] = 0;
+            q.ok[j] = act[j] && op.cand_w(vl[j], r.ws[j], q.c[j], a);
+            a.edges += act[j];
+        }
+        if constexpr (OP::kJumps) {
+#pragma unroll
+            for (int j = 0; j < 4; j++) push(rq[j], r.us[j], a);
+        }
+        int32_t pv[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) pv[j] = q.ok[j] ? op.probe(q.vs[j]) : 0;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const bool rqv = q.ok[j] && op.commit(q.vs[j], q.c[j], pv[j], a);
+            push(rqv, q.vs[j], a);
+        }
+    }
+}
+
 // ================================================================ the kernel
 // Resident CTAs per SM the register budget is sized for.  The vertex-sync,
 // pull and worklist kernels gain from more warps in flight (their gathers are
@@ -1858,15 +2036,28 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
                 };
                 LbPush push{g.row_off, g.vclass, p.wl[po][0], p.lb_off[po], &c->wl_pack[out_slot], p.wl_cap[0],
                             &wb[0], c};
-                if (ALGO == kBFS) {
-                    BfsAsyncOp op{p.A, gen};
-                    lb_expand(t, g.row_off, g.col, items, n_in[0], goff, T, op, push, a);
+                const bool dense = initial_cc || (uint64_t)T * 100u >= (uint64_t)g.m * (uint64_t)ea_dense_pct<ALGO>();
+                if constexpr (ALGO == kBFS) {
+                    if (dense) {
+                        BfsStreamOp op;
+                        op.L = p.A; op.gen = gen;
+                        stream_edges_async<false>(t, g, op, push, a);
+                    } else {
+                        BfsAsyncOp op{p.A, gen};
+                        lb_expand(t, g.row_off, g.col, items, n_in[0], goff, T, op, push, a);
+                    }
                 } else {
-                    AsyncOp<ALGO> op{g.w, p.A, p.S0, gen};
-                    lb_expand(t, g.row_off, g.col, items, n_in[0], goff, T, op, push, a);
+                    if (dense) {
+                        AsyncStreamOp<ALGO> op;
+                        op.w = g.w; op.D = p.A; op.stamp = p.S0; op.gen = gen;
+                        stream_edges_async<ALGO == kSSSP>(t, g, op, push, a);
+                    } else {
+                        AsyncOp<ALGO> op{g.w, p.A, p.S0, gen};
+                        lb_expand(t, g.row_off, g.col, items, n_in[0], goff, T, op, push, a);
+                    }
                 }
                 push.flush();
-                if (tid == 0) a.verts += (unsigned long long)n_in[0];
+                if (tid == 0 && !dense) a.verts += (unsigned long long)n_in[0];
             }
             if (!sync_()) break;
         }

@@ -199,3 +199,22 @@ def test_bucket_mode_any_width(delta):
             got, st = run(h, g.n, ALGOS["sssp"], s, fg.FG_BUCKET, delta=delta)
             np.testing.assert_array_equal(got, d)
             assert st.mode == fg.FG_BUCKET
+
+
+def test_edge_async_dense_generations_stream():
+    """Edge-async generations whose worklist holds a quarter of the edges or
+    more stream the whole edge list (stats.scanned counts the streamed edge
+    sources); the result stays the oracle's in all three algorithms, on a
+    skewed graph (dense middle generations) and a grid (CC's all-active
+    first generation, sparse wavefronts after)."""
+    for g in (gg.rmat(13, seed=41), gg.grid(80, seed=42)):
+        s = int(gg.sources(g, 1, seed=43)[0])
+        _, d = oracle.sssp(g.n, g.src, g.dst, g.w, s)
+        _, lv = oracle.bfs(g.n, g.src, g.dst, s)
+        _, lab = oracle.cc(g.n, g.src, g.dst)
+        with graph_handle(g) as h:
+            for algo, want in (("sssp", d), ("bfs", lv), ("cc", lab)):
+                got, st = run(h, g.n, ALGOS[algo], s, fg.FG_EDGE_ASYNC)
+                np.testing.assert_array_equal(got, want, err_msg=f"{g.name} {algo}")
+                if algo == "cc" or g.name.startswith("rmat"):
+                    assert st.scanned > 0, (g.name, algo)
