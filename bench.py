@@ -52,10 +52,10 @@ ALGO_NAMES = ["sssp", "bfs", "cc"]
 # at capture time).
 NCU_TRAFFIC: dict = {
     # profiles/sssp_rmat22_traffic.md: one launch each, first seeded source, R-MAT 22
-    "fixpoint_kernel<sssp,vertex_sync>": {"bytes_per_launch": 4246044160 + 544795136, "src_sha": "7d1b82cd8b16b14d"},
-    "fixpoint_kernel<sssp,vertex_async>": {"bytes_per_launch": 3288791296 + 227156480, "src_sha": "7d1b82cd8b16b14d"},
-    "fixpoint_kernel<sssp,edge_sync>": {"bytes_per_launch": 5306321408 + 203094016, "src_sha": "7d1b82cd8b16b14d"},
-    "fixpoint_kernel<sssp,edge_async>": {"bytes_per_launch": 3393273088 + 293337088, "src_sha": "7d1b82cd8b16b14d"},
+    "fixpoint_kernel<sssp,vertex_sync>": {"bytes_per_launch": 4246974976 + 545092864, "src_sha": "911514d77fb24fda"},
+    "fixpoint_kernel<sssp,vertex_async>": {"bytes_per_launch": 2951216384 + 203084288, "src_sha": "911514d77fb24fda"},
+    "fixpoint_kernel<sssp,edge_sync>": {"bytes_per_launch": 5304832256 + 203370496, "src_sha": "911514d77fb24fda"},
+    "fixpoint_kernel<sssp,edge_async>": {"bytes_per_launch": 4305143040 + 251591680, "src_sha": "911514d77fb24fda"},
 }
 
 
