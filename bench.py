@@ -393,7 +393,7 @@ def run_batched(device, reps: int = 3) -> dict:
             fg.fg_graph_destroy(h)
 
 
-def run_serving(device, full: bool = False, rates=(100, 1000, 10000), n_req: int = 1000,
+def run_serving(device, full: bool = False, rates=(100, 300, 1000, 3000, 10000), n_req: int = 2000,
                 seed: int = 0x5E57) -> dict:
     """Poisson arrivals of SSSP/BFS/CC requests (40/40/20, uniform over the
     resident graphs, seeded sources) served (a) by the continuous-batching
@@ -584,6 +584,8 @@ def run_ours(args):
     units_all, sec = aggregate(units, ms * 1e-3, pg, device)
     ms = sec * 1e3
     value = units_all / sec / 1e9
+    # raw relaxations per second: edges whose source was active, every query
+    relax_all, _ = aggregate(sum(int(st["edges_relaxed"]) for _a, _m, st in record), sec, pg, device)
 
     # ---- roofline of the dominant kernel (largest share of device time)
     per_kernel = {}
@@ -640,6 +642,9 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample(r.g, r.srcs, r.deg, args.workload)
     desc, nqueries = r.desc, len(r.queries)
+    gbytes = int(r.info["device_bytes"]) if r.info else 0
+    l2_note = (f"inputs larger than L2 (graph {gbytes / 1e9:.2f} GB built per step)" if gbytes > 129 << 20 else
+               f"inputs smaller than L2 ({gbytes / 1e6:.1f} MB graph), not flushed: a parity-size case")
     batched = serving = None
     del r
     torch.cuda.empty_cache()
@@ -656,8 +661,10 @@ def run_ours(args):
                 "data": "synthetic (seeded generators in graphgen/)",
                 "config": {"workload": desc, "queries_per_step": nqueries,
                            "teps_edges_per_step": units // max(args.steps, 1),
-                           "l2": "inputs larger than L2 (graph ~1.9-2.2 GB built per step)",
+                           "l2": l2_note,
                            "parallelism": f"replicas x{ws}"},
+                "relaxations": {"value": round(relax_all / sec / 1e9, 3), "unit": "G edge relaxations/s",
+                                "per_step": relax_all // max(args.steps * ws, 1)},
                 "roofline": roofline, "sweep_roofline": sweep, "extra_modes": extra, "grid_bucket": grid_bucket,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "per_kernel": per_mode, "batched": batched, "serving": serving}
@@ -792,7 +799,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving comparison")
     ap.add_argument("--serving-full", action="store_true",
                     help="serve the R-MAT 24-26 + 8192^2 grid resident set (~60 GB) instead of the reduced one")
-    ap.add_argument("--serving-requests", type=int, default=1000)
+    ap.add_argument("--serving-requests", type=int, default=2000)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

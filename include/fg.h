@@ -121,10 +121,34 @@ fg_status fg_graph_create_csr(int32_t n, int64_t m, const int64_t *row_off, cons
 fg_status fg_graph_create_coo(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
                               const int32_t *w, fg_graph **out);
 
+/*
+ * The same with creation flags (0 = the plain calls above).
+ *
+ * FG_GRAPH_LAZY   keep only the CSR and its degree buckets at creation (R-MAT
+ *                 22: 0.6 GB of the 1.95 GB a full build holds).  The COO's
+ *                 source array is built by the first edge-based query on the
+ *                 directed graph (FG_EDGE_SYNC, FG_EDGE_ASYNC, fg_sweep's
+ *                 edge variant, the transposed view of FG_PULL, or an SSSP
+ *                 whose overflow check runs), the symmetrised view by the
+ *                 first CC query; each is kept with the graph.  The call
+ *                 that builds a part also pays for it, and an out-of-memory
+ *                 error can then come from a query; fg_graph_info reports
+ *                 device_bytes as it grows and n_isolated as -1 until the
+ *                 symmetrised view exists.  Results are identical.
+ *
+ * Unknown flag bits: FG_ERR_INVALID_ARG.
+ */
+#define FG_GRAPH_LAZY 1u
+fg_status fg_graph_create_csr_ex(int32_t n, int64_t m, const int64_t *row_off, const int32_t *col,
+                                 const int32_t *w, uint32_t flags, fg_graph **out);
+fg_status fg_graph_create_coo_ex(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                                 const int32_t *w, uint32_t flags, fg_graph **out);
+
 /* Frees the graph's device memory.  NULL is accepted (no-op). */
 fg_status fg_graph_destroy(fg_graph *g);
 
-/* Host-side facts about a graph, computed at creation. */
+/* Host-side facts about a graph, computed at creation (device_bytes and
+   n_isolated also when a FG_GRAPH_LAZY graph builds a part). */
 typedef struct {
     int32_t n;
     int64_t m;
@@ -133,7 +157,8 @@ typedef struct {
     int32_t n_zero_out;         /* vertices with no out-edge */
     int32_t n_low, n_mid, n_high; /* degree-bucket sizes (1..31, 32..1023, >= 1024) */
     int32_t n_high_chunks;      /* 2048-edge chunks of the high bucket */
-    int32_t n_isolated;         /* vertices with no edge in either direction */
+    int32_t n_isolated;         /* vertices with no edge in either direction (-1 until a
+                                   FG_GRAPH_LAZY graph has built its symmetrised view) */
     int64_t device_bytes;       /* device memory held by the handle */
 } fg_graph_info_t;
 

@@ -41,6 +41,7 @@ FG_ALGO_SSSP = 0
 FG_ALGO_BFS = 1
 FG_ALGO_CC = 2
 FG_INF = 2**31 - 1
+FG_GRAPH_LAZY = 1
 
 
 class fg_options(ctypes.Structure):
@@ -106,6 +107,10 @@ _VP = ctypes.c_void_p
 _SIGNATURES = {
     "fg_graph_create_csr": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _VP, _VP, _VP, ctypes.POINTER(_VP)]),
     "fg_graph_create_coo": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _VP, _VP, _VP, ctypes.POINTER(_VP)]),
+    "fg_graph_create_csr_ex": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _VP, _VP, _VP, ctypes.c_uint32,
+                                              ctypes.POINTER(_VP)]),
+    "fg_graph_create_coo_ex": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _VP, _VP, _VP, ctypes.c_uint32,
+                                              ctypes.POINTER(_VP)]),
     "fg_graph_destroy": (ctypes.c_int, [_VP]),
     "fg_graph_info": (ctypes.c_int, [_VP, ctypes.POINTER(fg_graph_info_t)]),
     "fg_sssp": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int]),
@@ -192,22 +197,30 @@ def _len(x):
     return int(x.shape[0]) if x is not None else 0
 
 
-def fg_graph_create_coo(n, src, dst, w=None):
-    """Returns (status, handle)."""
+def fg_graph_create_coo(n, src, dst, w=None, flags=0):
+    """Returns (status, handle).  flags: 0 or FG_GRAPH_LAZY."""
     for a in (src, dst, w):
         _check_dtype(a, "int32")
     h = _VP()
-    st = load().fg_graph_create_coo(int(n), _len(src), _ptr(src), _ptr(dst), _ptr(w), ctypes.byref(h))
+    if flags:
+        st = load().fg_graph_create_coo_ex(int(n), _len(src), _ptr(src), _ptr(dst), _ptr(w), int(flags),
+                                           ctypes.byref(h))
+    else:
+        st = load().fg_graph_create_coo(int(n), _len(src), _ptr(src), _ptr(dst), _ptr(w), ctypes.byref(h))
     return st, (h.value if st == FG_OK else None)
 
 
-def fg_graph_create_csr(n, row_off, col, w=None):
-    """Returns (status, handle).  row_off is int64[n+1]."""
+def fg_graph_create_csr(n, row_off, col, w=None, flags=0):
+    """Returns (status, handle).  row_off is int64[n+1]; flags: 0 or FG_GRAPH_LAZY."""
     _check_dtype(row_off, "int64")
     _check_dtype(col, "int32")
     _check_dtype(w, "int32")
     h = _VP()
-    st = load().fg_graph_create_csr(int(n), _len(col), _ptr(row_off), _ptr(col), _ptr(w), ctypes.byref(h))
+    if flags:
+        st = load().fg_graph_create_csr_ex(int(n), _len(col), _ptr(row_off), _ptr(col), _ptr(w), int(flags),
+                                           ctypes.byref(h))
+    else:
+        st = load().fg_graph_create_csr(int(n), _len(col), _ptr(row_off), _ptr(col), _ptr(w), ctypes.byref(h))
     return st, (h.value if st == FG_OK else None)
 
 

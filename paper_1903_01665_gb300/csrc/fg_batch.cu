@@ -134,11 +134,9 @@ fg_status batch_launch(const fg_query *qs, int32_t nq, const fg_batch_options *o
             if (s != FG_OK) return s;
         }
         mode[i] = (Mode)m;
+        fg_status vs = ensure_views(q.g, (Algo)q.algo, (int)m);   // lazily built parts, transposed view
+        if (vs != FG_OK) return vs;
         view[i] = (q.algo == FG_ALGO_CC) ? &q.g->s : &q.g->g;
-        if (m == FG_PULL && q.algo != FG_ALGO_CC) {
-            fg_status s = ensure_transpose(q.g);
-            if (s != FG_OK) return s;
-        }
         KindPlan &kp = kinds[q.algo * 8 + (int)m];
         kp.kind = q.algo * 8 + (int)m;
         kp.queries.push_back(i);

@@ -421,12 +421,72 @@ const T *to_device(Builder &b, const T *p, int64_t count, T **tmp) {
     return d;
 }
 
+// The source of every CSR edge: with col and w it forms the source-sorted
+// COO that the edge-based modes stream (Sec. 3.1); also read by the
+// transposed view's build and the SSSP overflow check.
+void build_src(Builder &b, View &v) {
+    int32_t *esrc = b.alloc_graph<int32_t>(v.m);
+    if (b.status == FG_OK && v.m > 0) {
+        k_src_from_rows<<<grid_for((int64_t)v.n * 32), kBlock, 0, b.st>>>(v.n, v.row_off, esrc);
+        count_launch();
+        b.check(cudaGetLastError(), "edge sources");
+    }
+    if ((uintptr_t)esrc & 15u) {   // the edge stream's bulk copies need 16-byte alignment
+        b.status = FG_ERR_CUDA;
+        b.msg = "internal error: edge sources not 16-byte aligned";
+    }
+    v.src = esrc;
+}
+
+// The symmetrised view used by connected components: every edge u->v also
+// stored as v->u (the undirected nbrs iterator, Table "foreach iterators"),
+// as CSR plus edge sources.  Needs the directed view's edge sources.
+void build_sym(Builder &b, fg_graph *g) {
+    const View &v = g->g;
+    const int32_t n = v.n;
+    const int64_t m = v.m;
+    View &s = g->s;
+    s.n = n;
+    s.m = 2 * m;
+    uint32_t *sro = b.alloc_graph<uint32_t>((int64_t)n + 1);
+    int32_t *scol = b.alloc_graph<int32_t>(2 * m);
+    int32_t *ssrc = b.alloc_graph<int32_t>(2 * m);
+    if (b.status == FG_OK) {
+        uint32_t *deg = b.alloc_tmp<uint32_t>(n);
+        uint32_t *cursor = b.alloc_tmp<uint32_t>((int64_t)n + 1);
+        if (b.status == FG_OK) {
+            b.check(cudaMemsetAsync(deg, 0, (size_t)n * sizeof(uint32_t), b.st), "memset");
+            if (m > 0) { k_histogram<<<grid_for(m), kBlock, 0, b.st>>>(m, v.col, deg); count_launch(); }
+            k_sym_degree<<<grid_for(n), kBlock, 0, b.st>>>(n, v.row_off, deg);
+            count_launch();
+            b.check(exclusive_scan(deg, sro, n, b.st), "scan");
+            k_sym_cursor<<<grid_for(n), kBlock, 0, b.st>>>(n, sro, v.row_off, cursor);
+            count_launch();
+            if (m > 0) {
+                k_scatter_sym<<<grid_for(m), kBlock, 0, b.st>>>(m, v.src, v.col, v.row_off, sro, cursor, scol);
+                count_launch();
+                k_src_from_rows<<<grid_for((int64_t)n * 32), kBlock, 0, b.st>>>(n, sro, ssrc);
+                count_launch();
+            }
+            b.check(cudaGetLastError(), "symmetrise");
+        }
+        if (deg) cudaFreeAsync(deg, b.st);
+        if (cursor) cudaFreeAsync(cursor, b.st);
+    }
+    s.row_off = sro;
+    s.col = scol;
+    s.w = nullptr;
+    s.src = ssrc;
+    if (b.status == FG_OK) make_buckets(b, s);
+    if (b.status == FG_OK) g->info.n_isolated = s.n_zero;
+}
+
 }  // namespace
 
 // Builds a graph from COO (row_off_in == nullptr) or from CSR (row_off_in,
 // with src == nullptr and dst == col).
 fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
-                               const int32_t *w, bool from_csr, const int64_t *row_off_in,
+                               const int32_t *w, bool from_csr, const int64_t *row_off_in, uint32_t create_flags,
                                fg_graph **out) {
     fg_graph *g = new (std::nothrow) fg_graph();
     if (!g) return fail(FG_ERR_OUT_OF_MEMORY, "host allocation failed");
@@ -464,7 +524,6 @@ fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const i
     uint32_t *ro = b.alloc_graph<uint32_t>((int64_t)n + 1);
     int32_t *col = b.alloc_graph<int32_t>(m);
     int32_t *wt = b.alloc_graph<int32_t>(m);
-    int32_t *esrc = b.alloc_graph<int32_t>(m);
     if (b.status == FG_OK) {
         if (from_csr) {
             k_offsets_to_u32<<<grid_for((int64_t)n + 1), kBlock, 0, b.st>>>(n, d_ro, ro);
@@ -473,8 +532,6 @@ fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const i
                 b.check(cudaMemcpyAsync(col, d_dst, m * sizeof(int32_t), cudaMemcpyDeviceToDevice, b.st), "copy");
                 if (d_w) b.check(cudaMemcpyAsync(wt, d_w, m * sizeof(int32_t), cudaMemcpyDeviceToDevice, b.st), "copy");
                 else { k_fill_ones<<<grid_for(m), kBlock, 0, b.st>>>(m, wt); count_launch(); }
-                k_src_from_rows<<<grid_for((int64_t)n * 32), kBlock, 0, b.st>>>(n, ro, esrc);
-                count_launch();
             }
         } else {
             uint32_t *cnt = b.alloc_tmp<uint32_t>(n);
@@ -487,8 +544,6 @@ fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const i
                 if (m > 0) {
                     k_scatter_coo<<<grid_for(m), kBlock, 0, b.st>>>(m, d_src, d_dst, d_w, cursor, col, wt);
                     count_launch();
-                    k_src_from_rows<<<grid_for((int64_t)n * 32), kBlock, 0, b.st>>>(n, ro, esrc);
-                    count_launch();
                 }
                 b.check(cudaGetLastError(), "scatter");
             }
@@ -500,43 +555,15 @@ fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const i
     v.row_off = ro;
     v.col = col;
     v.w = wt;
-    v.src = esrc;
+    v.src = nullptr;
     if (b.status == FG_OK) make_buckets(b, v);
-
-    // symmetrised view: every edge u->v also stored as v->u
-    View &s = g->s;
-    s.n = n;
-    s.m = 2 * m;
-    uint32_t *sro = b.alloc_graph<uint32_t>((int64_t)n + 1);
-    int32_t *scol = b.alloc_graph<int32_t>(2 * m);
-    int32_t *ssrc = b.alloc_graph<int32_t>(2 * m);
-    if (b.status == FG_OK) {
-        uint32_t *deg = b.alloc_tmp<uint32_t>(n);
-        uint32_t *cursor = b.alloc_tmp<uint32_t>((int64_t)n + 1);
-        if (b.status == FG_OK) {
-            b.check(cudaMemsetAsync(deg, 0, (size_t)n * sizeof(uint32_t), b.st), "memset");
-            if (m > 0) { k_histogram<<<grid_for(m), kBlock, 0, b.st>>>(m, col, deg); count_launch(); }
-            k_sym_degree<<<grid_for(n), kBlock, 0, b.st>>>(n, ro, deg);
-            count_launch();
-            b.check(exclusive_scan(deg, sro, n, b.st), "scan");
-            k_sym_cursor<<<grid_for(n), kBlock, 0, b.st>>>(n, sro, ro, cursor);
-            count_launch();
-            if (m > 0) {
-                k_scatter_sym<<<grid_for(m), kBlock, 0, b.st>>>(m, esrc, col, ro, sro, cursor, scol);
-                count_launch();
-                k_src_from_rows<<<grid_for((int64_t)n * 32), kBlock, 0, b.st>>>(n, sro, ssrc);
-                count_launch();
-            }
-            b.check(cudaGetLastError(), "symmetrise");
-        }
-        if (deg) cudaFreeAsync(deg, b.st);
-        if (cursor) cudaFreeAsync(cursor, b.st);
+    g->s.n = n;
+    g->s.m = 2 * m;
+    g->info.n_isolated = -1;
+    if (!(create_flags & FG_GRAPH_LAZY)) {
+        build_src(b, v);
+        build_sym(b, g);
     }
-    s.row_off = sro;
-    s.col = scol;
-    s.w = nullptr;
-    s.src = ssrc;
-    if (b.status == FG_OK) make_buckets(b, s);
 
     if (t_src) cudaFreeAsync(t_src, b.st);
     if (t_dst) cudaFreeAsync(t_dst, b.st);
@@ -578,7 +605,6 @@ fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const i
     I.n_mid = v.n_mid;
     I.n_high = v.n_high;
     I.n_high_chunks = v.n_high_chunks;
-    I.n_isolated = s.n_zero;
     *out = g;
     return FG_OK;
 }
@@ -586,10 +612,59 @@ fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const i
 // The transposed view of the directed graph (in-neighbours with their
 // weights, bucketed by in-degree), built once on the first pull query and
 // kept with the graph.  Thread-safe: callers hold no lock.
+namespace {
+
+// Lazily built parts of a graph created with FG_GRAPH_LAZY; the caller holds
+// the graph's lock.  Arrays of a failed build stay with the graph (freed by
+// fg_graph_destroy) and the part is built again on the next use.
+fg_status ensure_src_locked(fg_graph *g) {
+    if (g->g.src) return FG_OK;
+    Builder b{g, (cudaStream_t)0};
+    View v = g->g;
+    build_src(b, v);
+    b.check(cudaStreamSynchronize(b.st), "edge sources");
+    if (b.status != FG_OK) return fail(b.status, b.msg);
+    g->g.src = v.src;
+    return FG_OK;
+}
+
+fg_status ensure_sym_locked(fg_graph *g) {
+    if (g->s.row_off) return FG_OK;
+    fg_status st = ensure_src_locked(g);
+    if (st != FG_OK) return st;
+    Builder b{g, (cudaStream_t)0};
+    build_sym(b, g);
+    b.check(cudaStreamSynchronize(b.st), "symmetrised view");
+    if (b.status != FG_OK) {
+        g->s.row_off = nullptr;   // built again on the next use
+        return fail(b.status, b.msg);
+    }
+    return FG_OK;
+}
+
+}  // namespace
+
+fg_status ensure_views(const fg_graph *cg, Algo algo, int mode) {
+    fg_graph *g = const_cast<fg_graph *>(cg);
+    if (algo != kCC && mode == kPull) return ensure_transpose(cg);
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (algo == kCC) return ensure_sym_locked(g);
+    if (mode == kEdgeSync || mode == kEdgeAsync || mode < 0) return ensure_src_locked(g);
+    return FG_OK;
+}
+
+fg_status ensure_src(const fg_graph *cg) {
+    fg_graph *g = const_cast<fg_graph *>(cg);
+    std::lock_guard<std::mutex> lk(g->mu);
+    return ensure_src_locked(g);
+}
+
 fg_status ensure_transpose(const fg_graph *cg) {
     fg_graph *g = const_cast<fg_graph *>(cg);
     std::lock_guard<std::mutex> lk(g->mu);
     if (g->t_ready) return FG_OK;
+    fg_status sst = ensure_src_locked(g);
+    if (sst != FG_OK) return sst;
     const View &v = g->g;
     const int32_t n = v.n;
     const int64_t m = v.m;

@@ -116,25 +116,37 @@ extern "C" {
 
 fg_status fg_graph_create_coo(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
                               const int32_t *w, fg_graph **out) {
+    return fg_graph_create_coo_ex(n, m, src, dst, w, 0u, out);
+}
+
+fg_status fg_graph_create_csr(int32_t n, int64_t m, const int64_t *row_off, const int32_t *col,
+                              const int32_t *w, fg_graph **out) {
+    return fg_graph_create_csr_ex(n, m, row_off, col, w, 0u, out);
+}
+
+fg_status fg_graph_create_coo_ex(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                                 const int32_t *w, uint32_t flags, fg_graph **out) {
     if (!out) return fail(FG_ERR_INVALID_ARG, "out is NULL");
+    if (flags & ~FG_GRAPH_LAZY) return fail(FG_ERR_INVALID_ARG, "unknown graph creation flags");
     if (n <= 0) return fail(FG_ERR_INVALID_ARG, "n must be positive");
     if (m < 0) return fail(FG_ERR_INVALID_ARG, "m must be non-negative");
     if (m >= ((int64_t)1 << 31)) return fail(FG_ERR_INVALID_ARG, "m must be below 2^31 (the symmetrised copy uses 32-bit offsets)");
     if (m > 0 && (!src || !dst)) return fail(FG_ERR_INVALID_ARG, "src or dst is NULL");
     if (!ensure_device(nullptr)) return fail(FG_ERR_CUDA, "no CUDA device");
-    return build_graph_from_coo(n, m, src, dst, w, false, nullptr, out);
+    return build_graph_from_coo(n, m, src, dst, w, false, nullptr, flags, out);
 }
 
-fg_status fg_graph_create_csr(int32_t n, int64_t m, const int64_t *row_off, const int32_t *col,
-                              const int32_t *w, fg_graph **out) {
+fg_status fg_graph_create_csr_ex(int32_t n, int64_t m, const int64_t *row_off, const int32_t *col,
+                                 const int32_t *w, uint32_t flags, fg_graph **out) {
     if (!out) return fail(FG_ERR_INVALID_ARG, "out is NULL");
+    if (flags & ~FG_GRAPH_LAZY) return fail(FG_ERR_INVALID_ARG, "unknown graph creation flags");
     if (n <= 0) return fail(FG_ERR_INVALID_ARG, "n must be positive");
     if (m < 0) return fail(FG_ERR_INVALID_ARG, "m must be non-negative");
     if (m >= ((int64_t)1 << 31)) return fail(FG_ERR_INVALID_ARG, "m must be below 2^31 (the symmetrised copy uses 32-bit offsets)");
     if (!row_off) return fail(FG_ERR_INVALID_ARG, "row_off is NULL");
     if (m > 0 && !col) return fail(FG_ERR_INVALID_ARG, "col is NULL");
     if (!ensure_device(nullptr)) return fail(FG_ERR_CUDA, "no CUDA device");
-    return build_graph_from_coo(n, m, nullptr, col, w, true, row_off, out);
+    return build_graph_from_coo(n, m, nullptr, col, w, true, row_off, flags, out);
 }
 
 fg_status fg_graph_destroy(fg_graph *g) {
@@ -152,6 +164,7 @@ fg_status fg_graph_destroy(fg_graph *g) {
 
 fg_status fg_graph_info(const fg_graph *g, fg_graph_info_t *out) {
     if (!g || !out) return fail(FG_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(g->mu);   // lazily built parts update it
     *out = g->info;
     return FG_OK;
 }

@@ -177,6 +177,10 @@ int32_t default_delta(const fg_graph *G) {
 
 fg_status run_query(const fg_graph *G, Algo algo, Mode mode, int32_t source, int32_t *out,
                     const fg_options *opt, fg_stats *stats) {
+    if (kernel_for(algo, mode)) {   // the parts of a FG_GRAPH_LAZY graph this query reads
+        fg_status vs = ensure_views(G, algo, (int)mode);
+        if (vs != FG_OK) return vs;
+    }
     const View &g = (algo == kCC) ? G->s : G->g;
     const int32_t n = g.n;
     cudaStream_t st = opt && opt->stream ? (cudaStream_t)opt->stream : (cudaStream_t)0;
@@ -187,10 +191,6 @@ fg_status run_query(const fg_graph *G, Algo algo, Mode mode, int32_t source, int
     if (!dp.coop) return fail(FG_ERR_CUDA, "device does not support cooperative launches");
     KernelFn fn = kernel_for(algo, mode);
     if (!fn) return fail(FG_ERR_INVALID_ARG, "invalid algorithm or mode");
-    if (mode == kPull && algo != kCC) {
-        fg_status ts = ensure_transpose(G);
-        if (ts != FG_OK) return ts;
-    }
 
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, kBlock, 0);
@@ -260,8 +260,13 @@ fg_status run_query(const fg_graph *G, Algo algo, Mode mode, int32_t source, int
         } else if ((hc.status & kStOverflow) && algo == kSSSP) {
             int *flag = reinterpret_cast<int *>(p.ctrl);   // reuse the control block
             int hf = 0;
+            const fg_status ss = ensure_src(G);   // the check reads the edge sources
+            if (ss != FG_OK) {
+                status = ss;
+                msg = fg_last_error();
+            }
             e = cudaMemsetAsync(flag, 0, sizeof(int), st);
-            if (e == cudaSuccess) {
+            if (e == cudaSuccess && ss == FG_OK) {
                 overflow_check_kernel<<<dp.sms * 8, kBlock, 0, st>>>(g, result, flag);
                 count_launch();
                 e = cudaGetLastError();
@@ -315,6 +320,10 @@ fg_status run_sweep(const fg_graph *G, Mode mode, const int32_t *cur, int32_t *n
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != G->device) return fail(FG_ERR_INVALID_ARG, "the current device is not the graph's device");
+    if (mode == kEdgeSync) {   // the edge variant streams the edge sources
+        fg_status ss = ensure_src(G);
+        if (ss != FG_OK) return ss;
+    }
     DeviceProps dp = device_props(dev);
     auto fn = (mode == kVertexSync) ? sweep_kernel<kVertexSync> : sweep_kernel<kEdgeSync>;
     int per_sm = 0;

@@ -330,7 +330,7 @@ fg_status cuda_fail(cudaError_t e, const char *what);
 
 // graph construction (fg_build.cu)
 fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
-                               const int32_t *w, bool src_sorted_csr, const int64_t *row_off_in,
+                               const int32_t *w, bool src_sorted_csr, const int64_t *row_off_in, uint32_t flags,
                                fg_graph **out);
 
 // 256-byte aligned bump allocator over one device allocation
@@ -355,6 +355,13 @@ void carve_query_workspace(char *base, const View &g, Algo algo, Mode mode, Para
 
 // the transposed view for pull queries (fg_build.cu)
 fg_status ensure_transpose(const fg_graph *g);
+
+// Graphs created with FG_GRAPH_LAZY build their edge sources and symmetrised
+// view on first use.  ensure_views builds what a query of `algo` in `mode`
+// reads (mode < 0: whatever any mode of `algo` reads, the transposed view
+// excepted); ensure_src builds the edge sources alone.  Thread-safe.
+fg_status ensure_views(const fg_graph *g, Algo algo, int mode);
+fg_status ensure_src(const fg_graph *g);
 
 // queries (fg_fixpoint.cu)
 int32_t default_delta(const fg_graph *G);

@@ -286,6 +286,11 @@ fg_status fg_server_submit(fg_server *s, const fg_query *q, uint64_t *ticket) {
         if (st != FG_OK) return st;
     }
     qq.mode = (int32_t)m;
+    {   // a FG_GRAPH_LAZY graph builds the parts this request reads now, so
+        // that the request's workspace size is known and no wave builds them
+        fg_status vs = ensure_views(qq.g, (Algo)qq.algo, (int)m);
+        if (vs != FG_OK) return vs;
+    }
     const int64_t edges = (qq.algo == FG_ALGO_CC) ? qq.g->s.m : qq.g->g.m;
     const bool exclusive = s->opt.exclusive_edges > 0 && edges >= s->opt.exclusive_edges;
     fg_server::Req r{0, qq, Clock::now(), request_bytes(qq, (Mode)m), exclusive};

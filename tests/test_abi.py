@@ -99,6 +99,11 @@ def test_host_side_argument_checks():
     st = fg.load().fg_graph_create_coo(3, 1 << 31, src.ctypes.data, dst.ctypes.data, None,
                                        ctypes.byref(ctypes.c_void_p()))
     assert st == fg.FG_ERR_INVALID_ARG
+    for bad_flags in (2, 0x80000000):
+        st, g = fg.fg_graph_create_coo(3, src, dst, flags=bad_flags)
+        assert st == fg.FG_ERR_INVALID_ARG and g is None and "flags" in fg.fg_last_error()
+        st, g = fg.fg_graph_create_csr(3, np.array([0, 1, 2, 2], np.int64), dst, flags=bad_flags)
+        assert st == fg.FG_ERR_INVALID_ARG and g is None
     out = np.zeros(3, np.int32)
     assert fg.fg_sssp(None, 0, out) == fg.FG_ERR_INVALID_ARG
     assert fg.fg_cc(None, out) == fg.FG_ERR_INVALID_ARG

@@ -218,3 +218,59 @@ def test_edge_async_dense_generations_stream():
                 np.testing.assert_array_equal(got, want, err_msg=f"{g.name} {algo}")
                 if algo == "cc" or g.name.startswith("rmat"):
                     assert st.scanned > 0, (g.name, algo)
+
+
+def _info(h):
+    st, info = fg.fg_graph_info(h)
+    fg.check(st)
+    return info
+
+
+def test_lazy_graph_builds_parts_on_first_use():
+    """FG_GRAPH_LAZY: the CSR alone at creation; the edge sources on the first
+    edge-based query, the symmetrised view on the first CC query (and in a
+    batch); every result stays the oracle's."""
+    g = gg.rmat(12, seed=51)
+    s = int(gg.sources(g, 1, seed=52)[0])
+    want = {"sssp": oracle.sssp(g.n, g.src, g.dst, g.w, s)[1], "bfs": oracle.bfs(g.n, g.src, g.dst, s)[1],
+            "cc": oracle.cc(g.n, g.src, g.dst)[1]}
+    with graph_handle(g) as hf:
+        full = _info(hf)
+    st, h = fg.fg_graph_create_coo(g.n, g.src, g.dst, g.w, flags=fg.FG_GRAPH_LAZY)
+    fg.check(st)
+    try:
+        b0 = _info(h).device_bytes
+        assert b0 < full.device_bytes and _info(h).n_isolated == -1
+        got, _ = run(h, g.n, ALGOS["sssp"], s, fg.FG_VERTEX_SYNC)
+        np.testing.assert_array_equal(got, want["sssp"])
+        assert _info(h).device_bytes == b0            # vertex modes read the CSR only
+        got, _ = run(h, g.n, ALGOS["bfs"], s, fg.FG_EDGE_ASYNC)
+        np.testing.assert_array_equal(got, want["bfs"])
+        b1 = _info(h).device_bytes
+        assert b1 >= b0 + 4 * g.m                     # the edge sources
+        lab = np.zeros(g.n, np.int32)
+        st_, sts, _, _ = fg.fg_run_batch([(h, fg.FG_ALGO_CC, 0, lab, fg.FG_EDGE_SYNC)])
+        fg.check(st_)
+        fg.check(sts[0])
+        np.testing.assert_array_equal(lab, want["cc"])
+        assert _info(h).n_isolated == full.n_isolated
+        assert _info(h).device_bytes == full.device_bytes
+        for algo in ("sssp", "bfs", "cc"):
+            for mode in MODES:
+                got, _ = run(h, g.n, ALGOS[algo], s, mode)
+                np.testing.assert_array_equal(got, want[algo], err_msg=f"{algo} mode {mode}")
+    finally:
+        fg.check(fg.fg_graph_destroy(h))
+    # the edge variant of the all-active round on a fresh lazy graph
+    import torch
+    st, h = fg.fg_graph_create_coo(g.n, g.src, g.dst, g.w, flags=fg.FG_GRAPH_LAZY)
+    fg.check(st)
+    try:
+        cur = np.where(want["sssp"] == fg.FG_INF, 1 << 30, want["sssp"]).astype(np.int32)
+        _, exp, _ = oracle.sweep(g.n, g.src, g.dst, g.w, cur, cur)
+        nxt = torch.from_numpy(cur.copy()).cuda()
+        st, _, _ = fg.fg_sweep(h, fg.FG_EDGE_SYNC, torch.from_numpy(cur).cuda(), nxt)
+        fg.check(st)
+        np.testing.assert_array_equal(nxt.cpu().numpy(), exp)
+    finally:
+        fg.check(fg.fg_graph_destroy(h))
