@@ -171,6 +171,7 @@ struct BfsSyncOp {
     static constexpr bool kNextProbe = false;
     int32_t *L;
     int32_t lev;
+    uint32_t *vis;     // visited bitmap: the probe's 32x denser copy of "L[v] != INF"
 
     __device__ __forceinline__ bool active(int32_t u, int32_t &val, bool &) const {
         val = lev;
@@ -196,10 +197,15 @@ struct BfsSyncOp {
         c = lev + 1;
         return true;
     }
-    __device__ __forceinline__ int32_t probe(int32_t v) const { return ldca(L + v); }
+    // The probe reads the visited bitmap (n/8 bytes, mostly L1 hits) instead
+    // of the level array: a visited vertex has a level <= lev + 1 and cannot
+    // be lowered.  A stale copy misses only bits set in this round, whose
+    // vertices then get the same level stored again.
+    __device__ __forceinline__ int32_t probe(int32_t v) const { return vis_test(vis, v) ? 0 : kInf; }
     __device__ __forceinline__ bool commit(int32_t v, int32_t c, int32_t pv, Acc &a) const {
         if (pv > c) {
             stcg(L + v, c);
+            red_or(vis + (v >> 5), 1u << (v & 31));
             a.changed++;
             a.updates++;
         }
@@ -305,6 +311,7 @@ struct BfsAsyncOp {
     static constexpr bool kNextProbe = false;
     int32_t *L;
     int32_t gen;
+    uint32_t *vis;     // visited bitmap; a vertex is claimed by setting its bit
     static constexpr bool kRefreshWindow = false;
 
     __device__ __forceinline__ bool active(int32_t, int32_t &val, bool &) const {
@@ -317,16 +324,17 @@ struct BfsAsyncOp {
         c = gen + 1;
         return true;
     }
-    // a level, once claimed, never changes: an L1 copy that shows it set is
-    // exact, one that shows INF may be stale and the CAS decides
-    __device__ __forceinline__ int32_t probe(int32_t v) const { return ldca(L + v); }
+    // a vertex, once claimed, stays claimed: an L1 copy of its bitmap word
+    // that shows the bit is exact, one that does not may be stale and the
+    // atomic OR decides; its one winner stores the level and queues it
+    __device__ __forceinline__ int32_t probe(int32_t v) const { return vis_test(vis, v) ? 0 : kInf; }
     __device__ __forceinline__ bool commit(int32_t v, int32_t c, int32_t pv, Acc &a) const {
         if (pv != kInf) return false;
-        if (atomicCAS(L + v, kInf, c) == kInf) {
-            a.updates++;
-            return true;
-        }
-        return false;
+        const uint32_t bit = 1u << (v & 31);
+        if (atomicOr(vis + (v >> 5), bit) & bit) return false;
+        stcg(L + v, c);
+        a.updates++;
+        return true;
     }
 };
 
@@ -1001,6 +1009,7 @@ struct PullMinOp {
 struct BfsPullOp {
     int32_t *L;
     int32_t lev;
+    uint32_t *vis;     // kept in step with L for the push rounds' probes
     static constexpr bool kEarly = true;
     static constexpr bool kWeights = false;
 
@@ -1011,12 +1020,14 @@ struct BfsPullOp {
     __device__ __forceinline__ void finish(int32_t v, int32_t m, Acc &a) const {
         if (m == 0) {
             stcg(L + v, lev + 1);
+            red_or(vis + (v >> 5), 1u << (v & 31));
             a.changed++;
             a.updates++;
         }
     }
     __device__ __forceinline__ void finish_part(int32_t v, int32_t m, bool, Acc &a) const {
         if (m == 0 && atomicCAS(L + v, kInf, lev + 1) == kInf) {
+            red_or(vis + (v >> 5), 1u << (v & 31));
             a.changed++;
             a.updates++;
         }
@@ -1748,6 +1759,9 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
         if (!SYNC && ALGO != kBFS) p.S0[v] = 0;
         if (MODE == kBucket && ALGO == kSSSP) p.far_mark[v] = 0;
     }
+    if (ALGO == kBFS)   // visited bitmap: the source alone
+        for (int64_t k = tid; k < ((int64_t)n + 31) / 32; k += nth)
+            p.vis[k] = (k == (p.source >> 5)) ? 1u << (p.source & 31) : 0u;
     if (MODE == kBucket && tid == 0)
         for (int k = 0; k < 3; k++) c->far_min[k] = kInf;
     if (MODE == kEdgeSync)
@@ -1809,9 +1823,9 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
             const bool pull = (MODE == kPull) && pull_round(r);
             if (pull && tid == 0) c->pull_rounds++;
             if constexpr (ALGO == kBFS) {
-                BfsSyncOp op{p.A, r - 1};
+                BfsSyncOp op{p.A, r - 1, p.vis};
                 if (pull) {
-                    pull_vertices(t, p.tv, BfsPullOp{p.A, r - 1}, a);
+                    pull_vertices(t, p.tv, BfsPullOp{p.A, r - 1, p.vis}, a);
                 } else if constexpr (MODE == kVertexSync || MODE == kPull) {
                     expand_vertices(t, g.row_off, g.col, g.low, 0, g.mid, g.n_mid, g.high, g.n_high_chunks, op,
                                     NoPush{}, a);
@@ -2009,7 +2023,7 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
                                reinterpret_cast<int2 *>(p.wl[po][kWlHigh]), osize,
                                p.wl_cap[kWlLow], p.wl_cap[kWlMid], p.wl_cap[kWlHigh] / 2, &wb[0], &wb[1], c};
                 if constexpr (ALGO == kBFS) {
-                    BfsAsyncOp op{p.A, gen};
+                    BfsAsyncOp op{p.A, gen, p.vis};
                     expand_vertices(t, g.row_off, g.col, low, n_in[kWlLow], mid, n_in[kWlMid], high, n_in[kWlHigh],
                                     op, push, a);
                 } else if constexpr (MODE == kBucket && ALGO == kSSSP) {
@@ -2040,10 +2054,10 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
                 if constexpr (ALGO == kBFS) {
                     if (dense) {
                         BfsStreamOp op;
-                        op.L = p.A; op.gen = gen;
+                        op.L = p.A; op.gen = gen; op.vis = p.vis;
                         stream_edges_async<false>(t, g, op, push, a);
                     } else {
-                        BfsAsyncOp op{p.A, gen};
+                        BfsAsyncOp op{p.A, gen, p.vis};
                         lb_expand(t, g.row_off, g.col, items, n_in[0], goff, T, op, push, a);
                     }
                 } else {

@@ -120,6 +120,7 @@ size_t query_workspace_bytes(const View &g, Algo algo, Mode mode) {
     if (sync && algo != kBFS) need += 3 * Workspace::need(n, 4);
     const int64_t nwt = (g.m + kWTile - 1) / kWTile;   // edge-sync: one flag per 128-edge warp tile
     if (mode == kEdgeSync) need += Workspace::need(nwt, 4);
+    if (algo == kBFS) need += Workspace::need(((int64_t)n + 31) / 32, 4);
     if (!sync) {
         if (algo != kBFS) need += Workspace::need(n, 4);
         for (int k = 0; k < 3; k++) need += 2 * Workspace::need(wl_cap_of(g, mode, k), 4);
@@ -145,6 +146,7 @@ void carve_query_workspace(char *base, const View &g, Algo algo, Mode mode, Para
         p.S1 = ws.take<int32_t>(n);
     }
     if (mode == kEdgeSync) p.eflag = ws.take<int32_t>(nwt);
+    if (algo == kBFS) p.vis = ws.take<uint32_t>(((int64_t)n + 31) / 32);
     if (!sync) {
         if (algo != kBFS) p.S0 = ws.take<int32_t>(n);
         for (int par = 0; par < 2; par++)

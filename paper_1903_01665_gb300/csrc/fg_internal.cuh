@@ -108,6 +108,7 @@ struct Params {
     int32_t wl_cap[3] = {};     // capacity per class (in int32 slots)
     uint32_t *lb_off[2] = {};   // edge-async: global edge offset of each worklist item, by parity
     int32_t *eflag = nullptr;   // edge-sync sparse rounds: round stamp per 128-edge warp tile
+    uint32_t *vis = nullptr;    // BFS: visited bitmap, bit v set once v has a level
     int32_t *far[2] = {};       // bucket mode: far lists by epoch parity
     int32_t *far_mark = nullptr; // bucket mode: epoch in whose far list a vertex is
     int32_t far_cap = 0;
@@ -160,6 +161,16 @@ __device__ __forceinline__ void stcg(int32_t *p, int32_t v) { __stcg(p, v); }
 // atomic MIN whose result is not needed (a reduction: no round trip)
 __device__ __forceinline__ void red_min(int32_t *p, int32_t v) {
     asm volatile("red.relaxed.gpu.global.min.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// atomic OR whose result is not needed
+__device__ __forceinline__ void red_or(uint32_t *p, uint32_t v) {
+    asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// BFS visited bitmap: bit v & 31 of word v >> 5.  Bits are only ever set
+// during a query, so a stale (L1) copy can only miss bits, never show one.
+__device__ __forceinline__ bool vis_test(const uint32_t *vis, int32_t v) {
+    return (((uint32_t)__ldca(reinterpret_cast<const int32_t *>(vis) + (v >> 5))) >> (v & 31)) & 1u;
 }
 
 // ---------------------------------------------------------------- bulk copies (TMA)
