@@ -274,6 +274,21 @@ struct AsyncOp {
     }
 };
 
+// Dense vertex-async SSSP generation: every vertex is tested instead of the
+// worklist's items; a vertex is expanded if it was queued for this
+// generation (stamp g) or lowered during it (stamp g + 1, queued for the
+// next as well): a relaxation with a current distance is always valid.
+#ifndef FG_VA_DENSE_DIV
+#define FG_VA_DENSE_DIV 4
+#endif
+struct AsyncScanOp : AsyncOp<kSSSP> {
+    __device__ __forceinline__ bool active(int32_t u, int32_t &val, bool &) const {
+        if (ldca(stamp + u) < gen) return false;
+        val = ldcg(D + u);
+        return val != kInf;
+    }
+};
+
 // Bucketed SSSP (near-far): as AsyncOp, but a target whose new distance is
 // not below the threshold T goes to the far list of the current epoch (once
 // per epoch, by far_mark) instead of the next generation's worklist.
@@ -2034,9 +2049,17 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
                     expand_vertices(t, g.row_off, g.col, low, n_in[kWlLow], mid, n_in[kWlMid], high, n_in[kWlHigh],
                                     op, push, a);
                 } else {
-                    AsyncOp<ALGO> op{g.w, p.A, p.S0, gen};
-                    expand_vertices(t, g.row_off, g.col, low, n_in[kWlLow], mid, n_in[kWlMid], high, n_in[kWlHigh],
-                                    op, push, a);
+                    const int64_t items = (int64_t)n_in[kWlLow] + n_in[kWlMid] + n_in[kWlHigh];
+                    if (ALGO == kSSSP && FG_VA_DENSE_DIV > 0 && items * FG_VA_DENSE_DIV >= (int64_t)g.n_nz) {
+                        AsyncScanOp op;
+                        op.w = g.w; op.D = p.A; op.stamp = p.S0; op.gen = gen;
+                        expand_vertices(t, g.row_off, g.col, g.low, g.n_low, g.mid, g.n_mid, g.high, g.n_high_chunks,
+                                        op, push, a);
+                    } else {
+                        AsyncOp<ALGO> op{g.w, p.A, p.S0, gen};
+                        expand_vertices(t, g.row_off, g.col, low, n_in[kWlLow], mid, n_in[kWlMid], high,
+                                        n_in[kWlHigh], op, push, a);
+                    }
                 }
                 push.flush();
             } else {
