@@ -52,10 +52,10 @@ ALGO_NAMES = ["sssp", "bfs", "cc"]
 # at capture time).
 NCU_TRAFFIC: dict = {
     # profiles/sssp_rmat22_traffic.md: one launch each, first seeded source, R-MAT 22
-    "fixpoint_kernel<sssp,vertex_sync>": {"bytes_per_launch": 4246974976 + 545092864, "src_sha": "911514d77fb24fda"},
-    "fixpoint_kernel<sssp,vertex_async>": {"bytes_per_launch": 2951216384 + 203084288, "src_sha": "911514d77fb24fda"},
-    "fixpoint_kernel<sssp,edge_sync>": {"bytes_per_launch": 5304832256 + 203370496, "src_sha": "911514d77fb24fda"},
-    "fixpoint_kernel<sssp,edge_async>": {"bytes_per_launch": 4305143040 + 251591680, "src_sha": "911514d77fb24fda"},
+    "fixpoint_kernel<sssp,vertex_sync>": {"bytes_per_launch": 4246765824 + 546964736, "src_sha": "32850671656ef4b4"},
+    "fixpoint_kernel<sssp,vertex_async>": {"bytes_per_launch": 2692361216 + 201051136, "src_sha": "32850671656ef4b4"},
+    "fixpoint_kernel<sssp,edge_sync>": {"bytes_per_launch": 5305813248 + 200901632, "src_sha": "32850671656ef4b4"},
+    "fixpoint_kernel<sssp,edge_async>": {"bytes_per_launch": 4290558720 + 247690496, "src_sha": "32850671656ef4b4"},
 }
 
 
