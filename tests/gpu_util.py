@@ -45,14 +45,24 @@ def graph_handle(g, kind="coo", where="host", weights=True):
         fg.check(fg.fg_graph_destroy(h))
 
 
-def run(h, n, algo, src, mode, where="device", **kw):
-    """Run one query; returns (result as numpy int32[n], stats)."""
+def make_out(n, where, fill=-7):
+    """An int32[n] output: "device" (torch CUDA), "host" (pageable numpy) or
+    "pinned" (page-locked torch CPU tensor)."""
     import torch
     if where == "device":
-        out = torch.full((n,), -7, dtype=torch.int32, device="cuda")
-    else:
-        out = np.full(n, -7, np.int32)
+        return torch.full((n,), fill, dtype=torch.int32, device="cuda")
+    if where == "pinned":
+        return torch.full((n,), fill, dtype=torch.int32).pin_memory()
+    return np.full(n, fill, np.int32)
+
+
+def as_numpy(out):
+    return out.cpu().numpy() if hasattr(out, "cpu") else out
+
+
+def run(h, n, algo, src, mode, where="device", **kw):
+    """Run one query; returns (result as numpy int32[n], stats)."""
+    out = make_out(n, where)
     st, stats = fg.fg_run(h, algo, int(src), out, mode, **kw)
     fg.check(st)
-    res = out.cpu().numpy() if where == "device" else out
-    return res, stats
+    return as_numpy(out), stats

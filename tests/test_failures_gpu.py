@@ -8,7 +8,10 @@ import pytest
 import graphgen as gg
 import oracle
 import paper_1903_01665_gb300 as fg
-from tests.gpu_util import ALGOS, MODES, graph_handle, run
+from tests.gpu_util import ALGOS, MODES, as_numpy, graph_handle, make_out, run
+
+# host outputs: pageable numpy arrays and page-locked tensors
+HOST_OUTS = ["host", "pinned"]
 
 pytestmark = pytest.mark.gpu
 
@@ -47,47 +50,51 @@ def test_query_argument_errors():
         assert np.all(out == 99)
 
 
+@pytest.mark.parametrize("out_where", HOST_OUTS)
 @pytest.mark.parametrize("mode", MODES)
-def test_overflow_rule(mode):
+def test_overflow_rule(mode, out_where):
     g = gg.path(3, weights=[2**30, 2**30])
     with graph_handle(g) as h:
-        out = np.full(3, 99, np.int32)
+        out = make_out(3, out_where, 99)
         st, _ = fg.fg_run(h, fg.FG_ALGO_SSSP, 0, out, mode)
         assert st == fg.FG_ERR_OVERFLOW
-        assert np.all(out == 99), "outputs must be untouched on error"
+        assert np.all(as_numpy(out) == 99), "outputs must be untouched on error"
         st, _ = fg.fg_run(h, fg.FG_ALGO_BFS, 0, out, mode)   # BFS ignores weights
-        assert st == fg.FG_OK and out.tolist() == [0, 1, 2]
+        assert st == fg.FG_OK and as_numpy(out).tolist() == [0, 1, 2]
+    # dropped overflow candidates, correct result: the host's check clears it
     g = gg.Graph(3, [0, 0, 1], [1, 2, 2], [1, 1, 2**31 - 1], "shadowed")
     with graph_handle(g) as h:
-        got, _ = run(h, 3, fg.FG_ALGO_SSSP, 0, mode)
+        got, _ = run(h, 3, fg.FG_ALGO_SSSP, 0, mode, where=out_where)
         assert got.tolist() == [0, 1, 1]
     g = gg.path(3, weights=[2**31 - 2, 0])
     with graph_handle(g) as h:
-        got, _ = run(h, 3, fg.FG_ALGO_SSSP, 0, mode)
+        got, _ = run(h, 3, fg.FG_ALGO_SSSP, 0, mode, where=out_where)
         assert got.tolist() == [0, 2**31 - 2, 2**31 - 2]
 
 
+@pytest.mark.parametrize("out_where", HOST_OUTS)
 @pytest.mark.parametrize("mode", MODES)
-def test_round_cap_returns_timeout(mode):
+def test_round_cap_returns_timeout(mode, out_where):
     g = gg.path(200)
     with graph_handle(g) as h:
-        out = np.full(200, 99, np.int32)
+        out = make_out(200, out_where, 99)
         st, _ = fg.fg_run(h, fg.FG_ALGO_SSSP, 0, out, mode, max_rounds=5)
         assert st == fg.FG_ERR_TIMEOUT and "round cap" in fg.fg_last_error()
-        assert np.all(out == 99)
+        assert np.all(as_numpy(out) == 99)
         # the same graph with the default cap converges
-        got, st = run(h, 200, fg.FG_ALGO_SSSP, 0, mode)
+        got, st = run(h, 200, fg.FG_ALGO_SSSP, 0, mode, where=out_where)
         assert got.tolist() == list(range(200))
 
 
+@pytest.mark.parametrize("out_where", HOST_OUTS)
 @pytest.mark.parametrize("mode", MODES)
-def test_missing_arrival_times_out_and_context_survives(mode):
+def test_missing_arrival_times_out_and_context_survives(mode, out_where):
     g = gg.rmat(12)
     _, d = oracle.sssp(g.n, g.src, g.dst, g.w, 0)
     with graph_handle(g) as h:
-        out = np.full(g.n, 99, np.int32)
+        out = make_out(g.n, out_where, 99)
         st, _ = fg.fg_run(h, fg.FG_ALGO_SSSP, 0, out, mode, wait_timeout_ms=50, inject_missing_arrival=1)
         assert st == fg.FG_ERR_TIMEOUT and "timeout" in fg.fg_last_error()
-        assert np.all(out == 99)
-        got, _ = run(h, g.n, fg.FG_ALGO_SSSP, 0, mode)
+        assert np.all(as_numpy(out) == 99)
+        got, _ = run(h, g.n, fg.FG_ALGO_SSSP, 0, mode, where=out_where)
         np.testing.assert_array_equal(got, d)

@@ -119,7 +119,7 @@ def test_sync_round_counts_equal_jacobi(name):
 
 
 @pytest.mark.parametrize("kind,where,out_where", [("coo", "device", "host"), ("csr", "host", "device"),
-                                                  ("csr", "device", "host")])
+                                                  ("csr", "device", "host"), ("coo", "host", "pinned")])
 def test_input_forms_and_host_outputs(kind, where, out_where):
     g = gg.rmat(12, seed=77)
     s = int(gg.sources(g, 1, seed=78)[0])
