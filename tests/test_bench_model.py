@@ -1,0 +1,55 @@
+"""The bench's algorithmic-byte model on hand-made counters (host logic, no
+GPU): each variant's bytes per query, written out term by term from the byte
+model of the measurement design, so that a dropped or misplaced term in
+bench.algorithmic_bytes fails here."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+INFO = {"n": 1000}
+
+
+def stats(S=0, Va=0, Ea=0, U=0, P=0, jumps=0):
+    return {"scanned": S, "vertices_processed": Va, "edges_relaxed": Ea, "updates": U, "pushes": P,
+            "jump_passes": jumps}
+
+
+def test_sync_modes():
+    st = stats(S=500, Va=40, Ea=300, U=7)
+    # SSSP: 4 per activity word, 16 per expanded vertex, 12 per edge, 12 per update
+    assert bench.algorithmic_bytes(0, 0, st, INFO) == 4 * 500 + 16 * 40 + 12 * 300 + 12 * 7
+    assert bench.algorithmic_bytes(0, 2, st, INFO) == 4 * 500 + 16 * 40 + 12 * 300 + 12 * 7
+    # BFS: 8 per vertex, 8 per edge, 4 per update
+    assert bench.algorithmic_bytes(1, 0, st, INFO) == 4 * 500 + 8 * 40 + 8 * 300 + 4 * 7
+    # CC: 8 per edge, plus 8 bytes per vertex per pointer-jumping pass
+    st_cc = stats(S=500, Va=40, Ea=300, U=7, jumps=3)
+    assert bench.algorithmic_bytes(2, 2, st_cc, INFO) == 4 * 500 + 16 * 40 + 8 * 300 + 12 * 7 + 3 * 1000 * 8
+
+
+def test_async_modes():
+    st = stats(Va=40, Ea=300, U=7, P=5)
+    # vertex-async SSSP: 16 per item, 12 per edge, 12 per update, 8 per push
+    assert bench.algorithmic_bytes(0, 1, st, INFO) == 16 * 40 + 12 * 300 + 12 * 7 + 8 * 5
+    # BFS items and claims are smaller
+    assert bench.algorithmic_bytes(1, 1, st, INFO) == 12 * 40 + 8 * 300 + 8 * 7 + 8 * 5
+    # edge-async: + 16 per item for the degree prefix ...
+    assert bench.algorithmic_bytes(0, 3, st, INFO) == 32 * 40 + 12 * 300 + 12 * 7 + 8 * 5
+    # ... and the edge sources its dense generations stream
+    st_dense = stats(S=2000, Va=40, Ea=300, U=7, P=5)
+    assert bench.algorithmic_bytes(0, 3, st_dense, INFO) == 4 * 2000 + 32 * 40 + 12 * 300 + 12 * 7 + 8 * 5
+    # vertex-async ignores the scan counter (its dense generations read no edge sources)
+    assert bench.algorithmic_bytes(0, 1, st_dense, INFO) == 16 * 40 + 12 * 300 + 12 * 7 + 8 * 5
+
+
+def test_model_grows_with_every_counter():
+    base = stats(S=10, Va=10, Ea=10, U=10, P=10, jumps=1)
+    for algo, mode in [(0, 0), (0, 1), (0, 2), (0, 3), (1, 0), (1, 3), (2, 0), (2, 1)]:
+        b0 = bench.algorithmic_bytes(algo, mode, base, INFO)
+        for key in ("vertices_processed", "edges_relaxed", "updates"):
+            more = dict(base)
+            more[key] += 1
+            assert bench.algorithmic_bytes(algo, mode, more, INFO) > b0, (algo, mode, key)
