@@ -1897,7 +1897,12 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
                 break;
             }
             if (ALGO == kCC) {
-                // pointer jumping on next until a pass changes nothing
+                // pointer jumping on next until every label is a root.  A
+                // label only points to a smaller id and a root (l with
+                // next[l] == l) never changes while jumping, so each vertex
+                // follows its chain up to 8 steps per pass; a pass in which
+                // every chain reached its root leaves labels that jumping
+                // cannot change, and ends the phase without a further pass.
                 int32_t *next = (r & 1) ? p.B : p.A;
                 int32_t *snext = (r & 1) ? p.S0 : p.S1;
                 bool jok = true;
@@ -1905,15 +1910,25 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
                     int slot = pass_ctr % 3;
                     if (tid == 0) c->jchanged[(pass_ctr + 1) % 3] = 0;
                     pass_ctr++;
-                    int jc = 0;
+                    int jc = 0;   // chains not yet at their root
                     for (int64_t v = tid; v < n; v += nth) {
-                        int32_t l = ldcg(next + v);
-                        if (l == (int32_t)v) continue;
-                        int32_t ll = ldcg(next + l);
-                        if (ll < l) {
-                            atomicMin(next + v, ll);
+                        const int32_t l0 = ldcg(next + v);
+                        if (l0 == (int32_t)v) continue;
+                        int32_t l = l0;
+                        bool root = false;
+#pragma unroll 1
+                        for (int k = 0; k < 8; k++) {
+                            const int32_t ll = ldcg(next + l);
+                            if (ll == l) {
+                                root = true;
+                                break;
+                            }
+                            l = ll;
+                        }
+                        if (!root) jc++;
+                        if (l < l0) {
+                            atomicMin(next + v, l);
                             stcg(snext + v, r + 1);
-                            jc++;
                         }
                     }
                     jc = block_sum(jc);
