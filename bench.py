@@ -52,10 +52,10 @@ ALGO_NAMES = ["sssp", "bfs", "cc"]
 # at capture time).
 NCU_TRAFFIC: dict = {
     # profiles/sssp_rmat22_traffic.md: one launch each, first seeded source, R-MAT 22
-    "fixpoint_kernel<sssp,vertex_sync>": {"bytes_per_launch": 4246765824 + 546964736, "src_sha": "32850671656ef4b4"},
-    "fixpoint_kernel<sssp,vertex_async>": {"bytes_per_launch": 2692361216 + 201051136, "src_sha": "32850671656ef4b4"},
-    "fixpoint_kernel<sssp,edge_sync>": {"bytes_per_launch": 5305813248 + 200901632, "src_sha": "32850671656ef4b4"},
-    "fixpoint_kernel<sssp,edge_async>": {"bytes_per_launch": 4290558720 + 247690496, "src_sha": "32850671656ef4b4"},
+    "fixpoint_kernel<sssp,vertex_sync>": {"bytes_per_launch": 4246407936 + 546715392, "src_sha": "14303aa67d8410ae"},
+    "fixpoint_kernel<sssp,vertex_async>": {"bytes_per_launch": 2702572800 + 201716224, "src_sha": "14303aa67d8410ae"},
+    "fixpoint_kernel<sssp,edge_sync>": {"bytes_per_launch": 5307464192 + 201518592, "src_sha": "14303aa67d8410ae"},
+    "fixpoint_kernel<sssp,edge_async>": {"bytes_per_launch": 4287900416 + 246216448, "src_sha": "14303aa67d8410ae"},
 }
 
 
