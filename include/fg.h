@@ -13,7 +13,10 @@
  *   FG_EDGE_SYNC    edge-based over the COO edge list (edges, Alg. 2),
  *                   double-buffered values, one grid barrier per round;
  *   FG_VERTEX_ASYNC data-driven (Sec. 3.3): a device worklist of vertices,
- *                   in-place atomic MIN, run until the worklist is empty;
+ *                   in-place atomic MIN, run until the worklist is empty; an
+ *                   SSSP generation whose worklist holds a quarter of the
+ *                   vertices with out-edges or more tests every vertex
+ *                   instead (queued, or lowered during the generation);
  *   FG_EDGE_ASYNC   the same worklist expanded to its out-edges and relaxed
  *                   edge-parallel, in place; a generation whose worklist holds
  *                   a quarter of the edges or more (BFS: half) streams the
@@ -56,8 +59,10 @@
  *   - Every call returns an fg_status; nothing throws across the ABI.  On
  *     error, fg_last_error() gives a message for the calling thread and the
  *     outputs are untouched.
- *   - A graph handle is immutable after creation and may be queried from
- *     several host threads and streams at once; each query owns its state.
+ *   - A graph handle is immutable after creation (a FG_GRAPH_LAZY graph
+ *     only adds the parts it builds on first use, under a lock) and may be
+ *     queried from several host threads and streams at once; each query
+ *     owns its state.
  *   - Queries run on the calling thread's current CUDA device, which must
  *     be the device the graph was created on.
  */
