@@ -59,6 +59,10 @@ NCU_TRAFFIC: dict = {
 }
 
 
+# DRAM bytes of one all-active sweep launch (R-MAT 22, the sweep roofline
+# state), same validity rule
+NCU_SWEEP_DRAM: dict = {}
+
 KERNEL_SOURCES = ("fg_internal.cuh", "fg_device.cuh", "fg_fixpoint.cu")
 
 
@@ -132,6 +136,60 @@ def algorithmic_bytes(algo: int, mode: int, st: dict, info: dict) -> float:
     if algo == 2:
         b += st["jump_passes"] * n * 8
     return float(b)
+
+
+def survey_bytes(algo: int, mode: int, st: dict, info: dict) -> float:
+    """Algorithmic bytes of one query by the measurement plan's per-round
+    formulas (4-byte offsets o, ids and values), summed over the rounds run:
+
+      vertex-sync (and pull): V*(o + 4 cur + 8 next init/copy) per round + E_a*(4 col + 4 w + 4 next[dst])
+                              + 4*U
+      edge-sync:              V*8 per round + E_a*(12 src,dst,w + 4 dist[src] + 4 dist[dst]) + 4*U
+      async (vertex, edge, bucket): per processed vertex 2o + 4 dist[u] + 4 worklist read, per edge 12
+                              (col, w, target), 4 per worklist push, 4 per update
+      CC:                     the same on the symmetrised graph, + 8*V per pointer-jumping pass
+
+    with V vertices, R rounds, E_a relaxed edges, U successful updates.
+    Weights are counted for SSSP only: BFS and CC read none (4 bytes less
+    per edge)."""
+    R, Va, Ea, U, P = (st["rounds"], st["vertices_processed"], st["edges_relaxed"], st["updates"],
+                       st["pushes"])
+    V = info["n"]
+    wb = 4 if algo == 0 else 0
+    if mode in (0, 5):
+        b = 16 * V * R + (8 + wb) * Ea + 4 * U
+    elif mode == 2:
+        b = 8 * V * R + (16 + wb) * Ea + 4 * U
+    else:
+        b = 16 * Va + (8 + wb) * Ea + 4 * P + 4 * U
+    if algo == 2:
+        b += 8 * V * st["jump_passes"]
+    return float(b)
+
+
+def host_info() -> dict:
+    """The host the CPU baseline runs on: logical CPUs (nproc) and model name."""
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    import platform
+    return {"host_cores": int(cores or 0), "cpu_model": model or platform.processor() or platform.machine(),
+            "arch": platform.machine()}
 
 
 # ---------------------------------------------------------------- clocks
@@ -591,15 +649,18 @@ def run_ours(args):
     per_kernel = {}
     for algo, mode, st in record:
         k = (algo, mode)
-        d = per_kernel.setdefault(k, {"ms": 0.0, "bytes": 0.0, "launches": 0})
+        d = per_kernel.setdefault(k, {"ms": 0.0, "bytes": 0.0, "model_bytes": 0.0, "launches": 0})
         d["ms"] += st["kernel_ms"]
-        d["bytes"] += algorithmic_bytes(algo, mode, st, r.info)
+        d["bytes"] += survey_bytes(algo, mode, st, r.info)
+        d["model_bytes"] += algorithmic_bytes(algo, mode, st, r.info)
         d["launches"] += 1
     total_kernel_ms = sum(d["ms"] for d in per_kernel.values())
     dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
     dk = per_kernel[dom]
     peaks = load_peaks()
-    achieved = (dk["bytes"] / dk["launches"]) / (dk["ms"] / dk["launches"] * 1e-3) / 1e9
+    launch_s = dk["ms"] / dk["launches"] * 1e-3
+    achieved = (dk["bytes"] / dk["launches"]) / launch_s / 1e9
+    achieved_model = (dk["model_bytes"] / dk["launches"]) / launch_s / 1e9
     kname = f"fixpoint_kernel<{ALGO_NAMES[dom[0]]},{MODE_NAMES[dom[1]]}>"
     traffic = None
     rec = NCU_TRAFFIC.get(kname)
@@ -607,14 +668,18 @@ def run_ours(args):
         traffic = rec["bytes_per_launch"]
     roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peaks[0],
                 "unit": "GB/s", "frac": round(achieved / peaks[0], 4), "peak_source": peaks[1],
-                "traffic": traffic, "algorithmic_bytes_per_launch": dk["bytes"] / dk["launches"],
-                "avg_launch_ms": dk["ms"] / dk["launches"],
+                "bytes": "measurement-plan formula, per launch", "traffic": traffic,
+                "algorithmic_bytes_per_launch": round(dk["bytes"] / dk["launches"]),
+                "frac_model": round(achieved_model / peaks[0], 4),
+                "dram_frac": None if traffic is None else round(traffic / launch_s / 1e9 / peaks[0], 4),
+                "avg_launch_ms": round(dk["ms"] / dk["launches"], 4),
                 "share_of_kernel_time": round(dk["ms"] / total_kernel_ms, 4)}
     per_mode = {}
     for (algo, mode), d in sorted(per_kernel.items()):
         per_mode[f"{ALGO_NAMES[algo]}/{MODE_NAMES[mode]}"] = {
             "avg_ms": round(d["ms"] / d["launches"], 4),
-            "gbps": round(d["bytes"] / (d["ms"] * 1e-3) / 1e9, 1)}
+            "gbps": round(d["bytes"] / (d["ms"] * 1e-3) / 1e9, 1),
+            "gbps_model": round(d["model_bytes"] / (d["ms"] * 1e-3) / 1e9, 1)}
 
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
@@ -655,6 +720,16 @@ def run_ours(args):
         serving = run_serving(device, full=args.serving_full, n_req=args.serving_requests)
 
     if rank == 0:
+        if sweep is not None:
+            # the headline all-active round, in the roofline object the record keeps whole
+            roofline["sweep"] = {k: {"us": v["us"], "gbps": v["gbps"], "frac": v["frac"]}
+                                 for k, v in sweep.items() if isinstance(v, dict)}
+            sweep_dram = {k: v for k, v in NCU_SWEEP_DRAM.items()
+                          if v.get("src_sha") == fixpoint_source_sha()}
+            for k, v in sweep_dram.items():
+                if k in roofline["sweep"]:
+                    us = roofline["sweep"][k]["us"]
+                    roofline["sweep"][k]["dram_frac"] = round(v["bytes"] / (us * 1e-6) / 1e9 / peaks[0], 4)
         line = {"metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
@@ -663,14 +738,39 @@ def run_ours(args):
                            "teps_edges_per_step": units // max(args.steps, 1),
                            "l2": l2_note,
                            "parallelism": f"replicas x{ws}"},
-                "relaxations": {"value": round(relax_all / sec / 1e9, 3), "unit": "G edge relaxations/s",
-                                "per_step": relax_all // max(args.steps * ws, 1)},
-                "roofline": roofline, "sweep_roofline": sweep, "extra_modes": extra, "grid_bucket": grid_bucket,
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "per_kernel": per_mode, "batched": batched, "serving": serving}
-        print(json.dumps(line), flush=True)
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk,
+                "relaxations_gps": round(relax_all / sec / 1e9, 3)}
+        if batched is not None:
+            line["batched"] = {k: batched[k] for k in ("batched_qps", "one_at_a_time_qps", "speedup", "bit_exact",
+                                                       "launches") if k in batched}
+        if serving is not None:
+            line["serving"] = compact_serving(serving)
+        detail = {"per_kernel": per_mode, "sweep_roofline": sweep, "extra_modes": extra, "grid_bucket": grid_bucket,
+                  "batched": batched, "serving": serving,
+                  "relaxations_per_step": relax_all // max(args.steps * ws, 1)}
+        if args.detail:
+            with open(args.detail, "w") as f:
+                json.dump({"line": line, "detail": detail}, f, indent=1)
+        print(json.dumps(line, separators=(",", ":")), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+def compact_serving(serving: dict) -> dict:
+    """Per arrival rate: p50/p99 latency (ms) and completed requests/s of the
+    server (continuous batching) and of the one-at-a-time baseline."""
+    out = {"graphs": len(serving.get("resident_graphs", [])), "device_gb": serving.get("resident_device_gb"),
+           "requests": serving.get("requests_per_rate"), "rates": {}}
+    for row in serving.get("rates", []):
+        b, o = row["batched"], row["one_at_a_time"]
+        out["rates"][str(row["rate_per_s"])] = {
+            "p50": [round(b["p50_ms"], 1), round(o["p50_ms"], 1)],
+            "p99": [round(b["p99_ms"], 1), round(o["p99_ms"], 1)],
+            "qps": [b["completed_per_s"], o["completed_per_s"]],
+            "ok": bool(b["all_ok"] and o["all_ok"])}
+    out["order"] = "[server, one-at-a-time]"
+    return out
 
 
 def load_peaks():
@@ -695,9 +795,11 @@ def cpu_baseline_sample(g, srcs, deg, workload):
         oracle.cc(g.n, g.src, g.dst)
         units += g.m
     dt = time.perf_counter() - t0
-    return {"value": round(units / dt / 1e9, 5), "unit": "GTEPS", "cores": 1, "kind": "oracle",
-            "sample": f"1 SSSP + 1 BFS from source {s}" + (" + 1 CC" if workload != "er16k" else "")
-                      + f" on {workload}, sequential C, {dt:.1f} s"}
+    out = {"value": round(units / dt / 1e9, 5), "unit": "GTEPS", "cores": 1, "kind": "oracle",
+           "sample": f"1 SSSP + 1 BFS from source {s}" + (" + 1 CC" if workload != "er16k" else "")
+                     + f" on {workload}, sequential C, {dt:.1f} s"}
+    out.update(host_info())
+    return out
 
 
 def run_reference(args):
@@ -734,7 +836,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic (seeded generators in graphgen/)", "config": {"workload": desc},
             "cpu_baseline": {"value": round(value, 5), "unit": "GTEPS", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, **host_info()},
             "e2e": {"value": round(value, 5), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -800,6 +902,8 @@ def main():
     ap.add_argument("--serving-full", action="store_true",
                     help="serve the R-MAT 24-26 + 8192^2 grid resident set (~60 GB) instead of the reduced one")
     ap.add_argument("--serving-requests", type=int, default=2000)
+    ap.add_argument("--detail", default=None, help="also write every measurement (per kernel, extra modes, "
+                                                   "serving rows) as JSON to this path")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

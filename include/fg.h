@@ -277,8 +277,10 @@ fg_status fg_sweep(const fg_graph *g, fg_mode mode, const int32_t *cur, int32_t 
  * fail.  It computes what fg_sssp computes with FG_VERTEX_SYNC, directly from
  * a caller-owned CSR:
  *   n <= FG_NOALLOC_MAX_VERTICES vertices (larger n: FG_ERR_INVALID_ARG);
+ *   m < 2^31 edges (larger m: FG_ERR_INVALID_ARG);
  *   row_off[n+1] int64, col[m] int32, w[m] int32 (>= 0) or NULL for unit
- *   weights, dist_out[n] int32 -- all device memory of the current device;
+ *   weights, dist_out[n] int32 -- all device memory owned by the current
+ *   device (host memory, or memory of another device: FG_ERR_INVALID_ARG);
  *   stream: cudaStream_t or NULL for the legacy default stream.
  * Its scratch (a second distance buffer, two activity-stamp arrays and the
  * control block) is one fixed array of about 12 MiB in the library's device
@@ -288,10 +290,15 @@ fg_status fg_sweep(const fg_graph *g, fg_mode mode, const int32_t *cur, int32_t 
  * stream capture.  Every call on a device shares the one array and starts by
  * clearing its control block: calls that overlap on the GPU (another stream,
  * another host thread) race and must not be issued.  dist_out doubles as the
- * first distance buffer, so on error its contents are unspecified.  Blocks
- * until the result is written.  Errors: FG_ERR_INVALID_ARG (sizes, NULL,
- * host pointers, invalid CSR or negative weight), FG_ERR_OVERFLOW,
- * FG_ERR_TIMEOUT, FG_ERR_CUDA.
+ * first distance buffer, so on error its contents are unspecified.  The call
+ * waits for `stream` to finish its work before it returns.  Unlike fg_run,
+ * its limits are fixed: every device-side wait gives up after 1 s, and the
+ * round cap is n + 2 (a synchronous round count never exceeds n + 1 for
+ * non-negative weights, so valid input does not reach it); FG_ERR_TIMEOUT
+ * comes from either.  The CSR (offsets, ids) and the weights are validated
+ * on the device before any indexed access.  Errors: FG_ERR_INVALID_ARG
+ * (sizes, NULL, pointers that are not this device's memory, invalid CSR or
+ * negative weight), FG_ERR_OVERFLOW, FG_ERR_TIMEOUT, FG_ERR_CUDA.
  */
 #define FG_NOALLOC_MAX_VERTICES 1048576
 fg_status fg_sssp_csr_noalloc(int32_t n, int64_t m, const int64_t *row_off, const int32_t *col,

@@ -414,6 +414,8 @@ fg_status run_batch(const fg_query *qs, int32_t nq, const fg_batch_options *opt,
 
 // whether a pointer is device-accessible memory of the current device
 bool is_device_pointer(const void *p);
+// whether a pointer is device (or managed) memory whose owning device is dev
+bool is_device_pointer_on(const void *p, int dev);
 
 // process-wide count of kernels this library has launched
 void count_launch();

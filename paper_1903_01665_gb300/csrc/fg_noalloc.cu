@@ -198,9 +198,10 @@ extern "C" fg_status fg_sssp_csr_noalloc(int32_t n, int64_t m, const int64_t *ro
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= 64) return cuda_fail(e, "fg_sssp_csr_noalloc: no CUDA device");
-    if (!is_device_pointer(row_off) || !is_device_pointer(dist_out) || (m > 0 && !is_device_pointer(col)) ||
-        (w && !is_device_pointer(w)))
-        return fail(FG_ERR_INVALID_ARG, "fg_sssp_csr_noalloc: inputs and output must be device memory");
+    // every array must be memory of this device: the kernel has no peer path
+    if (!is_device_pointer_on(row_off, dev) || !is_device_pointer_on(dist_out, dev) ||
+        (m > 0 && !is_device_pointer_on(col, dev)) || (w && !is_device_pointer_on(w, dev)))
+        return fail(FG_ERR_INVALID_ARG, "fg_sssp_csr_noalloc: inputs and output must be device memory of the current device");
     unsigned char *scratch = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_na_mu);

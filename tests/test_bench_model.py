@@ -53,3 +53,52 @@ def test_model_grows_with_every_counter():
             more = dict(base)
             more[key] += 1
             assert bench.algorithmic_bytes(algo, mode, more, INFO) > b0, (algo, mode, key)
+
+
+def rstats(R=0, Va=0, Ea=0, U=0, P=0, jumps=0):
+    d = stats(Va=Va, Ea=Ea, U=U, P=P, jumps=jumps)
+    d["rounds"] = R
+    return d
+
+
+def test_measurement_plan_formula_term_by_term():
+    """roofline.frac uses the measurement plan's per-round formulas: V = n per
+    round for the sync modes, 12 (vertex) or 20 (edge) bytes per relaxed SSSP
+    edge, 4 per update; async 16 per processed vertex, 12 per edge, 4 per push
+    and per update; 4 bytes less per edge without weights; CC + 8 n per jump."""
+    st = rstats(R=5, Va=40, Ea=300, U=7, P=9)
+    n = INFO["n"]
+    assert bench.survey_bytes(0, 0, st, INFO) == 16 * n * 5 + 12 * 300 + 4 * 7
+    assert bench.survey_bytes(0, 5, st, INFO) == 16 * n * 5 + 12 * 300 + 4 * 7
+    assert bench.survey_bytes(0, 2, st, INFO) == 8 * n * 5 + 20 * 300 + 4 * 7
+    assert bench.survey_bytes(1, 2, st, INFO) == 8 * n * 5 + 16 * 300 + 4 * 7
+    for mode in (1, 3, 6):
+        assert bench.survey_bytes(0, mode, st, INFO) == 16 * 40 + 12 * 300 + 4 * 9 + 4 * 7
+        assert bench.survey_bytes(1, mode, st, INFO) == 16 * 40 + 8 * 300 + 4 * 9 + 4 * 7
+    st_cc = rstats(R=5, Va=40, Ea=300, U=7, jumps=3)
+    assert bench.survey_bytes(2, 0, st_cc, INFO) == 16 * n * 5 + 8 * 300 + 4 * 7 + 8 * n * 3
+
+
+def test_measurement_plan_formula_matches_the_full_sweep_figures():
+    """One all-active round on R-MAT 22 (n = 2^22, m = 16 n, every edge
+    relaxed, no update): 872 MB vertex-sync, 1376 MB edge-sync, the
+    headline figures of the measurement plan."""
+    n, m = 1 << 22, 16 << 22
+    st = rstats(R=1, Ea=m)
+    assert abs(bench.survey_bytes(0, 0, st, {"n": n}) / 1e6 - 872.4) < 0.1
+    assert abs(bench.survey_bytes(0, 2, st, {"n": n}) / 1e6 - 1375.7) < 0.1
+
+
+def test_host_info_states_cores_and_model():
+    h = bench.host_info()
+    assert h["host_cores"] >= 1 and isinstance(h["cpu_model"], str) and h["cpu_model"]
+
+
+def test_compact_serving_keeps_both_arms_per_rate():
+    row = {"rate_per_s": 1000,
+           "batched": {"p50_ms": 1.04, "p99_ms": 9.96, "completed_per_s": 870.0, "all_ok": True},
+           "one_at_a_time": {"p50_ms": 2.0, "p99_ms": 20.0, "completed_per_s": 750.0, "all_ok": True}}
+    c = bench.compact_serving({"resident_graphs": ["a", "b"], "resident_device_gb": 4.0,
+                               "requests_per_rate": 2000, "rates": [row]})
+    r = c["rates"]["1000"]
+    assert r["qps"] == [870.0, 750.0] and r["p50"] == [1.0, 2.0] and r["p99"] == [10.0, 20.0] and r["ok"]

@@ -1,13 +1,14 @@
 """The query server (continuous batching) on the GPU: every request served
-in a mix with others must return exactly what the same query returns alone
-(fg_run), whatever wave it ran in; the HBM budget and the one-at-a-time
-baseline change scheduling only."""
+in a mix with others must return exactly the CPU oracle's result for its
+query (Dijkstra, FIFO BFS, union-find CC), whatever wave it ran in; the HBM
+budget and the one-at-a-time baseline change scheduling only."""
 import numpy as np
 import pytest
 
 import graphgen as gg
+import oracle
 import paper_1903_01665_gb300 as fg
-from tests.gpu_util import graph_handle, run
+from tests.gpu_util import graph_handle
 
 pytestmark = pytest.mark.gpu
 
@@ -61,9 +62,18 @@ def setup():
 
 
 def _alone(graphs, handles, reqs):
+    """The oracle's result of every distinct request (graph, algorithm, source)."""
     want = {}
     for gi, algo, s in set(reqs):
-        want[(gi, algo, s)] = run(handles[gi], graphs[gi].n, algo, s, fg.FG_AUTO)[0]
+        g = graphs[gi]
+        if algo == fg.FG_ALGO_SSSP:
+            rc, res = oracle.sssp(g.n, g.src, g.dst, g.w, s)
+        elif algo == fg.FG_ALGO_BFS:
+            rc, res = oracle.bfs(g.n, g.src, g.dst, s)
+        else:
+            rc, res = oracle.cc(g.n, g.src, g.dst)
+        assert rc == oracle.OK
+        want[(gi, algo, s)] = res
     return want
 
 
@@ -80,8 +90,8 @@ def test_results_in_the_mix_equal_results_alone(setup):
 
 def test_large_graphs_run_alone_and_match(setup):
     """Requests on graphs with at least exclusive_edges edges run alone (wave
-    size 1) on the whole device between the waves; every result is the same
-    as alone."""
+    size 1) on the whole device between the waves; every result is the
+    oracle's."""
     graphs, handles = setup
     reqs = _requests(graphs, 120, seed=8)
     cut = graphs[1].m   # rmat-15 and larger run alone
