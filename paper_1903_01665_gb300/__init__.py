@@ -121,6 +121,9 @@ _SIGNATURES = {
                               ctypes.POINTER(fg_options), ctypes.POINTER(fg_stats)]),
     "fg_sweep": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_int64),
                                 ctypes.POINTER(ctypes.c_float)]),
+    "fg_run_multi": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(_VP), ctypes.POINTER(fg_options), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(fg_stats)]),
     "fg_sssp_csr_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _VP, _VP, _VP, ctypes.c_int32,
                                            _VP, _VP]),
     "fg_run_batch": (ctypes.c_int, [ctypes.POINTER(fg_query), ctypes.c_int32, ctypes.POINTER(fg_batch_options),
@@ -267,6 +270,30 @@ def fg_run(g, algo, src, out, mode, stream=None, max_rounds=0, wait_timeout_ms=0
     stats = fg_stats()
     st = load().fg_run(g, int(algo), int(src), _ptr(out), int(mode), ctypes.byref(opt), ctypes.byref(stats))
     return st, stats
+
+
+FG_MULTI_MAX = 8
+
+
+def fg_run_multi(g, algo, srcs, outs, stream=None, max_rounds=0, wait_timeout_ms=0, blocks_per_sm=0):
+    """k = len(outs) queries of one algorithm on one graph (srcs: k sources,
+    ignored for CC).  Returns (status, [per-query status], fg_stats of the
+    fused sweep)."""
+    k = len(outs)
+    for o in outs:
+        _check_dtype(o, "int32")
+    src_list = [int(x) for x in srcs] if srcs is not None else [0] * k
+    if len(src_list) < k:
+        raise ValueError("one source per output")
+    src_arr = (ctypes.c_int32 * max(k, 1))(*src_list[:k])
+    out_arr = (ctypes.c_void_p * max(k, 1))(*[_ptr(o) for o in outs])
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    opt = fg_options(stream, int(max_rounds), int(wait_timeout_ms), int(blocks_per_sm), 0, None, 0, 0)
+    sts = (ctypes.c_int * max(k, 1))()
+    stats = fg_stats()
+    st = load().fg_run_multi(g, int(algo), int(k), src_arr, out_arr, ctypes.byref(opt), sts, ctypes.byref(stats))
+    return st, list(sts)[:k], stats
 
 
 def fg_sweep(g, mode, cur, nxt, stream=None):

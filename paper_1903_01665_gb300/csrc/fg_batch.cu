@@ -13,7 +13,7 @@
 #include <map>
 #include <vector>
 
-#include "fg_device.cuh"
+#include "fg_multi.cuh"
 
 namespace fg {
 
@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks<MODE>()) batch_kernel(Batch
         if (!team_sync(t, b.bctrl, b.timeout_ns)) return;
         const int qi = __ldcg(&b.team_q[ct.x]);
         if (qi >= b.cls_end[cls]) return;
-        fixpoint_body<ALGO, MODE>(b.params[b.order[qi]], t, ring_used);
+        query_body<ALGO, MODE>(b.params[b.order[qi]], t, ring_used);
         if (!team_sync(t, b.bctrl, b.timeout_ns)) return;
     }
 }

@@ -195,6 +195,27 @@ fg_status fg_run(const fg_graph *g, fg_algo algo, int32_t src, int32_t *out, fg_
     return query(g, algo, src, out, mode, opt, stats);
 }
 
+fg_status fg_run_multi(const fg_graph *g, fg_algo algo, int32_t k, const int32_t *srcs, int32_t *const *outs,
+                       const fg_options *opt, fg_status *status_out, fg_stats *stats) {
+    if (!g) return fail(FG_ERR_INVALID_ARG, "graph is NULL");
+    if (algo < FG_ALGO_SSSP || algo > FG_ALGO_CC) return fail(FG_ERR_INVALID_ARG, "invalid algorithm");
+    if (k < 1 || k > FG_MULTI_MAX) return fail(FG_ERR_INVALID_ARG, "k must be in [1, FG_MULTI_MAX = 8]");
+    if (!outs || (algo != FG_ALGO_CC && !srcs)) return fail(FG_ERR_INVALID_ARG, "NULL argument");
+    for (int32_t j = 0; j < k; j++) {
+        if (!outs[j]) return fail(FG_ERR_INVALID_ARG, "output buffer " + std::to_string(j) + " is NULL");
+        if (algo != FG_ALGO_CC && (srcs[j] < 0 || srcs[j] >= g->info.n))
+            return fail(FG_ERR_INVALID_ARG, "source " + std::to_string(j) + " outside [0, n)");
+    }
+    if (opt && (opt->max_rounds < 0 || opt->wait_timeout_ms < 0 || opt->blocks_per_sm < 0 || opt->delta < 0))
+        return fail(FG_ERR_INVALID_ARG, "negative option");
+    if (!ensure_device(nullptr)) return fail(FG_ERR_CUDA, "no CUDA device");
+    if (algo == FG_ALGO_CC) {   // the symmetrised view of a FG_GRAPH_LAZY graph
+        fg_status vs = ensure_views(g, kCC, -1);
+        if (vs != FG_OK) return vs;
+    }
+    return run_multi(g, (Algo)algo, k, srcs, outs, opt, status_out, stats);
+}
+
 fg_status fg_sweep(const fg_graph *g, fg_mode mode, const int32_t *cur, int32_t *next, void *stream,
                    int64_t *updates, float *kernel_ms) {
     if (!g || !cur || !next) return fail(FG_ERR_INVALID_ARG, "NULL argument");

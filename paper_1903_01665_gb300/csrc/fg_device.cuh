@@ -1719,12 +1719,17 @@ __device__ __forceinline__ void stream_edges_async(const Team &t, const View &g,
 #ifndef FG_EDGE_SYNC_MIN_BLOCKS
 #define FG_EDGE_SYNC_MIN_BLOCKS 4
 #endif
+// the multi-source sweep keeps two 8-value rows per edge in flight (64 registers)
+#ifndef FG_MULTI_MIN_BLOCKS
+#define FG_MULTI_MIN_BLOCKS 4
+#endif
 template <int MODE>
 constexpr int min_blocks() {
     return MODE == kVertexSync ? FG_SYNC_MIN_BLOCKS
          : MODE == kEdgeSync   ? FG_EDGE_SYNC_MIN_BLOCKS
          : MODE == kPull       ? FG_PULL_MIN_BLOCKS
          : MODE == kBucket     ? FG_BUCKET_MIN_BLOCKS
+         : MODE == kMulti      ? FG_MULTI_MIN_BLOCKS
                                : FG_ASYNC_MIN_BLOCKS;
 }
 

@@ -1,9 +1,10 @@
 // Single-query entry of the fixpoint sweep: one persistent cooperative
-// kernel per query, the whole grid as one team; plus the all-active sweep
-// used for roofline measurements and the overflow test.
+// kernel per query, the whole grid as one team; the multi-source sweep (up
+// to 8 queries on one graph in one launch); plus the all-active sweep used
+// for roofline measurements and the overflow test.
 #include <algorithm>
 
-#include "fg_device.cuh"
+#include "fg_multi.cuh"
 
 namespace fg {
 
@@ -14,7 +15,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks<MODE>()) fixpoint_kernel(Pa
     const Team t{(int)blockIdx.x, (int)gridDim.x, &p.ctrl->bar_count};
     uint32_t ring_used;
     fixpoint_prologue<ALGO, MODE>(ring_used);
-    fixpoint_body<ALGO, MODE>(p, t, ring_used);
+    query_body<ALGO, MODE>(p, t, ring_used);
 }
 
 // One all-active sweep: vertex variant over the buckets, edge variant over
@@ -63,6 +64,7 @@ KernelFn kernel_for(Algo algo, Mode mode) {
     FG_K(kCC, kVertexSync) FG_K(kCC, kVertexAsync) FG_K(kCC, kEdgeSync) FG_K(kCC, kEdgeAsync)
     FG_K(kSSSP, kPull) FG_K(kBFS, kPull) FG_K(kCC, kPull)
     FG_K(kSSSP, kBucket) FG_K(kBFS, kBucket) FG_K(kCC, kBucket)
+    FG_K(kSSSP, kMulti) FG_K(kBFS, kMulti)
 #undef FG_K
     return nullptr;
 }
@@ -115,6 +117,8 @@ int64_t wl_cap_of(const View &g, Mode mode, int k) {
 // aligned.
 size_t query_workspace_bytes(const View &g, Algo algo, Mode mode) {
     const int32_t n = g.n;
+    if (mode == kMulti)   // control block, rows of 8 values, stamps
+        return Workspace::need(1, sizeof(Ctrl)) + Workspace::need((int64_t)n * 8, 4) + Workspace::need(n, 4);
     const bool sync = (mode == kVertexSync || mode == kEdgeSync || mode == kPull);
     size_t need = Workspace::need(1, sizeof(Ctrl)) + Workspace::need(n, 4);
     if (sync && algo != kBFS) need += 3 * Workspace::need(n, 4);
@@ -139,6 +143,11 @@ void carve_query_workspace(char *base, const View &g, Algo algo, Mode mode, Para
     const int64_t nwt = (g.m + kWTile - 1) / kWTile;
     p.g = g;
     p.ctrl = ws.take<Ctrl>(1);
+    if (mode == kMulti) {
+        p.A = ws.take<int32_t>((int64_t)n * 8);
+        p.S0 = ws.take<int32_t>(n);
+        return;
+    }
     p.A = ws.take<int32_t>(n);
     if (sync && algo != kBFS) {
         p.B = ws.take<int32_t>(n);
@@ -313,6 +322,165 @@ fg_status run_query(const fg_graph *G, Algo algo, Mode mode, int32_t source, int
         stats->kernel_ms = ms;
     }
     if (status != FG_OK) return fail(status, msg);
+    return FG_OK;
+}
+
+// Up to kMsMax queries of one algorithm on one graph.  SSSP and BFS run as
+// one multi-source sweep (one launch); CC has no source, so it runs once and
+// its result is copied to every output.  Per-slot status: only an overflow
+// (SSSP) can differ between slots.
+fg_status run_multi(const fg_graph *G, Algo algo, int32_t k, const int32_t *srcs, int32_t *const *outs,
+                    const fg_options *opt, fg_status *status_out, fg_stats *stats) {
+    cudaStream_t st = opt && opt->stream ? (cudaStream_t)opt->stream : (cudaStream_t)0;
+    auto all = [&](fg_status x) {
+        if (status_out)
+            for (int j = 0; j < k; j++) status_out[j] = x;
+        return x;
+    };
+    if (algo == kCC) {
+        fg_mode m;
+        fg_status s = fg_select_mode(G, FG_ALGO_CC, &m);
+        if (s == FG_OK) s = run_query(G, kCC, (Mode)m, 0, outs[0], opt, stats);
+        if (s != FG_OK) return all(s);
+        cudaError_t e = cudaSuccess;
+        for (int j = 1; j < k && e == cudaSuccess; j++)
+            e = cudaMemcpyAsync(outs[j], outs[0], (size_t)G->s.n * sizeof(int32_t), cudaMemcpyDefault, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return all(cuda_fail(e, "result copies"));
+        return all(FG_OK);
+    }
+    const View &g = G->g;
+    const int32_t n = g.n;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != G->device) return all(fail(FG_ERR_INVALID_ARG, "the current device is not the graph's device"));
+    DeviceProps dp = device_props(dev);
+    if (!dp.coop) return all(fail(FG_ERR_CUDA, "device does not support cooperative launches"));
+    KernelFn fn = kernel_for(algo, kMulti);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, kBlock, 0);
+    if (e != cudaSuccess) return all(cuda_fail(e, "occupancy query"));
+    if (opt && opt->blocks_per_sm > 0) per_sm = std::min(per_sm, (int)opt->blocks_per_sm);
+    const int grid = std::min(per_sm * dp.sms, kMaxGrid);
+    if (grid < 1) return all(fail(FG_ERR_CUDA, "kernel does not fit on an SM"));
+
+    // one allocation: the query state, then device staging of host outputs
+    bool on_dev[kMsMax] = {};
+    int n_host = 0;
+    for (int j = 0; j < k; j++) {
+        on_dev[j] = is_device_pointer(outs[j]);
+        n_host += !on_dev[j];
+    }
+    const size_t qbytes = query_workspace_bytes(g, algo, kMulti);
+    const size_t sbytes = Workspace::need(n, 4);
+    char *base = nullptr;
+    e = cudaMallocAsync((void **)&base, qbytes + (size_t)n_host * sbytes, st);
+    if (e != cudaSuccess) return all(cuda_fail(e, "multi-source workspace"));
+    Params p;
+    carve_query_workspace(base, g, algo, kMulti, p);
+    p.ms_k = k;
+    int32_t *dout[kMsMax] = {};
+    for (int j = 0, h = 0; j < k; j++) {
+        p.ms_src[j] = srcs[j];
+        dout[j] = on_dev[j] ? outs[j] : reinterpret_cast<int32_t *>(base + qbytes + (size_t)(h++) * sbytes);
+        p.ms_out[j] = dout[j];
+    }
+    p.max_rounds = (opt && opt->max_rounds > 0) ? opt->max_rounds : (n > INT32_MAX - 2 ? INT32_MAX : n + 2);
+    const int tmo = (opt && opt->wait_timeout_ms > 0) ? opt->wait_timeout_ms : 1000;
+    p.timeout_ns = (unsigned long long)tmo * 1000000ull;
+
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    fg_status status = FG_OK;
+    std::string msg;
+    Ctrl hc{};
+    e = cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev0, st);
+    if (e == cudaSuccess) {
+        void *args[] = {&p};
+        e = cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(kBlock), args, 0, st);
+        if (e == cudaSuccess) count_launch();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev1, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        status = (e == cudaErrorMemoryAllocation) ? FG_ERR_OUT_OF_MEMORY : FG_ERR_CUDA;
+        msg = std::string("multi-source kernel: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+    } else if (hc.status & kStTimeout) {
+        status = FG_ERR_TIMEOUT;
+        msg = "a device-side wait exceeded the timeout";
+    } else if (hc.status & kStRoundCap) {
+        status = FG_ERR_TIMEOUT;
+        msg = "round cap reached before the fixpoint";
+    } else if (!hc.done) {
+        status = FG_ERR_CUDA;
+        msg = "internal error: the multi-source sweep ended without a fixpoint";
+    }
+    fg_status slot[kMsMax];
+    for (int j = 0; j < kMsMax; j++) slot[j] = status;
+    if (status == FG_OK && (hc.status & kStOverflow)) {
+        // which sources overflowed; the kernel wrote no output, so write the others'
+        int *flag = reinterpret_cast<int *>(p.ctrl);
+        int hf = 0;
+        e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+        if (e == cudaSuccess) {
+            ms_overflow_check_kernel<<<dp.sms * 8, kBlock, 0, st>>>(g, p.A, k, flag);
+            count_launch();
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        MsOuts ok_outs{};
+        for (int j = 0; j < k; j++) {
+            if ((hf >> j) & 1) slot[j] = FG_ERR_OVERFLOW;
+            else ok_outs.p[j] = dout[j];
+        }
+        if (e == cudaSuccess && hf != (1 << k) - 1) {
+            ms_output_kernel<<<dp.sms * 8, kBlock, 0, st>>>(p.A, n, k, ok_outs);
+            count_launch();
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) {
+            for (int j = 0; j < k; j++) slot[j] = FG_ERR_CUDA;
+            msg = std::string("overflow check: ") + cudaGetErrorString(e);
+        } else if (hf) {
+            msg = "a finite shortest distance is >= INT32_MAX";
+        }
+    }
+    for (int j = 0; j < k && e == cudaSuccess; j++)
+        if (slot[j] == FG_OK && !on_dev[j])
+            e = cudaMemcpyAsync(outs[j], dout[j], (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        for (int j = 0; j < k; j++) slot[j] = FG_ERR_CUDA;
+        msg = std::string("result copy: ") + cudaGetErrorString(e);
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    cudaFreeAsync(base, st);
+    if (stats) {
+        *stats = fg_stats{};
+        stats->mode = -1;
+        stats->rounds = hc.rounds;
+        stats->grid_blocks = grid;
+        stats->vertices_processed = (int64_t)hc.st_vertices;
+        stats->edges_relaxed = (int64_t)hc.st_edges;
+        stats->updates = (int64_t)hc.st_updates;
+        stats->scanned = (int64_t)hc.st_scanned;
+        stats->barriers = hc.barriers;
+        stats->kernel_ms = ms;
+    }
+    fg_status first = FG_OK;
+    for (int j = 0; j < k; j++) {
+        if (status_out) status_out[j] = slot[j];
+        if (first == FG_OK) first = slot[j];
+    }
+    if (first != FG_OK) return fail(first, msg);
     return FG_OK;
 }
 

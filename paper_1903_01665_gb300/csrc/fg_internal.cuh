@@ -92,7 +92,10 @@ struct Ctrl {
 };
 
 enum Algo { kSSSP = 0, kBFS = 1, kCC = 2 };
-enum Mode { kVertexSync = 0, kVertexAsync = 1, kEdgeSync = 2, kEdgeAsync = 3, kPull = 5, kBucket = 6 };
+// kMulti: the multi-source sweep (up to 8 SSSP or BFS sources on one graph in
+// one fixpoint); not a public fg_mode, it is reached through fg_run_multi
+// and the fusion of same-graph queries in batches and the server
+enum Mode { kVertexSync = 0, kVertexAsync = 1, kEdgeSync = 2, kEdgeAsync = 3, kPull = 5, kBucket = 6, kMulti = 7 };
 
 // worklist classes (vertex-async): low, mid, high chunks; edge-async uses class 0 only
 enum { kWlLow = 0, kWlMid = 1, kWlHigh = 2 };
@@ -118,9 +121,17 @@ struct Params {
     unsigned long long timeout_ns = 0;
     int32_t inject_missing_arrival = 0;
     int32_t *out = nullptr;                // batch: device output the team copies the result to
+    int32_t ms_k = 0;                      // multi-source: sources in the sweep (A = rows of 8 values, S0 = stamps)
+    int32_t ms_src[8] = {};                // multi-source: source of each slot
+    int32_t *ms_out[8] = {};               // multi-source: device output of each slot (null: not written)
     unsigned long long *trace = nullptr;   // optional per-barrier timestamps (CTA 0)
     int32_t trace_cap = 0;
     Ctrl *ctrl = nullptr;
+};
+
+// multi-source: one output pointer per slot, passed by value to a kernel
+struct MsOuts {
+    int32_t *p[8];
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -376,6 +387,8 @@ fg_status ensure_src(const fg_graph *g);
 
 // queries (fg_fixpoint.cu)
 int32_t default_delta(const fg_graph *G);
+fg_status run_multi(const fg_graph *g, Algo algo, int32_t k, const int32_t *srcs, int32_t *const *outs,
+                    const fg_options *opt, fg_status *status_out, fg_stats *stats);
 fg_status run_query(const fg_graph *g, Algo algo, Mode mode, int32_t source, int32_t *out,
                     const fg_options *opt, fg_stats *stats);
 fg_status run_sweep(const fg_graph *g, Mode mode, const int32_t *cur, int32_t *next,
