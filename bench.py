@@ -348,6 +348,44 @@ def run_extra_modes(r, per_kernel: dict, modes, reps: int = 2) -> dict:
     return out
 
 
+def run_fused_compare(r, per_kernel: dict, reps: int = 3) -> dict:
+    """The multi-source sweep on the step's workload: the 8 seeded sources of
+    SSSP (and of BFS) in one fg_run_multi sweep against the 8 queries of the
+    fastest paper mode measured in the timed step (device time), with every
+    fused output compared to a plain query's."""
+    fg, torch, g = r.fg, r.torch, r.g
+    st, h = fg.fg_graph_create_coo(g.n, r.d_src, r.d_dst, r.d_w)
+    fg.check(st)
+    out = {}
+    try:
+        srcs = list(r.srcs)
+        outs = [torch.empty(g.n, dtype=torch.int32, device=r.d_src.device) for _ in srcs]
+        for algo in (0, 1):
+            ms = []
+            for rep in range(reps + 1):
+                st, sts, stats = fg.fg_run_multi(h, algo, srcs, outs)
+                fg.check(st)
+                if rep:
+                    ms.append(stats.kernel_ms)
+            exact = True
+            for s_, o in zip(srcs, outs):
+                fg.check(fg.fg_run(h, algo, s_, r.outs[0], fg.FG_VERTEX_SYNC)[0])
+                exact &= bool(torch.equal(o, r.outs[0]))
+            cand = [k for k in per_kernel if k[0] == algo]
+            if not cand:
+                continue
+            best = min(cand, key=lambda k: per_kernel[k]["ms"] / per_kernel[k]["launches"])
+            sep = per_kernel[best]["ms"] / per_kernel[best]["launches"] * len(srcs)
+            fused = float(np.median(ms))
+            out[ALGO_NAMES[algo]] = {"fused_ms": round(fused, 3), "separate_ms": round(sep, 3),
+                                     "separate_mode": MODE_NAMES[best[1]], "speedup": round(sep / fused, 3),
+                                     "rounds": stats.rounds, "bit_exact": exact}
+        out["sources"] = len(srcs)
+    finally:
+        fg.check(fg.fg_graph_destroy(h))
+    return out
+
+
 def run_grid_bucket(device, reps: int = 2) -> dict:
     """The bucketed SSSP (near-far) where it is meant to help: the 4096^2
     road-like grid, SSSP from two seeded sources, against the paper's
@@ -414,8 +452,10 @@ def run_batched(device, reps: int = 3) -> dict:
                 tune[(gi, algo)] = best
         outs1 = [torch.empty(graphs[gi].n, dtype=torch.int32, device=device) for gi, _, _ in queries]
         outs2 = [torch.empty(graphs[gi].n, dtype=torch.int32, device=device) for gi, _, _ in queries]
+        outs3 = [torch.empty(graphs[gi].n, dtype=torch.int32, device=device) for gi, _, _ in queries]
         batch = [(handles[gi], algo, s, outs2[i], fg.FG_AUTO) for i, (gi, algo, s) in enumerate(queries)]
-        t_one, t_batch = [], []
+        fused = [(handles[gi], algo, s, outs3[i], fg.FG_AUTO) for i, (gi, algo, s) in enumerate(queries)]
+        t_one, t_batch, t_fused = [], [], []
         for _ in range(reps + 1):          # the first repetition is a warm-up
             torch.cuda.synchronize(device)
             t0 = time.perf_counter()
@@ -429,22 +469,32 @@ def run_batched(device, reps: int = 3) -> dict:
             fg.check(st)
             torch.cuda.synchronize(device)
             t_batch.append(time.perf_counter() - t0)
+            t0 = time.perf_counter()
+            st, sts, _, fbst = fg.fg_run_batch(fused, use_cuda_graph=True, fuse_same_graph=True)
+            fg.check(st)
+            torch.cuda.synchronize(device)
+            t_fused.append(time.perf_counter() - t0)
         exact = all(torch.equal(a, b) for a, b in zip(outs1, outs2))
+        exact_fused = all(torch.equal(a, b) for a, b in zip(outs1, outs3))
         edges = 0
         for i, (gi, algo, s) in enumerate(queries):
             edges += int(degs[gi][outs1[i] != fg.FG_INF].sum().item())
         one = statistics.median(t_one[1:])
         bat = statistics.median(t_batch[1:])
+        fus = statistics.median(t_fused[1:])
         modes = {}
         for (gi, algo), m in tune.items():
             key = f"{ALGO_NAMES[algo]}/{MODE_NAMES[m]}"
             modes[key] = modes.get(key, 0) + 1
         return {"queries": len(queries), "graphs": len(graphs),
-                "one_at_a_time_qps": round(len(queries) / one, 1), "batched_qps": round(len(queries) / bat, 1),
-                "speedup": round(one / bat, 3), "one_at_a_time_gteps": round(edges / one / 1e9, 3),
-                "batched_gteps": round(edges / bat / 1e9, 3), "bit_exact": exact,
-                "batch_kernel_ms": round(bst.kernel_ms, 3), "launches": bst.launches, "teams": bst.teams,
-                "ctas": bst.ctas, "autotuned_modes": modes,
+                "one_at_a_time_qps": round(len(queries) / one, 1), "batched_qps": round(len(queries) / fus, 1),
+                "speedup": round(one / fus, 3), "bit_exact": exact and exact_fused,
+                "unfused_qps": round(len(queries) / bat, 1), "unfused_speedup": round(one / bat, 3),
+                "one_at_a_time_gteps": round(edges / one / 1e9, 3), "batched_gteps": round(edges / fus / 1e9, 3),
+                "batch_kernel_ms": round(fbst.kernel_ms, 3), "launches": fbst.launches, "teams": fbst.teams,
+                "ctas": fbst.ctas, "unfused_launches": bst.launches, "autotuned_modes": modes,
+                "fusion": "queries on one graph share work: SSSP/BFS as multi-source sweeps of up to 8 "
+                          "sources, CC once (fuse_same_graph); unfused = one fixpoint per query",
                 "timing": "wall clock around each run, median of %d, after one warm-up" % reps}
     finally:
         for h in handles:
@@ -701,6 +751,7 @@ def run_ours(args):
                "d2h_bytes_per_step": 4 * r.g.n * len(r.queries), "steps": k2, "warmup": 1}
 
     sweep = None if args.no_sweep else run_sweep_roofline(r, peaks[0])
+    fused = None if args.no_fused or len(r.srcs) < 2 else run_fused_compare(r, per_kernel)
     extra = None if args.no_extra else run_extra_modes(r, per_kernel, [fg.FG_PULL, fg.FG_BUCKET])
 
     cpu = None
@@ -741,12 +792,16 @@ def run_ours(args):
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk,
                 "relaxations_gps": round(relax_all / sec / 1e9, 3)}
+        if fused is not None:
+            line["fused"] = {k: ({kk: v[kk] for kk in ("fused_ms", "separate_ms", "speedup", "bit_exact")}
+                                 if isinstance(v, dict) else v) for k, v in fused.items()}
         if batched is not None:
             line["batched"] = {k: batched[k] for k in ("batched_qps", "one_at_a_time_qps", "speedup", "bit_exact",
-                                                       "launches") if k in batched}
+                                                       "launches", "unfused_speedup") if k in batched}
         if serving is not None:
             line["serving"] = compact_serving(serving)
-        detail = {"per_kernel": per_mode, "sweep_roofline": sweep, "extra_modes": extra, "grid_bucket": grid_bucket,
+        detail = {"per_kernel": per_mode, "sweep_roofline": sweep, "fused": fused, "extra_modes": extra,
+                  "grid_bucket": grid_bucket,
                   "batched": batched, "serving": serving,
                   "relaxations_per_step": relax_all // max(args.steps * ws, 1)}
         if args.detail:
@@ -896,6 +951,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sweep", action="store_true", help="skip the all-active sweep roofline test")
     ap.add_argument("--no-extra", action="store_true", help="skip the pull/bucket comparison on the workload")
+    ap.add_argument("--no-fused", action="store_true", help="skip the multi-source sweep comparison")
     ap.add_argument("--no-grid-bucket", action="store_true", help="skip the bucketed-SSSP grid comparison")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload comparison")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving comparison")

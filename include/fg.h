@@ -365,6 +365,12 @@ typedef struct {
     void *stream;               /* cudaStream_t; NULL = legacy default stream */
     int32_t use_cuda_graph;     /* nonzero: capture the launches in a CUDA graph, launch it */
     int32_t wait_timeout_ms;    /* bound on any device-side wait; 0 = 1000 ms */
+    int32_t fuse_same_graph;    /* nonzero: queries on the same graph share work -- SSSP and BFS
+                                   queries run as multi-source sweeps of up to FG_MULTI_MAX
+                                   sources (fg_run_multi's sweep), CC queries as one computation
+                                   copied to every output (a lone query runs in its own mode);
+                                   results are identical, stats_out then describe the shared
+                                   sweep (mode -1 for a multi-source one) */
 } fg_batch_options;
 
 typedef struct {
@@ -393,8 +399,11 @@ fg_status fg_run_batch(const fg_query *queries, int32_t nq, const fg_batch_optio
  * and later ones of the same kind (graph, algorithm, mode), up to max_wave,
  * are launched together on the slot's stream -- so waves overlap on the
  * device and new requests start as soon as a slot and memory free up.
- * Requests on large graphs (exclusive_edges) run alone on the whole device.  one_at_a_time = 1 serves the queue strictly in order, one
- * request at a time, with the plain per-query kernel (the baseline).
+ * Requests on large graphs (exclusive_edges) run on the whole device without
+ * other graphs' requests (fused with the pending requests of their graph
+ * and algorithm unless no_fusion).  one_at_a_time = 1 serves the queue
+ * strictly in order, one request at a time, with the plain per-query kernel
+ * (the baseline).
  * A request's work is ordered after all work enqueued on the legacy default
  * stream before it was submitted (so outputs prepared there are safe); it
  * runs on the server's own streams otherwise.  Graphs must stay alive and
@@ -416,6 +425,16 @@ typedef struct {
                                    kernel: such a query already fills the GPU, and sharing
                                    SMs with other queries costs it L1 hits; 0 = 2^25,
                                    < 0 = never */
+    int32_t no_fusion;          /* 0 (default): requests on the same graph share work -- a
+                                   large-graph request runs together with the later pending
+                                   requests of its graph and algorithm (up to FG_MULTI_MAX
+                                   SSSP or BFS requests as one multi-source sweep, every
+                                   pending CC request as one computation copied to each
+                                   output), and waves on smaller graphs are fused the same way
+                                   (fg_batch_options.fuse_same_graph); results are identical
+                                   and fg_completion.wave_size counts the requests served
+                                   together.  Nonzero: every request runs its own fixpoint in
+                                   its own mode */
 } fg_server_options;
 
 typedef struct {

@@ -80,7 +80,7 @@ class fg_query(ctypes.Structure):
 
 class fg_batch_options(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("use_cuda_graph", ctypes.c_int32),
-                ("wait_timeout_ms", ctypes.c_int32)]
+                ("wait_timeout_ms", ctypes.c_int32), ("fuse_same_graph", ctypes.c_int32)]
 
 
 class fg_batch_stats(ctypes.Structure):
@@ -94,7 +94,8 @@ class fg_batch_stats(ctypes.Structure):
 class fg_server_options(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
                 ("max_wave", ctypes.c_int32), ("one_at_a_time", ctypes.c_int32),
-                ("wait_timeout_ms", ctypes.c_int32), ("exclusive_edges", ctypes.c_int64)]
+                ("wait_timeout_ms", ctypes.c_int32), ("exclusive_edges", ctypes.c_int64),
+                ("no_fusion", ctypes.c_int32)]
 
 
 class fg_completion(ctypes.Structure):
@@ -306,7 +307,7 @@ def fg_sweep(g, mode, cur, nxt, stream=None):
     return st, upd.value, ms.value
 
 
-def fg_run_batch(queries, stream=None, use_cuda_graph=False, wait_timeout_ms=0):
+def fg_run_batch(queries, stream=None, use_cuda_graph=False, wait_timeout_ms=0, fuse_same_graph=False):
     """queries: list of (graph, algo, src, out_array, mode).  Returns
     (status, [per-query status], [per-query fg_stats], fg_batch_stats)."""
     nq = len(queries)
@@ -316,7 +317,7 @@ def fg_run_batch(queries, stream=None, use_cuda_graph=False, wait_timeout_ms=0):
         arr[i] = fg_query(g, int(algo), int(src), _ptr(out), int(mode))
     if stream is not None and hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
-    opt = fg_batch_options(stream, 1 if use_cuda_graph else 0, int(wait_timeout_ms))
+    opt = fg_batch_options(stream, 1 if use_cuda_graph else 0, int(wait_timeout_ms), 1 if fuse_same_graph else 0)
     sts = (ctypes.c_int * nq)()
     stats = (fg_stats * nq)()
     bst = fg_batch_stats()
@@ -333,10 +334,10 @@ def fg_autotune(g, algo, src=0):
 
 
 def fg_server_create(hbm_budget_bytes=0, max_inflight=0, max_wave=0, one_at_a_time=False, wait_timeout_ms=0,
-                     exclusive_edges=0):
+                     exclusive_edges=0, no_fusion=False):
     """Returns (status, server handle)."""
     o = fg_server_options(int(hbm_budget_bytes), int(max_inflight), int(max_wave), 1 if one_at_a_time else 0,
-                          int(wait_timeout_ms), int(exclusive_edges))
+                          int(wait_timeout_ms), int(exclusive_edges), 1 if no_fusion else 0)
     h = _VP()
     st = load().fg_server_create(ctypes.byref(o), ctypes.byref(h))
     return st, (h.value if st == FG_OK else None)

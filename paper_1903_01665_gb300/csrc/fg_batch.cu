@@ -3,10 +3,13 @@
 // barrier-free kernels on separate streams (Sec. 3.2) and of its
 // independent parallel sections (Sec. 3.4).
 //
+// The queries are first grouped into units: each query alone, or -- with
+// fusion -- the queries on one graph merged (SSSP/BFS into multi-source
+// sweeps of up to 8 sources, CC into one computation for all its outputs).
 // Each launch is a persistent cooperative kernel whose CTAs are split into
-// teams; every team pulls queries from the queue of its size class and runs
+// teams; every team pulls units from the queue of its size class and runs
 // the whole fixpoint of each with a team-local barrier (a one-CTA team needs
-// only __syncthreads).  The team size of a query comes from its edge count,
+// only __syncthreads).  The team size of a unit comes from its edge count,
 // the CTA budget of each kind and class from its estimated work.  Kinds run
 // concurrently on forked streams, optionally captured in one CUDA graph.
 #include <algorithm>
@@ -26,8 +29,8 @@ struct BatchArgs {
     int *cls_next;            // per class: next queue slot
     const int *cls_begin;     // per class: queue range in `order`
     const int *cls_end;
-    const int *order;         // query indices, by class, largest work first
-    const Params *params;     // per query of the batch
+    const int *order;         // unit indices, by class, largest work first
+    const Params *params;     // per unit of the batch
     Ctrl *bctrl;              // status of the queue barriers
     unsigned long long timeout_ns;
 };
@@ -72,6 +75,8 @@ BatchFn batch_kernel_for(int kind) {
         case kSSSP * 8 + kBucket: return batch_kernel<kSSSP, kBucket>;
         case kBFS * 8 + kBucket: return batch_kernel<kBFS, kBucket>;
         case kCC * 8 + kBucket: return batch_kernel<kCC, kBucket>;
+        case kSSSP * 8 + kMulti: return batch_kernel<kSSSP, kMulti>;
+        case kBFS * 8 + kMulti: return batch_kernel<kBFS, kMulti>;
     }
     return nullptr;
 }
@@ -88,11 +93,20 @@ double work_of(int algo, const View &v) {
     return (double)v.m * (algo == kSSSP ? 4.0 : 1.0) + (double)v.n;
 }
 
+// relative work of a unit: a fused sweep of k sources costs a fraction of k
+// separate sweeps (R-MAT 22, 8 sources: SSSP about 2x one query, BFS about 4x)
+double unit_work(const BatchUnit &u, const View &v) {
+    const double one = work_of(u.algo, v);
+    if (u.mode != kMulti) return one;
+    const double k = (double)u.q.size();
+    return one * (1.0 + (k - 1.0) * (u.algo == kSSSP ? 0.15 : 0.45));
+}
+
 struct KindPlan {
     int kind = 0;
-    std::vector<int> queries;                 // indices into the batch
+    std::vector<int> queries;                 // units of the batch of this kind
     std::vector<int> class_size;              // team size per class
-    std::vector<std::vector<int>> class_q;    // queries per class, largest work first
+    std::vector<std::vector<int>> class_q;    // units per class, largest work first
     std::vector<int> class_teams;             // teams per class
     double work = 0;
     int ctas = 0;
@@ -100,13 +114,72 @@ struct KindPlan {
 
 }  // namespace
 
+// Groups the batch's queries into units.  Without fusion every query is a
+// unit of its own.  With fusion, queries on the same graph are merged: CC
+// queries into one unit (CC has no source: one result for every output),
+// SSSP and BFS queries into multi-source sweeps of up to 8 sources (a lone
+// query stays a plain unit in its own mode).  Units keep the order of their
+// first query.
+static std::vector<BatchUnit> plan_units(const fg_query *qs, int32_t nq, const std::vector<Mode> &mode,
+                                         bool fuse) {
+    std::vector<BatchUnit> units;
+    if (!fuse) {
+        for (int i = 0; i < nq; i++) {
+            BatchUnit u;
+            u.g = qs[i].g;
+            u.algo = (Algo)qs[i].algo;
+            u.mode = mode[i];
+            u.q.push_back(i);
+            units.push_back(u);
+        }
+        return units;
+    }
+    std::map<std::pair<const fg_graph *, int>, std::vector<int>> groups;
+    std::vector<std::pair<const fg_graph *, int>> order;
+    for (int i = 0; i < nq; i++) {
+        auto key = std::make_pair(qs[i].g, (int)qs[i].algo);
+        auto it = groups.find(key);
+        if (it == groups.end()) {
+            order.push_back(key);
+            groups[key].push_back(i);
+        } else {
+            it->second.push_back(i);
+        }
+    }
+    for (auto &key : order) {
+        const std::vector<int> &qi = groups[key];
+        const Algo algo = (Algo)key.second;
+        if (algo == kCC || qi.size() == 1) {
+            BatchUnit u;
+            u.g = key.first;
+            u.algo = algo;
+            u.mode = mode[qi[0]];
+            u.q = qi;
+            units.push_back(u);
+            continue;
+        }
+        for (size_t b = 0; b < qi.size(); b += 8) {
+            BatchUnit u;
+            u.g = key.first;
+            u.algo = algo;
+            const size_t e = std::min(qi.size(), b + 8);
+            u.q.assign(qi.begin() + (long)b, qi.begin() + (long)e);
+            u.mode = u.q.size() >= 2 ? kMulti : mode[u.q[0]];
+            units.push_back(u);
+        }
+    }
+    return units;
+}
+
 // Plans, allocates and enqueues a batch on opt->stream; nothing waits.  The
 // results reach device outputs directly; host outputs go to device staging
 // and, if enqueue_host_copies, are copied back on the stream (their contents
-// are then unspecified for a failed query).  cta_fraction scales the CTA
-// budget so that several batches can be resident at once.
+// are then unspecified for a failed query), as are the copies of a shared
+// CC result to its other outputs.  cta_fraction scales the CTA budget so
+// that several batches can be resident at once.  fuse merges queries on the
+// same graph (plan_units).
 fg_status batch_launch(const fg_query *qs, int32_t nq, const fg_batch_options *opt, double cta_fraction,
-                       bool enqueue_host_copies, Ctrl *h_ctrls_pinned, BatchJob &job) {
+                       bool enqueue_host_copies, bool fuse, Ctrl *h_ctrls_pinned, BatchJob &job) {
     job.nq = nq;
     job.qs.assign(qs, qs + nq);
     int dev = 0;
@@ -119,13 +192,8 @@ fg_status batch_launch(const fg_query *qs, int32_t nq, const fg_batch_options *o
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     if (!coop) return fail(FG_ERR_CUDA, "device does not support cooperative launches");
 
-    // ---- resolve modes, group by kind, plan teams
-    std::vector<Mode> &mode = job.mode;
-    std::vector<const View *> &view = job.view;
-    mode.resize(nq);
-    view.resize(nq);
-    std::map<int, KindPlan> kinds;
-    double total_work = 0;
+    // ---- resolve modes, form units, group them by kind, plan teams
+    std::vector<Mode> mode(nq);
     for (int i = 0; i < nq; i++) {
         const fg_query &q = qs[i];
         fg_mode m = (fg_mode)q.mode;
@@ -136,19 +204,35 @@ fg_status batch_launch(const fg_query *qs, int32_t nq, const fg_batch_options *o
         mode[i] = (Mode)m;
         fg_status vs = ensure_views(q.g, (Algo)q.algo, (int)m);   // lazily built parts, transposed view
         if (vs != FG_OK) return vs;
-        view[i] = (q.algo == FG_ALGO_CC) ? &q.g->s : &q.g->g;
-        KindPlan &kp = kinds[q.algo * 8 + (int)m];
-        kp.kind = q.algo * 8 + (int)m;
-        kp.queries.push_back(i);
-        double w = work_of(q.algo, *view[i]);
+    }
+    job.units = plan_units(qs, nq, mode, fuse);
+    const int nu = (int)job.units.size();
+    std::vector<BatchUnit> &units = job.units;
+    std::vector<const View *> &view = job.view;
+    view.resize(nu);
+    job.qmode.assign(nq, kVertexSync);
+    job.qunit.assign(nq, 0);
+    std::map<int, KindPlan> kinds;
+    double total_work = 0;
+    for (int u = 0; u < nu; u++) {
+        const BatchUnit &un = units[u];
+        view[u] = (un.algo == kCC) ? &un.g->s : &un.g->g;
+        for (int i : un.q) {
+            job.qmode[i] = un.mode;
+            job.qunit[i] = u;
+        }
+        KindPlan &kp = kinds[un.algo * 8 + (int)un.mode];
+        kp.kind = un.algo * 8 + (int)un.mode;
+        kp.queries.push_back(u);
+        const double w = unit_work(un, *view[u]);
         kp.work += w;
         total_work += w;
     }
     for (auto &kv : kinds) {
         KindPlan &kp = kv.second;
         std::map<int, std::vector<int>> by_size;
-        // a kind with few queries (at most 8) gives each a larger team (a lone
-        // query the whole budget); otherwise the size follows its edge count
+        // a kind with few units (at most 8) gives each a larger team (a lone
+        // unit the whole budget); otherwise the size follows its edge count
         int per_sm0 = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm0, (const void *)batch_kernel_for(kp.kind), kBlock, 0);
         const int cap0 = std::max(1, (int)(std::max(1, std::min(per_sm0 * sms, kMaxGrid)) * cta_fraction *
@@ -156,15 +240,15 @@ fg_status batch_launch(const fg_query *qs, int32_t nq, const fg_batch_options *o
         int share = 1;
         if (kp.queries.size() <= 8)
             while (share * 2 <= cap0 / (int)kp.queries.size()) share *= 2;
-        for (int i : kp.queries) by_size[std::max(team_size_for(view[i]->m), share)].push_back(i);
+        for (int u : kp.queries) by_size[std::max(team_size_for(view[u]->m), share)].push_back(u);
         std::vector<double> cw;
         for (auto &c : by_size) {
             std::vector<int> v = c.second;
             std::sort(v.begin(), v.end(), [&](int a, int b) {
-                return work_of(qs[a].algo, *view[a]) > work_of(qs[b].algo, *view[b]);
+                return unit_work(units[a], *view[a]) > unit_work(units[b], *view[b]);
             });
             double w = 0;
-            for (int i : v) w += work_of(qs[i].algo, *view[i]);
+            for (int u : v) w += unit_work(units[u], *view[u]);
             kp.class_size.push_back(c.first);
             kp.class_q.push_back(v);
             cw.push_back(w);
@@ -196,9 +280,9 @@ fg_status batch_launch(const fg_query *qs, int32_t nq, const fg_batch_options *o
         for (size_t c = 0; c < kp.class_size.size(); c++) kp.ctas += kp.class_teams[c] * kp.class_size[c];
     }
 
-    // ---- one device allocation: zeroed region | tables | query workspaces | staging
-    size_t zero_bytes = Workspace::need(1, sizeof(Ctrl)) + Workspace::need(nq, sizeof(Ctrl));
-    size_t table_bytes = Workspace::need(nq, sizeof(Params)) + Workspace::need(nq, sizeof(int));
+    // ---- one device allocation: zeroed region | tables | unit workspaces | staging
+    size_t zero_bytes = Workspace::need(1, sizeof(Ctrl)) + Workspace::need(nu, sizeof(Ctrl));
+    size_t table_bytes = Workspace::need(nu, sizeof(Params)) + Workspace::need(nu, sizeof(int));
     for (auto &kv : kinds) {
         KindPlan &kp = kv.second;
         int teams = 0;
@@ -207,12 +291,12 @@ fg_status batch_launch(const fg_query *qs, int32_t nq, const fg_batch_options *o
         zero_bytes += Workspace::need(2 * teams, 4) + Workspace::need(teams, 4) + Workspace::need(nc, 4);
         table_bytes += Workspace::need(kp.ctas, sizeof(int4)) + 2 * Workspace::need(nc, 4);
     }
-    std::vector<bool> dev_out(nq);
+    job.staged.assign(nq, false);
     size_t ws_bytes = 0;
+    for (int u = 0; u < nu; u++) ws_bytes += query_workspace_bytes(*view[u], units[u].algo, units[u].mode);
     for (int i = 0; i < nq; i++) {
-        ws_bytes += query_workspace_bytes(*view[i], (Algo)qs[i].algo, mode[i]);
-        dev_out[i] = is_device_pointer(qs[i].out);
-        if (!dev_out[i]) ws_bytes += Workspace::need(view[i]->n, 4);
+        job.staged[i] = !is_device_pointer(qs[i].out);
+        if (job.staged[i]) ws_bytes += Workspace::need(view[job.qunit[i]]->n, 4);
     }
     const size_t total = zero_bytes + table_bytes + ws_bytes;
     job.device_bytes = total;
@@ -227,32 +311,42 @@ fg_status batch_launch(const fg_query *qs, int32_t nq, const fg_batch_options *o
     std::vector<char> img(table_bytes, 0);
     Workspace zw{base}, tw{base + zero_bytes}, hw{img.data()}, qw{base + zero_bytes + table_bytes};
     Ctrl *bctrl = zw.take<Ctrl>(1);
-    job.d_ctrls = zw.take<Ctrl>(nq);
-    Params *d_params = tw.take<Params>(nq);
-    Params *h_params = hw.take<Params>(nq);
-    int *d_order = tw.take<int>(nq);
-    int *h_order = hw.take<int>(nq);
-    job.staging.assign(nq, nullptr);
-    for (int i = 0; i < nq; i++) {
+    job.d_ctrls = zw.take<Ctrl>(nu);
+    Params *d_params = tw.take<Params>(nu);
+    Params *h_params = hw.take<Params>(nu);
+    int *d_order = tw.take<int>(nu);
+    int *h_order = hw.take<int>(nu);
+    job.dout.assign(nq, nullptr);
+    for (int u = 0; u < nu; u++) {
+        const BatchUnit &un = units[u];
         char *w = qw.base + qw.off;
-        qw.off += query_workspace_bytes(*view[i], (Algo)qs[i].algo, mode[i]);
+        qw.off += query_workspace_bytes(*view[u], un.algo, un.mode);
         Params p;
-        carve_query_workspace(w, *view[i], (Algo)qs[i].algo, mode[i], p);
-        if (mode[i] == kPull) p.tv = (qs[i].algo == FG_ALGO_CC) ? qs[i].g->s : qs[i].g->t;
-        p.delta = default_delta(qs[i].g);
-        p.ctrl = job.d_ctrls + i;
-        p.source = qs[i].algo == FG_ALGO_CC ? 0 : qs[i].src;
-        p.max_rounds = view[i]->n > INT32_MAX - 2 ? INT32_MAX : view[i]->n + 2;
-        p.timeout_ns = (unsigned long long)tmo * 1000000ull;
-        if (dev_out[i]) {
-            p.out = qs[i].out;
-        } else {
-            job.staging[i] = qw.take<int32_t>(view[i]->n);
-            p.out = job.staging[i];
-        }
-        h_params[i] = p;
+        carve_query_workspace(w, *view[u], un.algo, un.mode, p);
+        h_params[u] = p;
     }
-    job.params.assign(h_params, h_params + nq);
+    for (int i = 0; i < nq; i++)
+        job.dout[i] = job.staged[i] ? qw.take<int32_t>(view[job.qunit[i]]->n) : qs[i].out;
+    for (int u = 0; u < nu; u++) {
+        const BatchUnit &un = units[u];
+        Params &p = h_params[u];
+        if (un.mode == kPull) p.tv = (un.algo == kCC) ? un.g->s : un.g->t;
+        p.delta = default_delta(un.g);
+        p.ctrl = job.d_ctrls + u;
+        p.source = un.algo == kCC ? 0 : qs[un.q[0]].src;
+        p.max_rounds = view[u]->n > INT32_MAX - 2 ? INT32_MAX : view[u]->n + 2;
+        p.timeout_ns = (unsigned long long)tmo * 1000000ull;
+        if (un.mode == kMulti) {
+            p.ms_k = (int32_t)un.q.size();
+            for (size_t j = 0; j < un.q.size(); j++) {
+                p.ms_src[j] = qs[un.q[j]].src;
+                p.ms_out[j] = job.dout[un.q[j]];
+            }
+        } else {
+            p.out = job.dout[un.q[0]];
+        }
+    }
+    job.params.assign(h_params, h_params + nu);
     std::vector<BatchArgs> args;
     std::vector<int> kind_ctas;
     std::vector<BatchFn> kind_fn;
@@ -273,7 +367,7 @@ fg_status batch_launch(const fg_query *qs, int32_t nq, const fg_batch_options *o
         int cta = 0, team = 0;
         for (int c = 0; c < nc; c++) {
             h_cb[c] = order_pos;
-            for (int i : kp.class_q[c]) h_order[order_pos++] = i;
+            for (int u : kp.class_q[c]) h_order[order_pos++] = u;
             h_ce[c] = order_pos;
             for (int k = 0; k < kp.class_teams[c]; k++, team++)
                 for (int r = 0; r < kp.class_size[c]; r++) h_ct[cta++] = make_int4(team, r, kp.class_size[c], c);
@@ -349,15 +443,22 @@ fg_status batch_launch(const fg_query *qs, int32_t nq, const fg_batch_options *o
     ck(cudaEventRecord(job.ev1, st), "event");
     job.h_ctrls = h_ctrls_pinned;
     if (!job.h_ctrls) {
-        job.own_ctrls.resize(nq);
+        job.own_ctrls.resize(nu);
         job.h_ctrls = job.own_ctrls.data();
     }
-    ck(cudaMemcpyAsync(job.h_ctrls, job.d_ctrls, nq * sizeof(Ctrl), cudaMemcpyDeviceToHost, st), "status copy");
+    ck(cudaMemcpyAsync(job.h_ctrls, job.d_ctrls, nu * sizeof(Ctrl), cudaMemcpyDeviceToHost, st), "status copy");
     if (enqueue_host_copies) {
-        for (int i = 0; i < nq; i++)
-            if (job.staging[i])
-                ck(cudaMemcpyAsync(qs[i].out, job.staging[i], (size_t)view[i]->n * sizeof(int32_t),
-                                   cudaMemcpyDeviceToHost, st), "result copy");
+        for (int u = 0; u < nu; u++) {
+            const BatchUnit &un = units[u];
+            const size_t bytes = (size_t)view[u]->n * sizeof(int32_t);
+            for (size_t j = 0; j < un.q.size(); j++) {
+                const int i = un.q[j];
+                if (un.mode != kMulti && j > 0)   // the unit's one result, to its other outputs
+                    ck(cudaMemcpyAsync(qs[i].out, job.dout[un.q[0]], bytes, cudaMemcpyDefault, st), "result copy");
+                else if (job.staged[i])
+                    ck(cudaMemcpyAsync(qs[i].out, job.dout[i], bytes, cudaMemcpyDeviceToHost, st), "result copy");
+            }
+        }
         job.host_copies_done = true;
     }
     ck(cudaEventRecord(job.done, st), "event");
@@ -368,6 +469,7 @@ fg_status batch_launch(const fg_query *qs, int32_t nq, const fg_batch_options *o
 // Waits for a launched batch, reports every query and releases the batch.
 fg_status batch_finish(BatchJob &job, fg_status *status_out, fg_stats *stats_out, fg_batch_stats *bstats) {
     const int nq = job.nq;
+    const int nu = (int)job.units.size();
     cudaStream_t st = job.st;
     auto ck = [&](cudaError_t err, const char *what) {
         if (err != cudaSuccess && job.status == FG_OK) {
@@ -379,53 +481,89 @@ fg_status batch_finish(BatchJob &job, fg_status *status_out, fg_stats *stats_out
     if (job.done) ck(cudaEventSynchronize(job.done), "batch");
     float ms = 0.f;
     if (job.status == FG_OK && job.ev0 && job.ev1) cudaEventElapsedTime(&ms, job.ev0, job.ev1);
-    fg_status first_err = FG_OK;
-    std::string first_msg;
-    for (int i = 0; i < nq && job.status == FG_OK; i++) {
-        const Ctrl &hc = job.h_ctrls[i];
-        const fg_query &q = job.qs[i];
-        const Params &p = job.params[i];
-        fg_status qs_st = FG_OK;
-        if (hc.status & kStTimeout) qs_st = FG_ERR_TIMEOUT;
-        else if (hc.status & kStRoundCap) qs_st = FG_ERR_TIMEOUT;
-        else if (hc.status & kStWorklist) qs_st = FG_ERR_CUDA;
-        else if (!hc.done) qs_st = FG_ERR_TIMEOUT;
-        else if ((hc.status & kStOverflow) && q.algo == FG_ALGO_SSSP) {
+    std::vector<fg_status> qst(nq, FG_OK);
+    for (int u = 0; u < nu && job.status == FG_OK; u++) {
+        const Ctrl &hc = job.h_ctrls[u];
+        const BatchUnit &un = job.units[u];
+        const Params &p = job.params[u];
+        const View &v = *job.view[u];
+        const size_t bytes = (size_t)v.n * sizeof(int32_t);
+        fg_status us = FG_OK;
+        if (hc.status & kStTimeout) us = FG_ERR_TIMEOUT;
+        else if (hc.status & kStRoundCap) us = FG_ERR_TIMEOUT;
+        else if (hc.status & kStWorklist) us = FG_ERR_CUDA;
+        else if (!hc.done) us = FG_ERR_TIMEOUT;
+        for (int i : un.q) qst[i] = us;
+        if (us == FG_OK && (hc.status & kStOverflow) && un.algo == kSSSP) {
             int *flag = reinterpret_cast<int *>(p.ctrl);
             int hf = 0;
             ck(cudaMemsetAsync(flag, 0, sizeof(int), st), "memset");
-            overflow_check_launch(*job.view[i], p.out, flag, st);
+            if (un.mode == kMulti) {
+                ms_overflow_check_launch(v, p.A, p.ms_k, flag, st);
+            } else {
+                overflow_check_launch(v, p.out, flag, st);
+            }
             ck(cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
             ck(cudaStreamSynchronize(st), "overflow check");
-            if (hf) qs_st = FG_ERR_OVERFLOW;
+            if (un.mode == kMulti) {
+                // the sweep wrote no output: write those of the sources that did not overflow
+                MsOuts ok{};
+                for (size_t j = 0; j < un.q.size(); j++) {
+                    if ((hf >> j) & 1) qst[un.q[j]] = FG_ERR_OVERFLOW;
+                    else ok.p[j] = job.dout[un.q[j]];
+                }
+                ms_output_launch(p.A, v.n, p.ms_k, ok, st);
+                if (job.host_copies_done)   // the early copies carried no result: copy again
+                    for (size_t j = 0; j < un.q.size(); j++) {
+                        const int i = un.q[j];
+                        if (qst[i] == FG_OK && job.staged[i])
+                            ck(cudaMemcpyAsync(job.qs[i].out, job.dout[i], bytes, cudaMemcpyDeviceToHost, st),
+                               "result copy");
+                    }
+            } else if (hf) {
+                for (int i : un.q) qst[i] = FG_ERR_OVERFLOW;
+            }
         }
-        if (qs_st == FG_OK && job.staging[i] && !job.host_copies_done)
-            ck(cudaMemcpyAsync(q.out, job.staging[i], (size_t)job.view[i]->n * sizeof(int32_t),
-                               cudaMemcpyDeviceToHost, st), "result copy");
-        if (status_out) status_out[i] = qs_st;
-        if (qs_st != FG_OK && first_err == FG_OK) {
-            first_err = qs_st;
-            first_msg = "batch query " + std::to_string(i) + " failed: " + fg_status_string(qs_st);
-        }
-        if (stats_out) {
-            fg_stats &s = stats_out[i];
-            s = fg_stats{};
-            s.mode = (int32_t)job.mode[i];
-            s.rounds = hc.rounds;
-            s.jump_passes = hc.jump_passes;
-            s.vertices_processed = (int64_t)hc.st_vertices;
-            s.edges_relaxed = (int64_t)hc.st_edges;
-            s.updates = (int64_t)hc.st_updates;
-            s.pushes = (int64_t)hc.st_pushes;
-            s.scanned = (int64_t)hc.st_scanned;
-            s.barriers = hc.barriers;
-            s.pull_rounds = hc.pull_rounds;
-            s.edges_pulled = (int64_t)hc.st_pulled;
+        if (!job.host_copies_done)
+            for (size_t j = 0; j < un.q.size(); j++) {
+                const int i = un.q[j];
+                if (qst[i] != FG_OK) continue;
+                if (un.mode != kMulti && j > 0)
+                    ck(cudaMemcpyAsync(job.qs[i].out, job.dout[un.q[0]], bytes, cudaMemcpyDefault, st),
+                       "result copy");
+                else if (job.staged[i])
+                    ck(cudaMemcpyAsync(job.qs[i].out, job.dout[i], bytes, cudaMemcpyDeviceToHost, st),
+                       "result copy");
+            }
+        if (stats_out)
+            for (int i : un.q) {
+                fg_stats &s = stats_out[i];
+                s = fg_stats{};
+                s.mode = un.mode == kMulti ? -1 : (int32_t)un.mode;
+                s.rounds = hc.rounds;
+                s.jump_passes = hc.jump_passes;
+                s.vertices_processed = (int64_t)hc.st_vertices;
+                s.edges_relaxed = (int64_t)hc.st_edges;
+                s.updates = (int64_t)hc.st_updates;
+                s.pushes = (int64_t)hc.st_pushes;
+                s.scanned = (int64_t)hc.st_scanned;
+                s.barriers = hc.barriers;
+                s.pull_rounds = hc.pull_rounds;
+                s.edges_pulled = (int64_t)hc.st_pulled;
+            }
+    }
+    ck(cudaStreamSynchronize(st), "result copies");
+    if (job.status != FG_OK)
+        for (int i = 0; i < nq; i++) qst[i] = job.status;
+    fg_status first_err = FG_OK;
+    std::string first_msg;
+    for (int i = 0; i < nq; i++) {
+        if (status_out) status_out[i] = qst[i];
+        if (qst[i] != FG_OK && first_err == FG_OK) {
+            first_err = qst[i];
+            first_msg = "batch query " + std::to_string(i) + " failed: " + fg_status_string(qst[i]);
         }
     }
-    if (job.status != FG_OK && status_out)
-        for (int i = 0; i < nq; i++) status_out[i] = job.status;
-    ck(cudaStreamSynchronize(st), "result copies");
     if (job.exec) cudaGraphExecDestroy(job.exec);
     if (job.graph) cudaGraphDestroy(job.graph);
     for (size_t k = 0; k < job.ks.size(); k++) {
@@ -457,7 +595,8 @@ fg_status batch_finish(BatchJob &job, fg_status *status_out, fg_stats *stats_out
 fg_status run_batch(const fg_query *qs, int32_t nq, const fg_batch_options *opt, fg_status *status_out,
                     fg_stats *stats_out, fg_batch_stats *bstats) {
     BatchJob job;
-    fg_status s = batch_launch(qs, nq, opt, 1.0, false, nullptr, job);
+    const bool fuse = opt && opt->fuse_same_graph;
+    fg_status s = batch_launch(qs, nq, opt, 1.0, false, fuse, nullptr, job);
     fg_status f = batch_finish(job, status_out, stats_out, bstats);
     return s != FG_OK ? s : f;
 }

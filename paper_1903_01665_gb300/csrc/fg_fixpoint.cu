@@ -89,6 +89,12 @@ DeviceProps device_props(int dev) {
     return p;
 }
 
+int current_device() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return dev;
+}
+
 
 }  // namespace
 
@@ -97,6 +103,16 @@ void overflow_check_launch(const View &g, const int32_t *D, int *flag, cudaStrea
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     overflow_check_kernel<<<std::max(1, sms) * 8, kBlock, 0, st>>>(g, D, flag);
+    count_launch();
+}
+
+void ms_overflow_check_launch(const View &g, const int32_t *D, int k, int *flag, cudaStream_t st) {
+    ms_overflow_check_kernel<<<std::max(1, device_props(current_device()).sms) * 8, kBlock, 0, st>>>(g, D, k, flag);
+    count_launch();
+}
+
+void ms_output_launch(const int32_t *D, int32_t n, int k, const MsOuts &outs, cudaStream_t st) {
+    ms_output_kernel<<<std::max(1, device_props(current_device()).sms) * 8, kBlock, 0, st>>>(D, n, k, outs);
     count_launch();
 }
 
@@ -427,8 +443,7 @@ fg_status run_multi(const fg_graph *G, Algo algo, int32_t k, const int32_t *srcs
         int hf = 0;
         e = cudaMemsetAsync(flag, 0, sizeof(int), st);
         if (e == cudaSuccess) {
-            ms_overflow_check_kernel<<<dp.sms * 8, kBlock, 0, st>>>(g, p.A, k, flag);
-            count_launch();
+            ms_overflow_check_launch(g, p.A, k, flag, st);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -439,8 +454,7 @@ fg_status run_multi(const fg_graph *G, Algo algo, int32_t k, const int32_t *srcs
             else ok_outs.p[j] = dout[j];
         }
         if (e == cudaSuccess && hf != (1 << k) - 1) {
-            ms_output_kernel<<<dp.sms * 8, kBlock, 0, st>>>(p.A, n, k, ok_outs);
-            count_launch();
+            ms_output_launch(p.A, n, k, ok_outs, st);
             e = cudaGetLastError();
         }
         if (e != cudaSuccess) {

@@ -394,15 +394,31 @@ fg_status run_query(const fg_graph *g, Algo algo, Mode mode, int32_t source, int
 fg_status run_sweep(const fg_graph *g, Mode mode, const int32_t *cur, int32_t *next,
                     cudaStream_t stream, int64_t *updates, float *kernel_ms);
 void overflow_check_launch(const View &g, const int32_t *D, int *flag, cudaStream_t st);
+// multi-source sweeps: bit s of *flag for each source s that overflowed; the
+// rows' slots to the outputs that are set
+void ms_overflow_check_launch(const View &g, const int32_t *D, int k, int *flag, cudaStream_t st);
+void ms_output_launch(const int32_t *D, int32_t n, int k, const MsOuts &outs, cudaStream_t st);
 
 // batches (fg_batch.cu)
+// One fixpoint of a batch: a plain query (its outputs all receive the one
+// result: several only for CC, which has no source), or a fused multi-source
+// sweep (mode kMulti: one output per slot, up to 8).
+struct BatchUnit {
+    const fg_graph *g = nullptr;
+    Algo algo = kSSSP;
+    Mode mode = kVertexSync;
+    std::vector<int> q;                   // the batch query of each output / slot
+};
 struct BatchJob {
     int nq = 0;
     std::vector<fg_query> qs;
-    std::vector<Mode> mode;
-    std::vector<const View *> view;
-    std::vector<Params> params;           // host copies of the device parameters
-    std::vector<int32_t *> staging;       // device staging of host outputs (null: device output)
+    std::vector<Mode> qmode;              // per query: the mode it ran in (kMulti if fused)
+    std::vector<int> qunit;               // per query: its unit
+    std::vector<BatchUnit> units;
+    std::vector<const View *> view;       // per unit
+    std::vector<Params> params;           // per unit: host copies of the device parameters
+    std::vector<int32_t *> dout;          // per query: device buffer its result lands in
+    std::vector<bool> staged;             // per query: host output, copied from dout
     bool host_copies_done = false;
     char *base = nullptr;                 // the batch's one device allocation
     size_t device_bytes = 0;
@@ -420,7 +436,7 @@ struct BatchJob {
     std::string msg;
 };
 fg_status batch_launch(const fg_query *qs, int32_t nq, const fg_batch_options *opt, double cta_fraction,
-                       bool enqueue_host_copies, Ctrl *h_ctrls_pinned, BatchJob &job);
+                       bool enqueue_host_copies, bool fuse, Ctrl *h_ctrls_pinned, BatchJob &job);
 fg_status batch_finish(BatchJob &job, fg_status *status_out, fg_stats *stats_out, fg_batch_stats *bstats);
 fg_status run_batch(const fg_query *qs, int32_t nq, const fg_batch_options *opt, fg_status *status_out,
                     fg_stats *stats_out, fg_batch_stats *bstats);

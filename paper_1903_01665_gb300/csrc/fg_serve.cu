@@ -10,10 +10,15 @@
 // Completion = the wave's results are in the callers' outputs; latency is
 // measured from submission to completion.
 //
-// A request on a large graph (exclusive_edges) is not batched: it runs alone
-// on the whole device with the plain per-query kernel as soon as the waves
+// A request on a large graph (exclusive_edges) is not batched with other
+// graphs' requests: it runs on the whole device as soon as the waves
 // admitted before it have finished (the queue stays first come, first
-// served).
+// served) -- alone with the plain per-query kernel, or, with fusion, together
+// with the later pending requests of the same graph and algorithm: up to 8
+// SSSP or BFS requests as one multi-source sweep, every pending CC request
+// as one computation copied to each output.  On such graphs one query fills
+// the device, and fusing the queries' sweeps is what still saves work.
+// Waves of smaller graphs fuse the same way inside the batch (fg_batch.cu).
 //
 // In one-at-a-time mode the worker serves the queue strictly one request at
 // a time with the plain per-query kernel (the baseline).
@@ -106,6 +111,66 @@ void serve_one_at_a_time(fg_server *s, std::unique_lock<std::mutex> &lk) {
     complete(s, r, st, 1, Clock::now());
 }
 
+// Runs a group of requests on one graph and algorithm alone on the whole
+// device: one request with the plain per-query kernel, several SSSP/BFS as
+// one multi-source sweep, several CC as one computation copied to each.
+void serve_group_alone(fg_server *s, std::unique_lock<std::mutex> &lk, const std::vector<fg_server::Req> &reqs) {
+    lk.unlock();
+    after_legacy_work(s, 0);
+    fg_options o{};
+    o.stream = s->streams[0];
+    o.wait_timeout_ms = s->opt.wait_timeout_ms;
+    const fg_query &q0 = reqs[0].q;
+    const int k = (int)reqs.size();
+    std::vector<fg_status> sts(k, FG_OK);
+    if (k == 1) {
+        sts[0] = run_query(q0.g, (Algo)q0.algo, (Mode)q0.mode, q0.algo == FG_ALGO_CC ? 0 : q0.src, q0.out, &o,
+                           nullptr);
+    } else if (q0.algo == FG_ALGO_CC) {
+        fg_status st = run_query(q0.g, kCC, (Mode)q0.mode, 0, q0.out, &o, nullptr);
+        cudaError_t e = cudaSuccess;
+        const size_t bytes = (size_t)q0.g->s.n * sizeof(int32_t);
+        for (int j = 1; j < k && st == FG_OK && e == cudaSuccess; j++)
+            e = cudaMemcpyAsync(reqs[j].q.out, q0.out, bytes, cudaMemcpyDefault, s->streams[0]);
+        if (st == FG_OK && e == cudaSuccess) e = cudaStreamSynchronize(s->streams[0]);
+        if (st == FG_OK && e != cudaSuccess) st = cuda_fail(e, "result copies");
+        for (int j = 0; j < k; j++) sts[j] = st;
+    } else {
+        int32_t srcs[8];
+        int32_t *outs[8];
+        for (int j = 0; j < k; j++) {
+            srcs[j] = reqs[j].q.src;
+            outs[j] = reqs[j].q.out;
+        }
+        run_multi(q0.g, (Algo)q0.algo, k, srcs, outs, &o, sts.data(), nullptr);
+    }
+    lk.lock();
+    const Clock::time_point now = Clock::now();
+    for (int j = 0; j < k; j++) complete(s, reqs[j], sts[j], k, now);
+}
+
+// The head request of the queue and the later pending requests that can
+// join it: same graph and algorithm (and mode, without fusion), up to `cap`;
+// they are taken out of the queue.
+std::vector<fg_server::Req> take_group(fg_server *s, size_t cap, bool want_exclusive) {
+    std::vector<fg_server::Req> out;
+    const fg_query head = s->pending.front().q;
+    const bool fuse = !s->opt.no_fusion;
+    size_t window = std::min(s->pending.size(), (size_t)s->opt.max_wave * 8);   // requests scanned
+    for (size_t i = 0; i < window && i < s->pending.size() && out.size() < cap;) {
+        const fg_server::Req &r = s->pending[i];
+        if (r.exclusive != want_exclusive || r.q.g != head.g || r.q.algo != head.algo ||
+            (!fuse && r.q.mode != head.mode)) {
+            i++;
+            continue;
+        }
+        out.push_back(r);
+        s->pending.erase(s->pending.begin() + (long)i);
+        window--;
+    }
+    return out;
+}
+
 void worker_main(fg_server *s) {
     cudaSetDevice(s->device);
     const int max_inflight = s->opt.max_inflight;
@@ -145,7 +210,13 @@ void worker_main(fg_server *s) {
         while (!s->pending.empty() && (int)s->inflight.size() < max_inflight) {
             if (s->pending.front().exclusive) {
                 if (!s->inflight.empty()) break;   // after the waves before it
-                serve_one_at_a_time(s, lk);
+                if (s->opt.no_fusion) {
+                    serve_one_at_a_time(s, lk);
+                } else {
+                    const size_t cap = s->pending.front().q.algo == FG_ALGO_CC ? (size_t)max_wave : 8;
+                    std::vector<fg_server::Req> grp = take_group(s, cap, true);
+                    serve_group_alone(s, lk, grp);
+                }
                 continue;
             }
             // a lone request on an idle device: the plain per-query kernel
@@ -156,17 +227,20 @@ void worker_main(fg_server *s) {
             }
             int slot = 0;
             while (s->slot_busy[slot]) slot++;
-            // A wave holds requests of one kind (graph, algorithm, mode): the
-            // oldest pending request and the later ones of its kind.  Mixed
-            // waves finish with their slowest kind while the CTAs of the
-            // others idle, and mix hot sets in each SM's L1.
+            // A wave holds requests of one kind (graph, algorithm; and mode
+            // without fusion): the oldest pending request and the later ones
+            // of its kind.  Mixed waves finish with their slowest kind while
+            // the CTAs of the others idle, and mix hot sets in each SM's L1;
+            // with fusion, the batch merges the wave's requests into
+            // multi-source sweeps (SSSP, BFS) and one computation (CC).
             std::unique_ptr<fg_server::Wave> w(new fg_server::Wave());
             size_t bytes = 0;
             const fg_query head = s->pending.front().q;
+            const bool fuse = !s->opt.no_fusion;
             size_t window = std::min(s->pending.size(), (size_t)max_wave * 8);   // requests scanned
             for (size_t i = 0; i < window && i < s->pending.size() && (int)w->reqs.size() < max_wave;) {
                 const fg_server::Req &r = s->pending[i];
-                if (r.exclusive || r.q.g != head.g || r.q.algo != head.algo || r.q.mode != head.mode) {
+                if (r.exclusive || r.q.g != head.g || r.q.algo != head.algo || (!fuse && r.q.mode != head.mode)) {
                     i++;
                     continue;
                 }
@@ -194,7 +268,7 @@ void worker_main(fg_server *s) {
             after_legacy_work(s, slot);
             // a wave shares the device with the waves already running
             const double fraction = 1.0 / (double)s->inflight.size();
-            fg_status ls = batch_launch(qs.data(), (int32_t)qs.size(), &bo, fraction, true,
+            fg_status ls = batch_launch(qs.data(), (int32_t)qs.size(), &bo, fraction, true, fuse,
                                         s->pinned + (size_t)slot * max_wave, wp->job);
             lk.lock();
             if (ls != FG_OK) {

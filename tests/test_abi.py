@@ -61,10 +61,12 @@ int main(void) {
   printf("fg_query %zu\nfg_batch_options %zu\nfg_batch_stats %zu\n", sizeof(fg_query), sizeof(fg_batch_options), sizeof(fg_batch_stats));
   P(fg_query, g); P(fg_query, algo); P(fg_query, src); P(fg_query, out); P(fg_query, mode);
   P(fg_batch_options, stream); P(fg_batch_options, use_cuda_graph); P(fg_batch_options, wait_timeout_ms);
+  P(fg_batch_options, fuse_same_graph);
   P(fg_batch_stats, kernel_ms); P(fg_batch_stats, launches); P(fg_batch_stats, teams); P(fg_batch_stats, ctas);
   printf("fg_server_options %zu\nfg_completion %zu\n", sizeof(fg_server_options), sizeof(fg_completion));
   P(fg_server_options, hbm_budget_bytes); P(fg_server_options, max_inflight); P(fg_server_options, max_wave);
   P(fg_server_options, one_at_a_time); P(fg_server_options, wait_timeout_ms); P(fg_server_options, exclusive_edges);
+  P(fg_server_options, no_fusion);
   P(fg_completion, ticket); P(fg_completion, status); P(fg_completion, wave_size); P(fg_completion, latency_ms);
   return 0;
 }
@@ -114,6 +116,8 @@ def test_host_side_argument_checks():
     assert st == fg.FG_ERR_INVALID_ARG and "graph is NULL" in fg.fg_last_error()
     st, _, _ = fg.fg_autotune(None, 0)
     assert st == fg.FG_ERR_INVALID_ARG
+    st, _, _ = fg.fg_run_multi(None, fg.FG_ALGO_SSSP, [0], [out])
+    assert st == fg.FG_ERR_INVALID_ARG and "graph is NULL" in fg.fg_last_error()
     assert fg.fg_status_string(fg.FG_ERR_OVERFLOW) == "FG_ERR_OVERFLOW"
     assert fg.fg_status_string(fg.FG_ERR_TIMEOUT) == "FG_ERR_TIMEOUT"
 

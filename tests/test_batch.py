@@ -79,3 +79,65 @@ def test_batch_auto_after_autotune_and_overflow_status():
         assert np.all(ob == 99)
         for a in (0, 1, 2):
             np.testing.assert_array_equal(outs[a].cpu().numpy(), _expected(g, a, s))
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_fused_batch_matches_oracle(use_graph):
+    """fuse_same_graph: the SSSP and BFS queries of a graph run as
+    multi-source sweeps of up to 8 sources (11 sources: a sweep of 8 and one
+    of 3), its CC queries as one computation; a graph's lone query keeps its
+    own mode.  Every output (device, pageable and pinned host; repeated
+    sources) must be the oracle's."""
+    import torch
+    from contextlib import ExitStack
+    graphs = _graphs()
+    with ExitStack() as stack:
+        handles = [stack.enter_context(graph_handle(g)) for g in graphs]
+        queries, want, fused = [], [], []
+        for gi, (g, h) in enumerate(zip(graphs, handles)):
+            srcs = [int(x) for x in gg.sources(g, 10, seed=200 + gi)]
+            srcs.append(srcs[0])   # a repeat
+            plan = [(0, s) for s in srcs] + [(1, s) for s in srcs[:3]] + [(2, 0)] * 3
+            if gi == 2:
+                plan = [(1, srcs[1])]   # a lone query on its graph
+            for k, (algo, s) in enumerate(plan):
+                where = k % 3
+                if where == 0:
+                    out = torch.full((g.n,), -5, dtype=torch.int32, device="cuda")
+                elif where == 1:
+                    out = np.full(g.n, -5, np.int32)
+                else:
+                    out = torch.full((g.n,), -5, dtype=torch.int32).pin_memory()
+                queries.append((h, algo, s, out, fg.FG_VERTEX_ASYNC))
+                want.append(_expected(g, algo, s))
+                fused.append(algo != 2 and gi != 2)
+        st, sts, stats, bst = fg.fg_run_batch(queries, use_cuda_graph=use_graph, fuse_same_graph=True)
+        assert st == fg.FG_OK, fg.fg_last_error()
+        assert all(x == fg.FG_OK for x in sts)
+        for (h, algo, s, out, mode), exp, stt, fu in zip(queries, want, stats, fused):
+            got = out.cpu().numpy() if hasattr(out, "cpu") else out
+            np.testing.assert_array_equal(got, exp, err_msg=f"algo={algo} src={s}")
+            assert stt.mode == (-1 if fu else mode)
+        assert bst.launches == 4   # SSSP sweeps, BFS sweeps, CC, the lone BFS query's kind
+
+
+def test_fused_batch_overflow_fails_only_its_slot():
+    """A fused sweep with sources 0 and 1 on 0 -> 1 -> 2 (2^30, 2^30): source
+    0 overflows at vertex 2, source 1 does not; the overflowed host output is
+    untouched, the other is the oracle's, and the other graph's queries are
+    unaffected."""
+    import torch
+    g = gg.rmat(12, seed=9)
+    bad = gg.path(3, weights=[2**30, 2**30])
+    with graph_handle(g) as h, graph_handle(bad) as hb:
+        s = [int(x) for x in gg.sources(g, 2, seed=5)]
+        outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in range(2)]
+        ob = [np.full(3, 99, np.int32), np.full(3, 98, np.int32)]
+        q = [(h, 0, s[0], outs[0], 0), (h, 0, s[1], outs[1], 0), (hb, 0, 0, ob[0], 0), (hb, 0, 1, ob[1], 0)]
+        st, sts, _, _ = fg.fg_run_batch(q, fuse_same_graph=True)
+        assert st == fg.FG_ERR_OVERFLOW
+        assert sts == [fg.FG_OK, fg.FG_OK, fg.FG_ERR_OVERFLOW, fg.FG_OK]
+        assert np.all(ob[0] == 99)
+        np.testing.assert_array_equal(ob[1], _expected(bad, 0, 1))
+        for j in range(2):
+            np.testing.assert_array_equal(outs[j].cpu().numpy(), _expected(g, 0, s[j]))

@@ -89,13 +89,13 @@ def test_results_in_the_mix_equal_results_alone(setup):
 
 
 def test_large_graphs_run_alone_and_match(setup):
-    """Requests on graphs with at least exclusive_edges edges run alone (wave
-    size 1) on the whole device between the waves; every result is the
-    oracle's."""
+    """Without fusion, requests on graphs with at least exclusive_edges edges
+    run alone (wave size 1) on the whole device between the waves; every
+    result is the oracle's."""
     graphs, handles = setup
     reqs = _requests(graphs, 120, seed=8)
     cut = graphs[1].m   # rmat-15 and larger run alone
-    outs, comps = _serve(handles, graphs, reqs, max_inflight=3, max_wave=16, exclusive_edges=cut)
+    outs, comps = _serve(handles, graphs, reqs, max_inflight=3, max_wave=16, exclusive_edges=cut, no_fusion=True)
     want = _alone(graphs, handles, reqs)
     for (gi, algo, s), out in zip(reqs, outs):
         np.testing.assert_array_equal(out.cpu().numpy(), want[(gi, algo, s)])
@@ -126,6 +126,36 @@ def test_one_at_a_time_baseline(setup):
     reqs = _requests(graphs, 40, seed=7)
     outs, comps = _serve(handles, graphs, reqs, one_at_a_time=True)
     assert all(c[2] == 1 for c in comps)
+    want = _alone(graphs, handles, reqs)
+    for (gi, algo, s), out in zip(reqs, outs):
+        np.testing.assert_array_equal(out.cpu().numpy(), want[(gi, algo, s)])
+
+
+def test_large_graph_requests_fuse_by_graph_and_algorithm(setup):
+    """With fusion (the default), a large-graph request runs on the whole
+    device together with the later pending requests of its graph and
+    algorithm: up to 8 SSSP or BFS requests in one multi-source sweep, the
+    pending CC requests in one computation.  A burst on large graphs only
+    must produce fused groups, and every result must be the oracle's."""
+    graphs, handles = setup
+    reqs = _requests(graphs, 200, seed=9)
+    outs, comps = _serve(handles, graphs, reqs, host_every=5, max_inflight=2, max_wave=32, exclusive_edges=1)
+    want = _alone(graphs, handles, reqs)
+    for (gi, algo, s), out in zip(reqs, outs):
+        np.testing.assert_array_equal(out.cpu().numpy(), want[(gi, algo, s)])
+    by_ticket = {c[0]: c for c in comps}
+    first = min(by_ticket)
+    sizes = {0: [], 1: [], 2: []}
+    for i, (gi, algo, s) in enumerate(reqs):
+        sizes[algo].append(by_ticket[first + i][2])
+    assert max(sizes[0]) > 1 and max(sizes[1]) > 1, "a burst should fuse SSSP and BFS requests"
+    assert max(sizes[0]) <= 8 and max(sizes[1]) <= 8
+
+
+def test_fusion_off_serves_the_same_results(setup):
+    graphs, handles = setup
+    reqs = _requests(graphs, 120, seed=10)
+    outs, comps = _serve(handles, graphs, reqs, max_inflight=2, max_wave=16, no_fusion=True)
     want = _alone(graphs, handles, reqs)
     for (gi, algo, s), out in zip(reqs, outs):
         np.testing.assert_array_equal(out.cpu().numpy(), want[(gi, algo, s)])
