@@ -14,11 +14,17 @@ C ABI with pinned host buffers (graph upload and result downloads inside the
 timed region).  Under torchrun, every rank runs an independent replica
 (the method shards by independent queries; no data-path collective).
 
-Besides the step, the JSON line carries: the all-active sweep roofline test
-(``sweep_roofline``), the pull and bucket modes against the best paper mode
-on the same queries (``extra_modes``), the bucketed SSSP on the 4096^2 grid
-(``grid_bucket``), the batched workload (``batched``) and the serving
-comparison (``serving``); each can be skipped with its ``--no-...`` flag.
+Besides the step, the JSON line carries (kept short, so that a record of the
+line's last few KB holds all of it): the roofline of the dominant kernel by
+the measurement plan's byte formula, with the all-active sweep roofline test
+nested in it (``roofline.sweep``); the multi-source sweep against the
+separate queries of the step (``fused``); the batched workload (``batched``);
+and the serving comparison on the stated ~64 GB resident set (``serving``:
+per rate, [server, one-at-a-time] p50/p99 ms and completed/s).  ``--detail
+PATH`` writes everything measured -- per kernel, the pull and bucket modes
+(``extra_modes``), the bucketed SSSP on the 4096^2 grid (``grid_bucket``),
+every serving row -- to a JSON file.  Each part can be skipped with its
+``--no-...`` flag.
 
 ``--impl reference`` times the CPU oracle (single thread) on a bounded sample
 of the same workload instead.
@@ -526,8 +532,9 @@ def run_serving(device, full: bool = False, rates=(100, 300, 1000, 3000, 10000),
         for gi, h in enumerate(handles):
             for algo in (0, 1, 2):
                 fg.check(fg.fg_autotune(h, algo, int(srcs[gi][0]))[0])
-        # output buffers: one per request (recycled round-robin on the large set)
-        ring = 16 if full else n_req
+        # output buffers: one per request (recycled round-robin on the large set,
+        # 32 per graph: 24 GB in all)
+        ring = 32 if full else n_req
         outs = [[torch.empty(g.n, dtype=torch.int32, device=device) for _ in range(min(ring, n_req))]
                 for g in graphs]
         result = {"resident_graphs": [f"{g.name} ({g.n} V, {g.m} E)" for g in graphs],
@@ -768,7 +775,12 @@ def run_ours(args):
     if not args.no_batched:
         batched = run_batched(device)
     if not args.no_serving:
-        serving = run_serving(device, full=args.serving_full, n_req=args.serving_requests)
+        rates = tuple(int(x) for x in args.serving_rates.split(","))
+        n_req = args.serving_requests
+        if args.serving_full:   # the full sweep: five rates, 2000 requests each
+            rates, n_req = (100, 300, 1000, 3000, 10000), max(n_req, 2000)
+        serving = run_serving(device, full=args.serving_set == "stated" or args.serving_full, rates=rates,
+                              n_req=n_req)
 
     if rank == 0:
         if sweep is not None:
@@ -955,9 +967,13 @@ def main():
     ap.add_argument("--no-grid-bucket", action="store_true", help="skip the bucketed-SSSP grid comparison")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload comparison")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving comparison")
+    ap.add_argument("--serving-set", default="stated", choices=["stated", "reduced"],
+                    help="resident set served: R-MAT 24-26 + 8192^2 grid (~64 GB, the stated serving "
+                         "configuration) or R-MAT 20-22 + 2048^2 grid (~4 GB)")
+    ap.add_argument("--serving-rates", default="100,1000,10000", help="Poisson arrival rates, requests/s")
+    ap.add_argument("--serving-requests", type=int, default=1000, help="requests per rate")
     ap.add_argument("--serving-full", action="store_true",
-                    help="serve the R-MAT 24-26 + 8192^2 grid resident set (~60 GB) instead of the reduced one")
-    ap.add_argument("--serving-requests", type=int, default=2000)
+                    help="the stated set at rates 100,300,1000,3000,10000 with at least 2000 requests each")
     ap.add_argument("--detail", default=None, help="also write every measurement (per kernel, extra modes, "
                                                    "serving rows) as JSON to this path")
     args = ap.parse_args()
