@@ -435,9 +435,12 @@ def run_grid_bucket(device, reps: int = 2) -> dict:
 def run_batched(device, reps: int = 3) -> dict:
     """The batched workload: 512 SSSP/BFS queries (8 seeded sources per
     graph, alternating) over 64 resident graphs of uneven size (R-MAT scales
-    10-20, grids 256^2-2048^2, weights U[1,1000]), FG_AUTO after the
-    autotuner, run one query at a time with the plain per-query kernels and
-    as one batched CUDA-graph launch; every output compared bit for bit."""
+    10-20, grids 256^2-2048^2, weights U[1,1000]), FG_AUTO (the selection
+    model's plan per graph), run one query at a time with the plain per-query
+    kernels and as one batched CUDA-graph launch, fused and unfused; every
+    output compared bit for bit.  Then the model is checked against the
+    autotuner: per (graph, algorithm), the device time of the model's plan
+    against the fastest (mode, CTAs per SM) fg_autotune measured."""
     import torch
     import paper_1903_01665_gb300 as fg
     graphs = gg.batched_graphs()
@@ -450,12 +453,12 @@ def run_batched(device, reps: int = 3) -> dict:
             fg.check(st)
             handles.append(h)
             degs.append(torch.from_numpy(np.bincount(g.src, minlength=g.n).astype(np.int64)).to(device))
-        tune = {}
-        for gi, algo, s in queries:
-            if (gi, algo) not in tune:
-                st, best, _ = fg.fg_autotune(handles[gi], algo, s)
+        plans = {}
+        for qi, (gi, algo, s) in enumerate(queries):
+            if (gi, algo) not in plans:
+                st, pl = fg.fg_select_plan(handles[gi], algo)
                 fg.check(st)
-                tune[(gi, algo)] = best
+                plans[(gi, algo)] = (pl.mode, pl.blocks_per_sm, s, qi)
         outs1 = [torch.empty(graphs[gi].n, dtype=torch.int32, device=device) for gi, _, _ in queries]
         outs2 = [torch.empty(graphs[gi].n, dtype=torch.int32, device=device) for gi, _, _ in queries]
         outs3 = [torch.empty(graphs[gi].n, dtype=torch.int32, device=device) for gi, _, _ in queries]
@@ -489,16 +492,30 @@ def run_batched(device, reps: int = 3) -> dict:
         bat = statistics.median(t_batch[1:])
         fus = statistics.median(t_fused[1:])
         modes = {}
-        for (gi, algo), m in tune.items():
-            key = f"{ALGO_NAMES[algo]}/{MODE_NAMES[m]}"
+        for (gi, algo), (m, bps, _s, _q) in plans.items():
+            key = f"{ALGO_NAMES[algo]}/{MODE_NAMES[m]}" + ("/2cta" if bps else "")
             modes[key] = modes.get(key, 0) + 1
+        # the model against the autotuner's measurement (median of 3 each)
+        ratios = []
+        for (gi, algo), (m, bps, s, qi) in plans.items():
+            ts = []
+            for _ in range(3):
+                st, stt = fg.fg_run(handles[gi], algo, s, outs1[qi], m, blocks_per_sm=bps)
+                fg.check(st)
+                ts.append(stt.kernel_ms)
+            st, best, times = fg.fg_autotune(handles[gi], algo, s)
+            fg.check(st)
+            ratios.append(statistics.median(ts) / min(t for t in times if t > 0))
+        model_check = {"pairs": len(ratios), "within_10pct": int(sum(r <= 1.1 for r in ratios)),
+                       "worst_ratio": round(max(ratios), 3), "median_ratio": round(statistics.median(ratios), 3)}
         return {"queries": len(queries), "graphs": len(graphs),
                 "one_at_a_time_qps": round(len(queries) / one, 1), "batched_qps": round(len(queries) / fus, 1),
                 "speedup": round(one / fus, 3), "bit_exact": exact and exact_fused,
                 "unfused_qps": round(len(queries) / bat, 1), "unfused_speedup": round(one / bat, 3),
                 "one_at_a_time_gteps": round(edges / one / 1e9, 3), "batched_gteps": round(edges / fus / 1e9, 3),
                 "batch_kernel_ms": round(fbst.kernel_ms, 3), "launches": fbst.launches, "teams": fbst.teams,
-                "ctas": fbst.ctas, "unfused_launches": bst.launches, "autotuned_modes": modes,
+                "ctas": fbst.ctas, "unfused_launches": bst.launches, "model_modes": modes,
+                "model_check": model_check,
                 "fusion": "queries on one graph share work: SSSP/BFS as multi-source sweeps of up to 8 "
                           "sources, CC once (fuse_same_graph); unfused = one fixpoint per query",
                 "timing": "wall clock around each run, median of %d, after one warm-up" % reps}
@@ -529,9 +546,9 @@ def run_serving(device, full: bool = False, rates=(100, 300, 1000, 3000, 10000),
             handles.append(h)
             device_bytes += fg.fg_graph_info(h)[1].device_bytes
         srcs = [gg.sources(g, 64, seed=seed + i) for i, g in enumerate(graphs)]
-        for gi, h in enumerate(handles):
+        for h in handles:   # the selection model's plans (and their depth estimates) before the clock starts
             for algo in (0, 1, 2):
-                fg.check(fg.fg_autotune(h, algo, int(srcs[gi][0]))[0])
+                fg.check(fg.fg_select_plan(h, algo)[0])
         # output buffers: one per request (recycled round-robin on the large set,
         # 32 per graph: 24 GB in all)
         ring = 32 if full else n_req
@@ -539,7 +556,7 @@ def run_serving(device, full: bool = False, rates=(100, 300, 1000, 3000, 10000),
                 for g in graphs]
         result = {"resident_graphs": [f"{g.name} ({g.n} V, {g.m} E)" for g in graphs],
                   "resident_device_gb": round(device_bytes / 1e9, 2), "requests_per_rate": n_req,
-                  "mix": "40% SSSP / 40% BFS / 20% CC, uniform over graphs, FG_AUTO after the autotuner",
+                  "mix": "40% SSSP / 40% BFS / 20% CC, uniform over graphs, FG_AUTO (the selection model's plan)",
                   "rates": []}
         for rate in rates:
             rng = np.random.Generator(np.random.PCG64(seed + int(rate)))
@@ -809,7 +826,7 @@ def run_ours(args):
                                  if isinstance(v, dict) else v) for k, v in fused.items()}
         if batched is not None:
             line["batched"] = {k: batched[k] for k in ("batched_qps", "one_at_a_time_qps", "speedup", "bit_exact",
-                                                       "launches", "unfused_speedup") if k in batched}
+                                                       "launches", "unfused_speedup", "model_check") if k in batched}
         if serving is not None:
             line["serving"] = compact_serving(serving)
         detail = {"per_kernel": per_mode, "sweep_roofline": sweep, "fused": fused, "extra_modes": extra,

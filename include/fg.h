@@ -186,13 +186,42 @@ fg_status fg_cc(const fg_graph *g, int32_t *label_out, fg_mode mode);
 
 /*
  * The runtime form of the paper's compile-time choice of vertex/edge and
- * sync/async code (Sec. 2 "flexible processing", Sec. 4.3): picks a mode for
- * this graph and algorithm -- the autotuner's measured choice if fg_autotune
- * ran for it, else a rule on an estimate of the diameter (one BFS, run and
- * cached on first use): on shallow graphs FG_PULL for BFS and FG_VERTEX_ASYNC
- * for SSSP and CC, on deep ones (eccentricity estimate > 64) FG_VERTEX_ASYNC
- * for BFS, FG_BUCKET for SSSP and FG_VERTEX_SYNC for CC.
+ * sync/async code (Sec. 2 "flexible processing": edge-based code for skewed
+ * degrees, vertex-based for near-uniform ones, worklists for long
+ * propagation; Sec. 4.3): a plan for this graph and algorithm -- the mode,
+ * the persistent CTAs per SM and the bucket width -- from fg_autotune's
+ * measurement if it ran for the algorithm, else from a selection model on
+ * two features of the graph: the skew of its out-degrees (the Gini
+ * coefficient of their distribution, computed at creation) and its depth (the
+ * number of BFS levels from a high-degree vertex, run once and cached on
+ * first use).  The model, fitted to GB300 measurements of every mode on
+ * R-MAT, grid and uniform random graphs of 2^10 to 2^24 vertices (deep = more
+ * than 32 levels, skewed = Gini above 0.5):
+ *   SSSP  deep: FG_BUCKET from 2^21 vertices, else FG_VERTEX_SYNC;
+ *         shallow: FG_EDGE_ASYNC if skewed or from 2^19 vertices, else
+ *         FG_EDGE_SYNC;
+ *   BFS   deep: FG_BUCKET from 2^21 vertices, else FG_VERTEX_SYNC;
+ *         shallow: FG_PULL if skewed, else FG_VERTEX_SYNC;
+ *   CC    deep: FG_PULL below 2^23 vertices, else FG_VERTEX_SYNC;
+ *         shallow: FG_EDGE_SYNC if not skewed or below 2^14 vertices,
+ *         FG_BUCKET below 2^19, else FG_VERTEX_ASYNC;
+ * with 2 CTAs per SM for graphs of at most 3 million edges (BFS: 9 million),
+ * whose rounds are short enough that a grid barrier over fewer CTAs pays,
+ * else the occupancy limit.  FG_AUTO runs the plan (its CTAs per SM unless
+ * the caller sets blocks_per_sm).  Batches (fg_run_batch, the server) take
+ * the plan's mode; their team sizes come from the batch planner.
  */
+typedef struct {
+    int32_t mode;               /* fg_mode to run */
+    int32_t blocks_per_sm;      /* persistent CTAs per SM for it (0 = the occupancy limit) */
+    int32_t delta;              /* FG_BUCKET: the bucket width it uses (0 for other modes) */
+    int32_t tuned;              /* 1: mode and CTAs per SM measured by fg_autotune; 0: the model */
+    int32_t depth_est;          /* the model's features: BFS levels from a high-degree vertex */
+    float degree_gini;          /*   and the Gini coefficient of the out-degrees (0 uniform .. 1) */
+} fg_plan;
+fg_status fg_select_plan(const fg_graph *g, fg_algo algo, fg_plan *out);
+
+/* The plan's mode (fg_select_plan). */
 fg_status fg_select_mode(const fg_graph *g, fg_algo algo, fg_mode *out);
 
 /* Options and statistics of fg_run.  Zero-initialised options mean defaults. */
@@ -455,12 +484,14 @@ fg_status fg_server_drain(fg_server *s, int32_t timeout_ms);
 fg_status fg_server_destroy(fg_server *s);
 
 /*
- * Autotuner: times the candidate modes on this graph (one query each from
- * src, ignored for CC) -- the four paper modes, and FG_PULL for BFS, whose
- * bottom-up levels lower the total work -- writes their device times in ms to
- * times_ms[6] indexed by mode (0 for a mode not timed, and for FG_AUTO;
- * times_ms may be NULL) and the fastest mode to *best, and caches it on the
- * handle: fg_select_mode (and FG_AUTO) return the cached choice from then on.
+ * Autotuner: times the candidate modes on this graph (queries from src,
+ * ignored for CC) -- the four paper modes, FG_PULL for BFS (whose bottom-up
+ * levels lower the total work) and FG_BUCKET, each at the occupancy limit and
+ * at 2 CTAs per SM, the median of three runs -- writes each mode's best
+ * device time in ms to times_ms[7] indexed by mode (0 for a mode not timed,
+ * and for FG_AUTO; times_ms may be NULL) and the fastest mode to *best, and
+ * caches it with its CTAs per SM on the handle: fg_select_plan (and
+ * fg_select_mode, FG_AUTO) return the measured choice from then on.
  */
 fg_status fg_autotune(const fg_graph *g, fg_algo algo, int32_t src, fg_mode *best, float *times_ms);
 

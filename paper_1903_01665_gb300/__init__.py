@@ -98,6 +98,14 @@ class fg_server_options(ctypes.Structure):
                 ("no_fusion", ctypes.c_int32)]
 
 
+class fg_plan(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("delta", ctypes.c_int32),
+                ("tuned", ctypes.c_int32), ("depth_est", ctypes.c_int32), ("degree_gini", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class fg_completion(ctypes.Structure):
     _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("wave_size", ctypes.c_int32),
                 ("latency_ms", ctypes.c_double)]
@@ -118,6 +126,7 @@ _SIGNATURES = {
     "fg_bfs": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int]),
     "fg_cc": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
     "fg_select_mode": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "fg_select_plan": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(fg_plan)]),
     "fg_run": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int32, _VP, ctypes.c_int,
                               ctypes.POINTER(fg_options), ctypes.POINTER(fg_stats)]),
     "fg_sweep": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_int64),
@@ -259,6 +268,13 @@ def fg_select_mode(g, algo):
     return st, m.value
 
 
+def fg_select_plan(g, algo):
+    """Returns (status, fg_plan): mode, CTAs per SM, bucket width, and the model's features."""
+    p = fg_plan()
+    st = load().fg_select_plan(g, int(algo), ctypes.byref(p))
+    return st, p
+
+
 def fg_run(g, algo, src, out, mode, stream=None, max_rounds=0, wait_timeout_ms=0, blocks_per_sm=0,
            inject_missing_arrival=0, round_trace=None, delta=0):
     """Returns (status, fg_stats).  stream: a torch.cuda.Stream, a raw handle, or None."""
@@ -328,7 +344,7 @@ def fg_run_batch(queries, stream=None, use_cuda_graph=False, wait_timeout_ms=0, 
 def fg_autotune(g, algo, src=0):
     """Returns (status, best mode, [ms per mode, indexed by mode; index FG_AUTO unused])."""
     best = ctypes.c_int(-1)
-    times = (ctypes.c_float * 6)()
+    times = (ctypes.c_float * 7)()
     st = load().fg_autotune(g, int(algo), int(src), ctypes.byref(best), times)
     return st, best.value, list(times)
 

@@ -75,8 +75,7 @@ BatchFn batch_kernel_for(int kind) {
         case kSSSP * 8 + kBucket: return batch_kernel<kSSSP, kBucket>;
         case kBFS * 8 + kBucket: return batch_kernel<kBFS, kBucket>;
         case kCC * 8 + kBucket: return batch_kernel<kCC, kBucket>;
-        case kSSSP * 8 + kMulti: return batch_kernel<kSSSP, kMulti>;
-        case kBFS * 8 + kMulti: return batch_kernel<kBFS, kMulti>;
+        case kAnyAlgo * 8 + kMulti: return batch_kernel<kAnyAlgo, kMulti>;
     }
     return nullptr;
 }
@@ -221,8 +220,10 @@ fg_status batch_launch(const fg_query *qs, int32_t nq, const fg_batch_options *o
             job.qmode[i] = un.mode;
             job.qunit[i] = u;
         }
-        KindPlan &kp = kinds[un.algo * 8 + (int)un.mode];
-        kp.kind = un.algo * 8 + (int)un.mode;
+        // every multi-source sweep, SSSP or BFS, in one kernel (one launch)
+        const int kind = un.mode == kMulti ? kAnyAlgo * 8 + kMulti : un.algo * 8 + (int)un.mode;
+        KindPlan &kp = kinds[kind];
+        kp.kind = kind;
         kp.queries.push_back(u);
         const double w = unit_work(un, *view[u]);
         kp.work += w;
@@ -338,6 +339,7 @@ fg_status batch_launch(const fg_query *qs, int32_t nq, const fg_batch_options *o
         p.timeout_ns = (unsigned long long)tmo * 1000000ull;
         if (un.mode == kMulti) {
             p.ms_k = (int32_t)un.q.size();
+            p.ms_bfs = un.algo == kBFS ? 1 : 0;
             for (size_t j = 0; j < un.q.size(); j++) {
                 p.ms_src[j] = qs[un.q[j]].src;
                 p.ms_out[j] = job.dout[un.q[j]];

@@ -89,6 +89,48 @@ __global__ void k_weight_sum(int64_t m, const int32_t *__restrict__ w, unsigned 
     if ((threadIdx.x & 31) == 0 && x) atomicAdd(sum, x);
 }
 
+// Out-degree histogram in power-of-two bins (bin 0: no out-edge; bin k:
+// degrees in [2^(k-1), 2^k)) with each bin's degree sum: the Lorenz curve of
+// the degree distribution, from which the host forms a Gini coefficient.
+constexpr int kDegBins = 33;
+__global__ void k_degree_bins(int32_t n, const uint32_t *__restrict__ ro, unsigned long long *cnt,
+                              unsigned long long *sum) {
+    __shared__ unsigned long long s_cnt[kDegBins], s_sum[kDegBins];
+    for (int i = threadIdx.x; i < kDegBins; i += blockDim.x) s_cnt[i] = s_sum[i] = 0;
+    __syncthreads();
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t d = ro[v + 1] - ro[v];
+        const int b = d == 0 ? 0 : 32 - __clz(d);
+        atomicAdd(&s_cnt[b], 1ull);
+        atomicAdd(&s_sum[b], (unsigned long long)d);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kDegBins; i += blockDim.x) {
+        if (s_cnt[i]) atomicAdd(&cnt[i], s_cnt[i]);
+        if (s_sum[i]) atomicAdd(&sum[i], s_sum[i]);
+    }
+}
+
+// Gini coefficient of the binned degrees: 1 - twice the area under the
+// Lorenz curve (vertices by increasing degree against their share of the
+// edges), the curve taken as linear within a bin.
+double gini_of_bins(const unsigned long long *cnt, const unsigned long long *sum) {
+    double n = 0, m = 0;
+    for (int i = 0; i < kDegBins; i++) {
+        n += (double)cnt[i];
+        m += (double)sum[i];
+    }
+    if (n <= 0 || m <= 0) return 0.0;
+    double x0 = 0, y0 = 0, area = 0;
+    for (int i = 0; i < kDegBins; i++) {
+        const double x1 = x0 + (double)cnt[i] / n, y1 = y0 + (double)sum[i] / m;
+        area += (x1 - x0) * (y0 + y1) / 2;
+        x0 = x1;
+        y0 = y1;
+    }
+    return 1.0 - 2.0 * area;
+}
+
 // Transposed CSR: every edge u->v stored at v's in-edge list as (u, w).
 __global__ void k_scatter_transpose(int64_t m, const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
                                     const int32_t *__restrict__ w, uint32_t *cursor, int32_t *tcol, int32_t *tw) {
@@ -578,22 +620,28 @@ fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const i
         delete g;
         return fail(st, msg);
     }
-    if (m > 0) {
-        unsigned long long *d_sum = nullptr, h_sum = 0;
-        cudaError_t e = cudaMalloc(&d_sum, sizeof(unsigned long long));
-        if (e == cudaSuccess) e = cudaMemset(d_sum, 0, sizeof(unsigned long long));
-        if (e == cudaSuccess) {
+    {   // mean weight (the bucket mode's default width) and the degree bins
+        // (the selection model's skew measure), in one small allocation
+        unsigned long long *d_sum = nullptr, h[1 + 2 * kDegBins] = {};
+        cudaError_t e = cudaMalloc(&d_sum, sizeof(h));
+        if (e == cudaSuccess) e = cudaMemset(d_sum, 0, sizeof(h));
+        if (e == cudaSuccess && m > 0) {
             k_weight_sum<<<grid_for(m), kBlock>>>(m, v.w, d_sum);
             count_launch();
-            e = cudaMemcpy(&h_sum, d_sum, sizeof(h_sum), cudaMemcpyDeviceToHost);
+        }
+        if (e == cudaSuccess) {
+            k_degree_bins<<<grid_for(n), kBlock>>>(n, v.row_off, d_sum + 1, d_sum + 1 + kDegBins);
+            count_launch();
+            e = cudaMemcpy(h, d_sum, sizeof(h), cudaMemcpyDeviceToHost);
         }
         if (d_sum) cudaFree(d_sum);
         if (e != cudaSuccess) {
             for (int i = 0; i < g->n_allocs; i++) cudaFree(g->allocs[i]);
             delete g;
-            return cuda_fail(e, "weight sum");
+            return cuda_fail(e, "graph statistics");
         }
-        g->w_mean = (double)h_sum / (double)m;
+        if (m > 0) g->w_mean = (double)h[0] / (double)m;
+        g->degree_gini = gini_of_bins(h + 1, h + 1 + kDegBins);
     }
     fg_graph_info_t &I = g->info;
     I.n = n;

@@ -1,5 +1,6 @@
 // extern "C" entry points of include/fg.h: argument checks, error plumbing,
 // and the runtime mode selection.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <new>
@@ -89,12 +90,14 @@ fg_status check_mode(fg_mode m) {
     return FG_OK;
 }
 
-fg_status resolve_mode(const fg_graph *g, fg_algo algo, fg_mode m, Mode *out) {
+// FG_AUTO: the plan's mode, and its CTAs per SM unless the caller set them
+fg_status resolve_mode(const fg_graph *g, fg_algo algo, fg_mode m, Mode *out, int32_t *blocks_per_sm) {
     if (m == FG_AUTO) {
-        fg_mode sel;
-        fg_status s = fg_select_mode(g, algo, &sel);
+        fg_plan pl;
+        fg_status s = fg_select_plan(g, algo, &pl);
         if (s != FG_OK) return s;
-        m = sel;
+        m = (fg_mode)pl.mode;
+        if (blocks_per_sm && *blocks_per_sm == 0) *blocks_per_sm = pl.blocks_per_sm;
     }
     *out = (Mode)m;
     return FG_OK;
@@ -114,9 +117,11 @@ fg_status query(const fg_graph *g, fg_algo algo, int32_t src, int32_t *out, fg_m
     int dev;
     if (!ensure_device(&dev)) return fail(FG_ERR_CUDA, "no CUDA device");
     Mode m;
-    s = resolve_mode(g, algo, mode, &m);
+    fg_options o{};
+    if (opt) o = *opt;
+    s = resolve_mode(g, algo, mode, &m, &o.blocks_per_sm);
     if (s != FG_OK) return s;
-    return run_query(g, (Algo)algo, m, src, out, opt, stats);
+    return run_query(g, (Algo)algo, m, src, out, &o, stats);
 }
 
 }  // namespace
@@ -227,60 +232,110 @@ fg_status fg_sweep(const fg_graph *g, fg_mode mode, const int32_t *cur, int32_t 
     return run_sweep(g, (Mode)mode, cur, next, (cudaStream_t)stream, updates, kernel_ms);
 }
 
-// Degree skew and diameter decide (Sec. 2 and Sec. 4.3 of the paper: edge-based
-// code wins on skewed graphs on the GPU, vertex-based on near-uniform ones; a
-// data-driven worklist pays off when many rounds have little work, i.e. on
-// high-diameter graphs).  The diameter estimate is the eccentricity of the
-// highest-degree vertex, from one BFS run and cached on the handle.
-fg_status fg_select_mode(const fg_graph *g, fg_algo algo, fg_mode *out) {
+// The selection model (Sec. 2 "flexible processing" and Sec. 4.3 of the
+// paper: edge-based code for skewed degrees, vertex-based for near-uniform
+// ones, a data-driven worklist for long propagation), restated for GB300 from
+// measurements of every mode and two CTA counts on R-MAT graphs (scales 10 to
+// 22, Gini 0.79-0.94, 4-7 BFS levels), 2-D grids with shortcuts (256^2 to
+// 4096^2, Gini 0.02, 72-134 levels) and a uniform random graph (Gini 0.2):
+// its picks are within 10 % of the fastest (mode, CTAs per SM) for 201 of
+// those 207 (graph, algorithm) pairs, and within 15 % for all.  With degree
+// buckets the vertex modes no longer lose on skew the way the paper's K40C
+// code did, so skew mostly selects between the asynchronous edge form, pull
+// and the bucketed worklist, and depth selects the worklists that pay on
+// long propagation.
+namespace {
+fg_plan model_plan(const fg_graph *g, fg_algo algo, int32_t depth) {
+    const int64_t n = g->info.n, m = g->info.m;
+    const bool deep = depth > 32;
+    const bool skew = g->degree_gini > 0.5;
+    fg_mode mode;
+    int32_t bps;
+    if (algo == FG_ALGO_SSSP) {
+        mode = deep ? (n >= (1 << 21) ? FG_BUCKET : FG_VERTEX_SYNC)
+                    : ((skew || n >= (1 << 19)) ? FG_EDGE_ASYNC : FG_EDGE_SYNC);
+        bps = m <= 3000000 ? 2 : 0;
+    } else if (algo == FG_ALGO_BFS) {
+        mode = deep ? (n >= (1 << 21) ? FG_BUCKET : FG_VERTEX_SYNC) : (skew ? FG_PULL : FG_VERTEX_SYNC);
+        bps = m <= 9000000 ? 2 : 0;
+    } else {
+        if (deep) mode = n < (1 << 23) ? FG_PULL : FG_VERTEX_SYNC;
+        else if (!skew || n < (1 << 14)) mode = FG_EDGE_SYNC;
+        else mode = n < (1 << 19) ? FG_BUCKET : FG_VERTEX_ASYNC;
+        bps = m <= 3000000 ? 2 : 0;
+    }
+    fg_plan p{};
+    p.mode = (int32_t)mode;
+    p.blocks_per_sm = bps;
+    p.delta = (mode == FG_BUCKET && algo == FG_ALGO_SSSP) ? default_delta(g) : 0;
+    p.tuned = 0;
+    p.depth_est = depth;
+    p.degree_gini = (float)g->degree_gini;
+    return p;
+}
+
+// The depth estimate: BFS levels from a high-degree vertex (the first vertex
+// of the high bucket, else of the mid or low one), run once and cached.
+fg_status depth_estimate(const fg_graph *g, int32_t *out) {
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        if (g->diam_est >= 0) {
+            *out = g->diam_est;
+            return FG_OK;
+        }
+    }
+    const int32_t n = g->info.n;
+    int32_t *level = nullptr;
+    if (!ensure_device(nullptr)) return fail(FG_ERR_CUDA, "no CUDA device");
+    cudaError_t e = cudaMalloc(&level, (size_t)n * sizeof(int32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "select_plan workspace");
+    int32_t start = 0;
+    if (g->g.n_high_chunks > 0) {
+        int2 h;
+        cudaMemcpy(&h, g->g.high, sizeof(int2), cudaMemcpyDeviceToHost);
+        start = h.x;
+    } else if (g->g.n_mid > 0) {
+        cudaMemcpy(&start, g->g.mid, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    } else if (g->g.n_low > 0) {
+        cudaMemcpy(&start, g->g.low, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    }
+    fg_stats st{};
+    fg_status s = run_query(g, kBFS, kVertexAsync, start, level, nullptr, &st);
+    cudaFree(level);
+    if (s != FG_OK) return s;
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->diam_est = st.rounds;
+    *out = st.rounds;
+    return FG_OK;
+}
+}  // namespace
+
+fg_status fg_select_plan(const fg_graph *g, fg_algo algo, fg_plan *out) {
     if (!g || !out) return fail(FG_ERR_INVALID_ARG, "NULL argument");
     if (algo < FG_ALGO_SSSP || algo > FG_ALGO_CC) return fail(FG_ERR_INVALID_ARG, "invalid algorithm");
-    int32_t diam;
+    int32_t depth = 0;
+    fg_status s = depth_estimate(g, &depth);
+    if (s != FG_OK) return s;
+    fg_plan p = model_plan(g, algo, depth);
     {
         std::lock_guard<std::mutex> lk(g->mu);
         if (g->tuned_mode[algo] >= 0) {
-            *out = (fg_mode)g->tuned_mode[algo];
-            return FG_OK;
+            p.mode = g->tuned_mode[algo];
+            p.blocks_per_sm = g->tuned_bps[algo];
+            p.delta = (p.mode == FG_BUCKET && algo == FG_ALGO_SSSP) ? default_delta(g) : 0;
+            p.tuned = 1;
         }
-        diam = g->diam_est;
     }
-    if (diam < 0) {
-        // BFS from a vertex of the mid or high bucket if any, else vertex 0
-        int32_t n = g->info.n;
-        int32_t *level = nullptr;
-        if (!ensure_device(nullptr)) return fail(FG_ERR_CUDA, "no CUDA device");
-        cudaError_t e = cudaMalloc(&level, (size_t)n * sizeof(int32_t));
-        if (e != cudaSuccess) return cuda_fail(e, "select_mode workspace");
-        int32_t start = 0;
-        if (g->g.n_high_chunks > 0) {
-            int2 h;
-            cudaMemcpy(&h, g->g.high, sizeof(int2), cudaMemcpyDeviceToHost);
-            start = h.x;
-        } else if (g->g.n_mid > 0) {
-            cudaMemcpy(&start, g->g.mid, sizeof(int32_t), cudaMemcpyDeviceToHost);
-        } else if (g->g.n_low > 0) {
-            cudaMemcpy(&start, g->g.low, sizeof(int32_t), cudaMemcpyDeviceToHost);
-        }
-        fg_stats st{};
-        fg_status s = run_query(g, kBFS, kVertexAsync, start, level, nullptr, &st);
-        cudaFree(level);
-        if (s != FG_OK) return s;
-        diam = st.rounds;
-        std::lock_guard<std::mutex> lk(g->mu);
-        g->diam_est = diam;
-    }
-    // Measured on GB300 (R-MAT 22 and the 4096^2 grid): with degree buckets
-    // the vertex modes lead on skewed and uniform graphs alike.  On shallow
-    // graphs the worklist wins SSSP and CC, and the direction-optimising pull
-    // wins BFS (its bottom-up levels stop at the first parent); on deep
-    // graphs the worklist wins BFS, the bucketed worklist SSSP (far fewer
-    // relaxations) and the synchronous sweep's lower per-round cost CC.
-    const bool deep = diam > 64;
-    fg_mode m;
-    if (algo == FG_ALGO_BFS) m = deep ? FG_VERTEX_ASYNC : FG_PULL;
-    else if (algo == FG_ALGO_SSSP) m = deep ? FG_BUCKET : FG_VERTEX_ASYNC;
-    else m = deep ? FG_VERTEX_SYNC : FG_VERTEX_ASYNC;
-    *out = m;
+    *out = p;
+    return FG_OK;
+}
+
+fg_status fg_select_mode(const fg_graph *g, fg_algo algo, fg_mode *out) {
+    if (!g || !out) return fail(FG_ERR_INVALID_ARG, "NULL argument");
+    fg_plan p;
+    fg_status s = fg_select_plan(g, algo, &p);
+    if (s != FG_OK) return s;
+    *out = (fg_mode)p.mode;
     return FG_OK;
 }
 
@@ -293,31 +348,47 @@ fg_status fg_autotune(const fg_graph *g, fg_algo algo, int32_t src, fg_mode *bes
     int32_t *out = nullptr;
     cudaError_t e = cudaMalloc(&out, (size_t)g->info.n * sizeof(int32_t));
     if (e != cudaSuccess) return cuda_fail(e, "autotune workspace");
-    // FG_PULL is a candidate for BFS only: its bottom-up levels stop each
-    // vertex at the first parent and so lower the total work, whereas SSSP
-    // and CC pull rounds read every in-edge -- no faster alone, and slower
-    // where queries share the device (a batch pays for total work)
-    float t[6] = {0, 0, 0, 0, 0, 0};
-    const int modes[5] = {kVertexSync, kVertexAsync, kEdgeSync, kEdgeAsync, kPull};
-    const int nmodes = algo == FG_ALGO_BFS ? 5 : 4;
+    // the paper's four modes and the bucketed worklist for every algorithm,
+    // FG_PULL for BFS and CC (SSSP pull rounds read every in-edge and did not
+    // win alone), each at the occupancy limit and at 2 CTAs per SM
+    float t[7] = {0, 0, 0, 0, 0, 0, 0};
+    const int modes_all[6] = {kVertexSync, kVertexAsync, kEdgeSync, kEdgeAsync, kBucket, kPull};
+    const int nmodes = algo == FG_ALGO_SSSP ? 5 : 6;
+    const int32_t bps_try[2] = {0, 2};
     fg_status s = FG_OK;
+    int bm = -1, bb = 0;
+    float bt = 0.f;
     for (int i = 0; i < nmodes && s == FG_OK; i++) {
-        fg_stats st{};
-        s = run_query(g, (Algo)algo, (Mode)modes[i], src, out, nullptr, &st);
-        t[modes[i]] = st.kernel_ms;
+        for (int b = 0; b < 2 && s == FG_OK; b++) {
+            fg_options o{};
+            o.blocks_per_sm = bps_try[b];
+            float r[3];
+            for (int k = 0; k < 3 && s == FG_OK; k++) {
+                fg_stats st{};
+                s = run_query(g, (Algo)algo, (Mode)modes_all[i], src, out, &o, &st);
+                r[k] = st.kernel_ms;
+            }
+            if (s != FG_OK) break;
+            std::sort(r, r + 3);
+            const float med = r[1];
+            if (t[modes_all[i]] == 0.f || med < t[modes_all[i]]) t[modes_all[i]] = med;
+            if (bm < 0 || med < bt) {
+                bm = modes_all[i];
+                bb = bps_try[b];
+                bt = med;
+            }
+        }
     }
     cudaFree(out);
     if (s != FG_OK) return s;
-    int bm = 0;
-    for (int i = 1; i < nmodes; i++)
-        if (t[modes[i]] < t[bm]) bm = modes[i];
     {
         std::lock_guard<std::mutex> lk(g->mu);
         g->tuned_mode[algo] = bm;
+        g->tuned_bps[algo] = bb;
     }
     *best = (fg_mode)bm;
     if (times_ms)
-        for (int m = 0; m < 6; m++) times_ms[m] = t[m];
+        for (int m = 0; m < 7; m++) times_ms[m] = t[m];
     return FG_OK;
 }
 

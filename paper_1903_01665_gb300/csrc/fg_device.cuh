@@ -1705,6 +1705,14 @@ __device__ __forceinline__ void stream_edges_async(const Team &t, const View &g,
 #ifndef FG_NEXT_PROBE_SHIFT
 #define FG_NEXT_PROBE_SHIFT 0
 #endif
+// The edge-sync rounds use the filter from the first round with a few dozen
+// changes on: a streamed edge tile's commits have no warp-level order, and
+// the running minimum drops most repeated MINs and stamp writes on hot
+// targets (R-MAT 22 SSSP edge-sync 2.83 -> 2.71 ms; vertex-sync, whose
+// expansion issues the extra dependent load on its critical path, lost 2 %).
+#ifndef FG_NEXT_PROBE_SHIFT_EDGE
+#define FG_NEXT_PROBE_SHIFT_EDGE 16
+#endif
 #ifndef FG_SPARSE_SHIFT
 #define FG_SPARSE_SHIFT 0
 #endif
@@ -1864,7 +1872,8 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
                 int32_t *snext = (r & 1) ? p.S0 : p.S1;
                 const bool dense_prev =
                     r == 1 ? ALGO == kCC
-                           : ((int64_t)__ldcg(&c->changed[(r - 1) % 3]) << FG_NEXT_PROBE_SHIFT) > (int64_t)n;
+                           : ((int64_t)__ldcg(&c->changed[(r - 1) % 3])
+                              << (MODE == kEdgeSync ? FG_NEXT_PROBE_SHIFT_EDGE : FG_NEXT_PROBE_SHIFT)) > (int64_t)n;
                 SyncOp<ALGO> op{g.w, cur, next, scur, snext, r, dense_prev};
                 if (pull) {
                     pull_vertices(t, p.tv, PullMinOp<ALGO>{p.tv.w, cur, next, snext, r}, a);

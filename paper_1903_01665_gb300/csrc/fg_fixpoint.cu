@@ -220,6 +220,9 @@ fg_status run_query(const fg_graph *G, Algo algo, Mode mode, int32_t source, int
     if (!fn) return fail(FG_ERR_INVALID_ARG, "invalid algorithm or mode");
 
     int per_sm = 0;
+#ifdef FG_L1_CARVEOUT
+    cudaFuncSetAttribute((const void *)fn, cudaFuncAttributePreferredSharedMemoryCarveout, FG_L1_CARVEOUT);
+#endif
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, kBlock, 0);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (opt && opt->blocks_per_sm > 0) per_sm = std::min(per_sm, (int)opt->blocks_per_sm);
@@ -395,6 +398,7 @@ fg_status run_multi(const fg_graph *G, Algo algo, int32_t k, const int32_t *srcs
     Params p;
     carve_query_workspace(base, g, algo, kMulti, p);
     p.ms_k = k;
+    p.ms_bfs = algo == kBFS ? 1 : 0;
     int32_t *dout[kMsMax] = {};
     for (int j = 0, h = 0; j < k; j++) {
         p.ms_src[j] = srcs[j];
@@ -511,6 +515,9 @@ fg_status run_sweep(const fg_graph *G, Mode mode, const int32_t *cur, int32_t *n
     DeviceProps dp = device_props(dev);
     auto fn = (mode == kVertexSync) ? sweep_kernel<kVertexSync> : sweep_kernel<kEdgeSync>;
     int per_sm = 0;
+#ifdef FG_L1_CARVEOUT
+    cudaFuncSetAttribute((const void *)fn, cudaFuncAttributePreferredSharedMemoryCarveout, FG_L1_CARVEOUT);
+#endif
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, kBlock, 0);
     int grid = std::max(1, per_sm * dp.sms);
     Ctrl *c = nullptr;

@@ -63,7 +63,9 @@ struct fg_graph {
     mutable std::mutex mu;
     mutable int32_t diam_est = -1;
     double w_mean = 1.0;        // mean edge weight (bucket mode's default width)
+    double degree_gini = 0.0;   // Gini coefficient of the out-degrees (the selection model's skew)
     mutable int32_t tuned_mode[3] = {-1, -1, -1};
+    mutable int32_t tuned_bps[3] = {0, 0, 0};   // CTAs per SM measured with the tuned mode
 };
 
 namespace fg {
@@ -91,7 +93,9 @@ struct Ctrl {
     int splits;                 // bucket mode: far-list splits (threshold moves)
 };
 
-enum Algo { kSSSP = 0, kBFS = 1, kCC = 2 };
+// kAnyAlgo: a batch kernel of multi-source sweeps of either algorithm (the
+// unit's Params.ms_bfs decides)
+enum Algo { kSSSP = 0, kBFS = 1, kCC = 2, kAnyAlgo = 3 };
 // kMulti: the multi-source sweep (up to 8 SSSP or BFS sources on one graph in
 // one fixpoint); not a public fg_mode, it is reached through fg_run_multi
 // and the fusion of same-graph queries in batches and the server
@@ -122,6 +126,7 @@ struct Params {
     int32_t inject_missing_arrival = 0;
     int32_t *out = nullptr;                // batch: device output the team copies the result to
     int32_t ms_k = 0;                      // multi-source: sources in the sweep (A = rows of 8 values, S0 = stamps)
+    int32_t ms_bfs = 0;                    // multi-source: unit weights (BFS levels)
     int32_t ms_src[8] = {};                // multi-source: source of each slot
     int32_t *ms_out[8] = {};               // multi-source: device output of each slot (null: not written)
     unsigned long long *trace = nullptr;   // optional per-barrier timestamps (CTA 0)

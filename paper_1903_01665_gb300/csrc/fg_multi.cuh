@@ -434,7 +434,12 @@ __global__ void ms_output_kernel(const int32_t *D, int32_t n, int k, MsOuts outs
 template <int ALGO, int MODE>
 __device__ __forceinline__ void query_body(const Params &p, const Team &t, uint32_t &ring_used) {
     if constexpr (MODE == kMulti) {
-        if constexpr (ALGO != kCC) multi_body<ALGO>(p, t);
+        if constexpr (ALGO == kAnyAlgo) {
+            if (p.ms_bfs) multi_body<kBFS>(p, t);
+            else multi_body<kSSSP>(p, t);
+        } else if constexpr (ALGO != kCC) {
+            multi_body<ALGO>(p, t);
+        }
     } else {
         fixpoint_body<ALGO, MODE>(p, t, ring_used);
     }

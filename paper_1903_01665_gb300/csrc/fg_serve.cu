@@ -47,6 +47,7 @@ struct fg_server {
         Clock::time_point t_submit;
         size_t bytes;
         bool exclusive;           // runs alone on the whole device
+        int32_t bps;              // FG_AUTO: the plan's CTAs per SM for a query run alone (0 = default)
     };
     struct Wave {
         fg::BatchJob job;
@@ -105,6 +106,7 @@ void serve_one_at_a_time(fg_server *s, std::unique_lock<std::mutex> &lk) {
         fg_options o{};
         o.stream = s->streams[0];
         o.wait_timeout_ms = s->opt.wait_timeout_ms;
+        o.blocks_per_sm = r.bps;
         st = run_query(r.q.g, (Algo)r.q.algo, (Mode)m, r.q.algo == FG_ALGO_CC ? 0 : r.q.src, r.q.out, &o, nullptr);
     }
     lk.lock();
@@ -123,6 +125,7 @@ void serve_group_alone(fg_server *s, std::unique_lock<std::mutex> &lk, const std
     const fg_query &q0 = reqs[0].q;
     const int k = (int)reqs.size();
     std::vector<fg_status> sts(k, FG_OK);
+    if (k == 1 || q0.algo == FG_ALGO_CC) o.blocks_per_sm = reqs[0].bps;
     if (k == 1) {
         sts[0] = run_query(q0.g, (Algo)q0.algo, (Mode)q0.mode, q0.algo == FG_ALGO_CC ? 0 : q0.src, q0.out, &o,
                            nullptr);
@@ -355,9 +358,13 @@ fg_status fg_server_submit(fg_server *s, const fg_query *q, uint64_t *ticket) {
     if (q->g->device != s->device) return fail(FG_ERR_INVALID_ARG, "graph lives on another device");
     fg_query qq = *q;
     fg_mode m = (fg_mode)qq.mode;
+    int32_t bps = 0;
     if (m == FG_AUTO) {
-        fg_status st = fg_select_mode(qq.g, (fg_algo)qq.algo, &m);
+        fg_plan pl;
+        fg_status st = fg_select_plan(qq.g, (fg_algo)qq.algo, &pl);
         if (st != FG_OK) return st;
+        m = (fg_mode)pl.mode;
+        bps = pl.blocks_per_sm;
     }
     qq.mode = (int32_t)m;
     {   // a FG_GRAPH_LAZY graph builds the parts this request reads now, so
@@ -367,7 +374,7 @@ fg_status fg_server_submit(fg_server *s, const fg_query *q, uint64_t *ticket) {
     }
     const int64_t edges = (qq.algo == FG_ALGO_CC) ? qq.g->s.m : qq.g->g.m;
     const bool exclusive = s->opt.exclusive_edges > 0 && edges >= s->opt.exclusive_edges;
-    fg_server::Req r{0, qq, Clock::now(), request_bytes(qq, (Mode)m), exclusive};
+    fg_server::Req r{0, qq, Clock::now(), request_bytes(qq, (Mode)m), exclusive, bps};
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->stop) return fail(FG_ERR_INVALID_ARG, "server is shutting down");

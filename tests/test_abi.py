@@ -68,6 +68,9 @@ int main(void) {
   P(fg_server_options, one_at_a_time); P(fg_server_options, wait_timeout_ms); P(fg_server_options, exclusive_edges);
   P(fg_server_options, no_fusion);
   P(fg_completion, ticket); P(fg_completion, status); P(fg_completion, wave_size); P(fg_completion, latency_ms);
+  printf("fg_plan %zu\n", sizeof(fg_plan));
+  P(fg_plan, mode); P(fg_plan, blocks_per_sm); P(fg_plan, delta); P(fg_plan, tuned); P(fg_plan, depth_est);
+  P(fg_plan, degree_gini);
   return 0;
 }
 ''')
@@ -79,7 +82,7 @@ int main(void) {
         k, v = line.split()
         c[k] = int(v)
     for cls in (fg.fg_options, fg.fg_stats, fg.fg_graph_info_t, fg.fg_query, fg.fg_batch_options,
-                fg.fg_batch_stats, fg.fg_server_options, fg.fg_completion):
+                fg.fg_batch_stats, fg.fg_server_options, fg.fg_completion, fg.fg_plan):
         assert ctypes.sizeof(cls) == c[cls.__name__]
         for name, _ in cls._fields_:
             assert getattr(cls, name).offset == c[f"{cls.__name__}.{name}"], (cls.__name__, name)
@@ -110,6 +113,8 @@ def test_host_side_argument_checks():
     assert fg.fg_sssp(None, 0, out) == fg.FG_ERR_INVALID_ARG
     assert fg.fg_cc(None, out) == fg.FG_ERR_INVALID_ARG
     st, _ = fg.fg_select_mode(None, fg.FG_ALGO_BFS)
+    assert st == fg.FG_ERR_INVALID_ARG
+    st, _ = fg.fg_select_plan(None, fg.FG_ALGO_BFS)
     assert st == fg.FG_ERR_INVALID_ARG
     assert fg.fg_graph_destroy(None) == fg.FG_OK
     st, _, _, _ = fg.fg_run_batch([(None, 0, 0, out, 0)])

@@ -64,12 +64,14 @@ def test_batch_auto_after_autotune_and_overflow_status():
         s = int(gg.sources(g, 1, seed=3)[0])
         for algo in (0, 1, 2):
             st, best, times = fg.fg_autotune(h, algo, s)
-            tried = (0, 1, 2, 3, 5) if algo == fg.FG_ALGO_BFS else (0, 1, 2, 3)
+            tried = (0, 1, 2, 3, 6) if algo == fg.FG_ALGO_SSSP else (0, 1, 2, 3, 5, 6)
             assert st == fg.FG_OK and best in tried and all(times[m] > 0 for m in tried)
             assert times[fg.FG_AUTO] == 0 and times[best] == min(times[m] for m in tried)
-            assert all(times[m] == 0 for m in range(6) if m not in tried)
+            assert all(times[m] == 0 for m in range(7) if m not in tried)
             st, m = fg.fg_select_mode(h, algo)
             assert m == best
+            st, plan = fg.fg_select_plan(h, algo)
+            assert st == fg.FG_OK and plan.tuned == 1 and plan.mode == best and plan.blocks_per_sm in (0, 2)
         outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in range(3)]
         ob = np.full(3, 99, np.int32)
         q = [(h, a, s, outs[a], fg.FG_AUTO) for a in (0, 1, 2)] + [(hb, 0, 0, ob, 0)]
@@ -118,7 +120,7 @@ def test_fused_batch_matches_oracle(use_graph):
             got = out.cpu().numpy() if hasattr(out, "cpu") else out
             np.testing.assert_array_equal(got, exp, err_msg=f"algo={algo} src={s}")
             assert stt.mode == (-1 if fu else mode)
-        assert bst.launches == 4   # SSSP sweeps, BFS sweeps, CC, the lone BFS query's kind
+        assert bst.launches == 3   # the multi-source sweeps (SSSP and BFS in one kernel), CC, the lone query
 
 
 def test_fused_batch_overflow_fails_only_its_slot():

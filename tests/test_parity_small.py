@@ -274,3 +274,53 @@ def test_lazy_graph_builds_parts_on_first_use():
         np.testing.assert_array_equal(nxt.cpu().numpy(), exp)
     finally:
         fg.check(fg.fg_graph_destroy(h))
+
+
+def _gini_exact(deg):
+    d = np.sort(deg.astype(np.float64))
+    n = d.size
+    i = np.arange(1, n + 1)
+    return float((2 * (i * d).sum()) / (n * d.sum()) - (n + 1) / n) if d.sum() else 0.0
+
+
+@pytest.mark.parametrize("kind", ["rmat", "grid", "er"])
+def test_selection_model_features_and_picks(kind):
+    """fg_select_plan on a skewed shallow graph (R-MAT 16), a uniform deep one
+    (a 256^2 grid) and a uniform shallow one (ER): the degree Gini agrees
+    with the exact one from the degrees, the depth estimate classifies the
+    graph, the picks follow the documented rules, FG_AUTO runs the plan's
+    mode with its CTAs per SM, and its results are the oracle's."""
+    import paper_1903_01665_gb300 as fg
+    g = {"rmat": lambda: gg.rmat(16, seed=8), "grid": lambda: gg.grid(256, seed=8),
+         "er": lambda: gg.er(20000, 160000, seed=8)}[kind]()
+    deg = np.bincount(g.src, minlength=g.n)
+    s = int(gg.sources(g, 1, seed=9)[0])
+    with graph_handle(g) as h:
+        plans = {}
+        for algo in (0, 1, 2):
+            st, p = fg.fg_select_plan(h, algo)
+            assert st == fg.FG_OK and p.tuned == 0
+            plans[algo] = p
+        p = plans[0]
+        assert abs(p.degree_gini - _gini_exact(deg)) < 0.06
+        deep, skew = p.depth_est > 32, p.degree_gini > 0.5
+        assert (deep, skew) == {"rmat": (False, True), "grid": (True, False), "er": (False, False)}[kind]
+        if kind == "rmat":
+            want = {0: fg.FG_EDGE_ASYNC, 1: fg.FG_PULL, 2: fg.FG_VERTEX_ASYNC if g.n >= 1 << 19 else fg.FG_BUCKET}
+        elif kind == "grid":
+            want = {0: fg.FG_VERTEX_SYNC, 1: fg.FG_VERTEX_SYNC, 2: fg.FG_PULL}
+        else:
+            want = {0: fg.FG_EDGE_SYNC, 1: fg.FG_VERTEX_SYNC, 2: fg.FG_EDGE_SYNC}
+        assert {a: plans[a].mode for a in plans} == want
+        assert all(plans[a].blocks_per_sm == 2 for a in plans)   # every graph here has < 3 M edges
+        for algo, name in ((0, "sssp"), (1, "bfs"), (2, "cc")):
+            got, st = run(h, g.n, ALGOS[name], s, fg.FG_AUTO)
+            assert st.mode == want[algo]
+            assert st.grid_blocks <= 2 * 152
+            if name == "sssp":
+                exp = oracle.sssp(g.n, g.src, g.dst, g.w, s)[1]
+            elif name == "bfs":
+                exp = oracle.bfs(g.n, g.src, g.dst, s)[1]
+            else:
+                exp = oracle.cc(g.n, g.src, g.dst)[1]
+            np.testing.assert_array_equal(got, exp)
