@@ -58,16 +58,20 @@ ALGO_NAMES = ["sssp", "bfs", "cc"]
 # at capture time).
 NCU_TRAFFIC: dict = {
     # profiles/sssp_rmat22_traffic.md: one launch each, first seeded source, R-MAT 22
-    "fixpoint_kernel<sssp,vertex_sync>": {"bytes_per_launch": 4246407936 + 546715392, "src_sha": "14303aa67d8410ae"},
-    "fixpoint_kernel<sssp,vertex_async>": {"bytes_per_launch": 2702572800 + 201716224, "src_sha": "14303aa67d8410ae"},
-    "fixpoint_kernel<sssp,edge_sync>": {"bytes_per_launch": 5307464192 + 201518592, "src_sha": "14303aa67d8410ae"},
-    "fixpoint_kernel<sssp,edge_async>": {"bytes_per_launch": 4287900416 + 246216448, "src_sha": "14303aa67d8410ae"},
+    "fixpoint_kernel<sssp,vertex_sync>": {"bytes_per_launch": 4248252672 + 547456000, "src_sha": "f6a823493813f9a6"},
+    "fixpoint_kernel<sssp,vertex_async>": {"bytes_per_launch": 2705021952 + 202434816, "src_sha": "f6a823493813f9a6"},
+    "fixpoint_kernel<sssp,edge_sync>": {"bytes_per_launch": 5180406528 + 161949696, "src_sha": "f6a823493813f9a6"},
+    "fixpoint_kernel<sssp,edge_async>": {"bytes_per_launch": 4268786176 + 244483584, "src_sha": "f6a823493813f9a6"},
 }
 
 
 # DRAM bytes of one all-active sweep launch (R-MAT 22, the sweep roofline
 # state), same validity rule
-NCU_SWEEP_DRAM: dict = {}
+NCU_SWEEP_DRAM: dict = {
+    # profiles/sweep_rmat22.md: the sweep roofline state on R-MAT 22, one launch each
+    "vertex_sync": {"bytes": 670645504 + 12172544, "src_sha": "f6a823493813f9a6"},
+    "edge_sync": {"bytes": 837081088 + 5563904, "src_sha": "f6a823493813f9a6"},
+}
 
 KERNEL_SOURCES = ("fg_internal.cuh", "fg_device.cuh", "fg_fixpoint.cu")
 
@@ -931,7 +935,7 @@ def run_case(args):
     import torch
     import paper_1903_01665_gb300 as fg
     algo_name, mode_name = args.case.split(":")
-    mode = {v: k for k, v in MODE_NAMES.items()}[mode_name]
+    mode = {v: k for k, v in MODE_NAMES.items()}.get(mode_name, -1)
     if args.case_graph == "rmat":
         g = gg.rmat(args.case_scale)
     else:
@@ -957,6 +961,17 @@ def run_case(args):
             print(i, json.dumps({"writes": upd, "kernel_ms": ms}), flush=True)
         fg.check(fg.fg_graph_destroy(h))
         return
+    if mode_name == "multi":
+        # the multi-source sweep of the 8 seeded sources
+        algo = ALGO_NAMES.index(algo_name)
+        srcs = [int(x) for x in gg.sources(g, 8)]
+        outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in srcs]
+        for i in range(2):
+            st, sts, stats = fg.fg_run_multi(h, algo, srcs, outs)
+            fg.check(st)
+            print(i, json.dumps(stats.as_dict()), flush=True)
+        fg.check(fg.fg_graph_destroy(h))
+        return
     algo = ALGO_NAMES.index(algo_name)
     out = torch.empty(g.n, dtype=torch.int32, device="cuda")
     for i in range(2):
@@ -968,7 +983,8 @@ def run_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default=None, help="profiling driver, e.g. sssp:edge_sync or sweep:edge_sync")
+    ap.add_argument("--case", default=None,
+                    help="profiling driver, e.g. sssp:edge_sync, sweep:edge_sync or sssp:multi (8-source sweep)")
     ap.add_argument("--case-graph", default="rmat", choices=["rmat", "grid"])
     ap.add_argument("--case-scale", type=int, default=20, help="R-MAT scale or grid side")
     ap.add_argument("--gpus", type=int, default=1)
