@@ -141,7 +141,10 @@ __device__ __forceinline__ void ms_relax_one_source(const View &g, int32_t *D, i
     }
 }
 
-constexpr int kMsU = 2;   // edges per lane per step (each with two 16-byte row loads in flight)
+#ifndef FG_MULTI_EDGES_PER_LANE
+#define FG_MULTI_EDGES_PER_LANE 2
+#endif
+constexpr int kMsU = FG_MULTI_EDGES_PER_LANE;   // edges per lane per step (each with two 16-byte row loads in flight)
 
 // One round: every vertex stamped >= r is expanded -- high-degree chunks by
 // whole CTAs, mid-degree vertices by warps, low-degree vertices found by a
