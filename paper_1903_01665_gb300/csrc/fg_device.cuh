@@ -1713,6 +1713,14 @@ __device__ __forceinline__ void stream_edges_async(const Team &t, const View &g,
 #ifndef FG_NEXT_PROBE_SHIFT_EDGE
 #define FG_NEXT_PROBE_SHIFT_EDGE 16
 #endif
+// vertex-sync: also in a round after one that changed more than
+// FG_GROW_FILTER times as many vertices as the round before it (0: never):
+// R-MAT 22 SSSP vertex-sync 2.69 -> 2.58 ms, any factor from 2 to 8; pull
+// rounds lost 6 % with it and keep the dense-round rule alone
+
+#ifndef FG_GROW_FILTER
+#define FG_GROW_FILTER 4
+#endif
 #ifndef FG_SPARSE_SHIFT
 #define FG_SPARSE_SHIFT 0
 #endif
@@ -1823,6 +1831,7 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
 
     if (SYNC && ok) {
         int pass_ctr = 0;
+        int64_t ch_before = 0;   // changes of the round before the previous one (the same in every thread)
         constexpr bool kW = (ALGO == kSSSP);   // the edge rings carry weights for SSSP only
         // edge-sync: a round is sparse if the previous one accepted fewer
         // candidates than n / 2^FG_SPARSE_SHIFT (round 1: only the source is
@@ -1870,10 +1879,18 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
                 int32_t *next = (r & 1) ? p.B : p.A;
                 const int32_t *scur = (r & 1) ? p.S1 : p.S0;
                 int32_t *snext = (r & 1) ? p.S0 : p.S1;
+                const int64_t ch_prev = r == 1 ? 0 : (int64_t)__ldcg(&c->changed[(r - 1) % 3]);
+                // a growing frontier reaches many vertices for the first time:
+                // most candidates then pass the first filter (R-MAT 22 SSSP round
+                // 3: 15.7 M of 20.8 M), and the running minimum saves their MINs
+                const bool growing = FG_GROW_FILTER > 0 && r > 1 &&
+                                     ch_prev > (int64_t)FG_GROW_FILTER * (ch_before > 0 ? ch_before : 1);
                 const bool dense_prev =
                     r == 1 ? ALGO == kCC
-                           : ((int64_t)__ldcg(&c->changed[(r - 1) % 3])
-                              << (MODE == kEdgeSync ? FG_NEXT_PROBE_SHIFT_EDGE : FG_NEXT_PROBE_SHIFT)) > (int64_t)n;
+                           : (ch_prev << (MODE == kEdgeSync ? FG_NEXT_PROBE_SHIFT_EDGE : FG_NEXT_PROBE_SHIFT)) >
+                                     (int64_t)n ||
+                                 (MODE == kVertexSync && growing);
+                ch_before = ch_prev;
                 SyncOp<ALGO> op{g.w, cur, next, scur, snext, r, dense_prev};
                 if (pull) {
                     pull_vertices(t, p.tv, PullMinOp<ALGO>{p.tv.w, cur, next, snext, r}, a);
