@@ -285,17 +285,22 @@ fg_status fg_run(const fg_graph *g, fg_algo algo, int32_t src, int32_t *out, fg_
  * in host or device memory).  Output j receives exactly what fg_run(g, algo,
  * srcs[j], ...) gives in any mode.
  *
- * SSSP and BFS run as one multi-source sweep, the k-source form of Alg. 1:
+ * SSSP runs as one multi-source sweep, the k-source form of Alg. 1:
  * vertex-based over the degree buckets, every vertex's k values in one
  * 32-byte row (one L2 sector), updated in place by atomic MIN and driven by a
  * per-vertex round stamp until a round lowers nothing.  Each relaxed edge
  * reads its target id and weight once for all k sources and probes the
  * target's k values with one sector access, so k queries cost far less than
- * k separate sweeps.  This is the on-device form of the paper's overlap of
+ * k separate sweeps.  BFS runs as a k-source level-synchronous sweep (Alg. 3
+ * for k sources at once): one byte per vertex holds which sources have
+ * reached it, the frontier of each round is a byte mask per vertex, an edge
+ * claims its target for the frontier's new sources with one atomic OR, and
+ * each source's level is written to its output when the source first
+ * reaches the vertex.  This is the on-device form of the paper's overlap of
  * independent computations (barrier-free kernels on separate streams,
  * Sec. 3.2; independent parallel sections, Sec. 3.4) for queries that share
- * a graph.  BFS is the same sweep with unit weights.  CC has no source: it
- * runs once (in fg_select_mode's mode) and is copied to every output.
+ * a graph.  CC has no source: it runs once (in fg_select_mode's mode) and is
+ * copied to every output.
  *
  * Options: stream, max_rounds (0 = n + 2), wait_timeout_ms, blocks_per_sm;
  * the other fields are ignored.  status_out[k] (may be NULL) receives each
@@ -303,9 +308,11 @@ fg_status fg_run(const fg_graph *g, fg_algo algo, int32_t src, int32_t *out, fg_
  * (FG_ERR_OVERFLOW for those, FG_OK and their outputs for the others).
  * stats (may be NULL) describes the one fused sweep (mode = -1).  Returns
  * FG_OK if every query succeeded, else the first failing status; a failing
- * query's output is untouched.  Blocks until the outputs are written.
- * Device state: 36 bytes per vertex (rows and stamps), plus 4 per vertex for
- * each host output.  Errors: FG_ERR_INVALID_ARG (k outside [1,
+ * SSSP query's output is untouched, while BFS writes its levels as the
+ * sweep runs, so after a BFS error (a timeout) the outputs are unspecified.
+ * Blocks until the outputs are written.  Device state: SSSP 36 bytes per
+ * vertex (rows and stamps), BFS 4 bytes per vertex (masks), plus 4 per
+ * vertex for each host output.  Errors: FG_ERR_INVALID_ARG (k outside [1,
  * FG_MULTI_MAX], NULL, a source outside [0,n), wrong device),
  * FG_ERR_OVERFLOW, FG_ERR_OUT_OF_MEMORY, FG_ERR_TIMEOUT, FG_ERR_CUDA.
  */

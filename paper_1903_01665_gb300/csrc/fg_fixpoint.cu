@@ -133,8 +133,13 @@ int64_t wl_cap_of(const View &g, Mode mode, int k) {
 // aligned.
 size_t query_workspace_bytes(const View &g, Algo algo, Mode mode) {
     const int32_t n = g.n;
-    if (mode == kMulti)   // control block, rows of 8 values, stamps
+    if (mode == kMulti) {
+        if (algo == kBFS)   // control block, reached-by masks, three frontier mask arrays
+            return Workspace::need(1, sizeof(Ctrl)) + Workspace::need(msb_pad(n), 1) +
+                   Workspace::need(3 * msb_pad(n), 1);
+        // control block, rows of 8 values, stamps
         return Workspace::need(1, sizeof(Ctrl)) + Workspace::need((int64_t)n * 8, 4) + Workspace::need(n, 4);
+    }
     const bool sync = (mode == kVertexSync || mode == kEdgeSync || mode == kPull);
     size_t need = Workspace::need(1, sizeof(Ctrl)) + Workspace::need(n, 4);
     if (sync && algo != kBFS) need += 3 * Workspace::need(n, 4);
@@ -160,8 +165,13 @@ void carve_query_workspace(char *base, const View &g, Algo algo, Mode mode, Para
     p.g = g;
     p.ctrl = ws.take<Ctrl>(1);
     if (mode == kMulti) {
-        p.A = ws.take<int32_t>((int64_t)n * 8);
-        p.S0 = ws.take<int32_t>(n);
+        if (algo == kBFS) {
+            p.A = reinterpret_cast<int32_t *>(ws.take<uint8_t>(msb_pad(n)));
+            p.S0 = reinterpret_cast<int32_t *>(ws.take<uint8_t>(3 * msb_pad(n)));
+        } else {
+            p.A = ws.take<int32_t>((int64_t)n * 8);
+            p.S0 = ws.take<int32_t>(n);
+        }
         return;
     }
     p.A = ws.take<int32_t>(n);

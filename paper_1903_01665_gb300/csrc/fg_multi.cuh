@@ -433,15 +433,284 @@ __global__ void ms_output_kernel(const int32_t *D, int32_t n, int k, MsOuts outs
     }
 }
 
+// ================================================================ k-source BFS with source masks
+// BFS needs no distances per source: a level is the round in which a source
+// first reaches the vertex.  The k-source BFS keeps one byte per vertex, bit
+// s set once source s has reached it (64 MB at 2^26 vertices: the probes stay
+// in L2, where the 32-byte rows of the SSSP sweep do not), and the frontier
+// of each round as byte masks (the sources that reached the vertex in the
+// previous round).  An edge u -> v of a frontier vertex with mask f claims v
+// for the sources in f that have not reached it, with one atomic OR on v's
+// byte; each source s that newly reaches v writes level r to its output, and
+// v joins the next frontier for those sources.  Three frontier buffers
+// rotate: round r reads F[r % 3], fills F[(r + 1) % 3] and clears
+// F[(r + 2) % 3], which held the previous round's frontier.
+__device__ __forceinline__ uint32_t ldcg_u32(const uint8_t *p) {
+    return (uint32_t)__ldcg(reinterpret_cast<const int32_t *>(p));
+}
+
+// Up to N edges per lane: targets first, then their mask bytes, then claims.
+template <int N>
+__device__ __forceinline__ void msb_relax(const View &g, const Params &p, uint8_t *vis, uint8_t *nxt, int32_t r,
+                                          const uint32_t (&e)[N], const bool (&in)[N], const uint32_t (&f)[N],
+                                          Acc &a) {
+    int32_t v[N];
+    uint32_t seen[N];
+#pragma unroll
+    for (int j = 0; j < N; j++) v[j] = in[j] ? __ldg(g.col + e[j]) : 0;
+#pragma unroll
+    for (int j = 0; j < N; j++) seen[j] = in[j] ? (uint32_t)__ldca(vis + v[j]) : 0xffu;
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+        const uint32_t bits = in[j] ? f[j] & ~seen[j] & 0xffu : 0u;
+        if (!bits) continue;
+        // a stale (L1) byte misses bits set since: the OR's old value decides
+        const int sh = (v[j] & 3) * 8;
+        const uint32_t old = atomicOr(reinterpret_cast<uint32_t *>(vis + (v[j] & ~3)), bits << sh);
+        const uint32_t newly = bits & ~(old >> sh) & 0xffu;
+        if (!newly) continue;
+        red_or(reinterpret_cast<uint32_t *>(nxt + (v[j] & ~3)), newly << sh);
+#pragma unroll
+        for (int s = 0; s < kMsMax; s++)
+            if ((newly >> s) & 1u) stcg(p.ms_out[s] + v[j], r);
+        a.changed++;
+        a.updates++;
+    }
+}
+
+__device__ __forceinline__ void msb_round(const Team &t, const View &g, const Params &p, uint8_t *vis,
+                                          const uint8_t *cur, uint8_t *nxt, int32_t r, Acc &a) {
+    __shared__ int32_t s_list[kBlock];
+    __shared__ int s_n;
+    __shared__ uint32_t s_rb[kWarps][128];
+    __shared__ uint32_t s_d[kWarps][128];
+    __shared__ uint32_t s_f[kWarps][128];
+    const unsigned lane = lane_id();
+    const int wid = threadIdx.x >> 5;
+    // ---- high-degree chunks: dealt to the team's CTAs round-robin
+    const int64_t G = t.size;
+    for (int64_t base = t.rank; base < g.n_high_chunks; base += G * kBlock) {
+        const int64_t ci = base + (int64_t)threadIdx.x * G;
+        bool act = false;
+        if (ci < g.n_high_chunks) {
+            const int32_t cv = __ldg(&g.high[ci].x);
+            act = __ldcg(cur + cv) != 0;
+            if (act && (uint32_t)__ldg(&g.high[ci].y) == __ldg(g.row_off + cv)) a.verts++;
+        }
+        const int na = block_compact(act, (int32_t)threadIdx.x, s_list, &s_n);
+        for (int i = 0; i < na; i++) {
+            const int64_t cj = base + (int64_t)s_list[i] * G;
+            const int32_t u = __ldg(&g.high[cj].x);
+            const uint32_t e0 = (uint32_t)__ldg(&g.high[cj].y);
+            const uint32_t e1 = min(e0 + (uint32_t)kChunk, __ldg(g.row_off + u + 1));
+            const uint32_t fu = __ldcg(cur + u);
+            if (threadIdx.x == 0) a.edges += e1 - e0;
+            for (uint32_t eb = e0; eb < e1; eb += kBlock * 4) {
+                uint32_t e[4], f[4];
+                bool in[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    e[j] = eb + j * kBlock + threadIdx.x;
+                    in[j] = e[j] < e1;
+                    f[j] = fu;
+                }
+                msb_relax(g, p, vis, nxt, r, e, in, f, a);
+            }
+        }
+        __syncthreads();
+    }
+    const int gw = (int)((t.rank * (unsigned)kBlock + threadIdx.x) >> 5);
+    const int nw = (int)(t.size * (unsigned)kWarps);
+    // ---- mid-degree vertices: a warp tests 32 at once, expands the active ones in turn
+    for (int base = gw; base < g.n_mid; base += nw * 32) {
+        const int i = base + (int)lane * nw;
+        int32_t u = 0;
+        uint32_t fu = 0;
+        if (i < g.n_mid) {
+            u = __ldg(g.mid + i);
+            fu = __ldcg(cur + u);
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, fu != 0);
+        if (lane == 0) a.verts += __popc(bal);
+        while (bal) {
+            const int l = __ffs(bal) - 1;
+            bal &= bal - 1;
+            const int32_t uu = __shfl_sync(0xffffffffu, u, l);
+            const uint32_t ff = __shfl_sync(0xffffffffu, fu, l);
+            const uint32_t b = __ldg(g.row_off + uu), en = __ldg(g.row_off + uu + 1);
+            if (lane == 0) a.edges += en - b;
+            for (uint32_t eb = b; eb < en; eb += 32 * 4) {
+                uint32_t e[4], f[4];
+                bool in[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    e[j] = eb + 32 * j + lane;
+                    in[j] = e[j] < en;
+                    f[j] = ff;
+                }
+                msb_relax(g, p, vis, nxt, r, e, in, f, a);
+            }
+        }
+    }
+    // ---- low-degree vertices (1..31 out-edges): dense scan of the frontier bytes, 128 per warp step
+    const int32_t n = g.n;
+    for (int64_t w0 = (int64_t)gw * 128; w0 < n; w0 += (int64_t)nw * 128) {
+        const int64_t v0 = w0 + 4 * lane;
+        if (lane == 0) a.scanned += min((int64_t)128, (int64_t)n - w0);
+        const uint32_t w4 = v0 < n ? ldcg_u32(cur + v0) : 0u;   // the buffers are padded to 16 bytes
+        bool act[4];
+        uint32_t rb[4], d[4], fm[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            fm[j] = (w4 >> (8 * j)) & 0xffu;
+            act[j] = fm[j] != 0 && v0 + j < n;
+            rb[j] = 0;
+            d[j] = 0;
+            if (act[j]) {
+                rb[j] = __ldg(g.row_off + v0 + j);
+                d[j] = __ldg(g.row_off + v0 + j + 1) - rb[j];
+                act[j] = d[j] >= 1 && d[j] < (uint32_t)kLowMax;
+            }
+        }
+        const unsigned cnt_lane = act[0] + act[1] + act[2] + act[3];
+        if (!__ballot_sync(0xffffffffu, cnt_lane != 0)) continue;
+        const unsigned incl = warp_inclusive_scan(cnt_lane);
+        const unsigned tot = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned slot = incl - cnt_lane;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if (act[j]) {
+                s_rb[wid][slot] = rb[j];
+                s_d[wid][slot] = d[j];
+                s_f[wid][slot] = fm[j];
+                slot++;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) a.verts += tot;
+        for (unsigned g0 = 0; g0 < tot; g0 += 32) {
+            const unsigned k = g0 + lane;
+            uint32_t r0 = 0, dd = 0, f0 = 0;
+            if (k < tot) {
+                r0 = s_rb[wid][k];
+                dd = s_d[wid][k];
+                f0 = s_f[wid][k];
+            }
+            const uint32_t inc = warp_inclusive_scan(dd);
+            const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+            const uint32_t exc = inc - dd;
+            if (lane == 0) a.edges += total;
+            for (uint32_t k0 = 0; k0 < total; k0 += 32 * 4) {
+                uint32_t e[4], f[4];
+                bool in[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const uint32_t x = k0 + 32 * j + lane;
+                    int owner = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const uint32_t pv = __shfl_sync(0xffffffffu, inc, owner + step - 1);
+                        if (pv <= x) owner += step;
+                    }
+                    const uint32_t ob = __shfl_sync(0xffffffffu, r0, owner);
+                    const uint32_t oe = __shfl_sync(0xffffffffu, exc, owner);
+                    f[j] = __shfl_sync(0xffffffffu, f0, owner);
+                    in[j] = x < total;
+                    e[j] = ob + (x - oe);
+                }
+                msb_relax(g, p, vis, nxt, r, e, in, f, a);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Bytes of the k-source BFS state per mask array: n rounded up to 16.
+__host__ __device__ __forceinline__ int64_t msb_pad(int32_t n) { return ((int64_t)n + 15) & ~(int64_t)15; }
+
+// The whole k-source BFS run by one team: init (masks, frontier, outputs),
+// rounds until one reaches nothing new.
+__device__ __forceinline__ void multi_bfs_body(const Params &p, const Team &t) {
+    Ctrl *c = p.ctrl;
+    const View &g = p.g;
+    const int32_t n = g.n;
+    const int k = p.ms_k;
+    const int64_t np = msb_pad(n);
+    uint8_t *vis = reinterpret_cast<uint8_t *>(p.A);
+    uint8_t *F = reinterpret_cast<uint8_t *>(p.S0);   // three frontier arrays of np bytes
+    const int64_t tid = t.rank * (int64_t)kBlock + threadIdx.x;
+    const int64_t nth = (int64_t)t.size * kBlock;
+    Acc a;
+    int rounds = 0, n_barriers = 0;
+    bool done = false;
+    auto sync_ = [&]() -> bool {
+        const bool ok = team_sync(t, c, p.timeout_ns);
+        n_barriers++;
+        return ok;
+    };
+    // ---- init: the sources' bits (reached, and the frontier of round 1), level 0 at the sources, INF elsewhere
+    for (int64_t v = tid; v < np; v += nth) {
+        uint32_t bits = 0;
+#pragma unroll
+        for (int s = 0; s < kMsMax; s++)
+            if (s < k && p.ms_src[s] == (int32_t)v) bits |= 1u << s;
+        vis[v] = (uint8_t)bits;
+        F[np + v] = (uint8_t)bits;   // F[1]
+        F[v] = 0;                    // F[0]
+        F[2 * np + v] = 0;           // F[2]
+        if (v < n)
+#pragma unroll
+            for (int s = 0; s < kMsMax; s++)
+                if (s < k) p.ms_out[s][v] = ((bits >> s) & 1u) ? 0 : kInf;
+    }
+    bool ok = sync_();
+    for (int r = 1; ok; r++) {
+        if (r > p.max_rounds) {
+            if (tid == 0) atomicOr(&c->status, kStRoundCap);
+            break;
+        }
+        if (tid == 0) c->changed[(r + 1) % 3] = 0;
+        rounds = r;
+        const uint8_t *cur = F + (r % 3) * np;
+        uint8_t *nxt = F + ((r + 1) % 3) * np;
+        int4 *clr = reinterpret_cast<int4 *>(F + ((r + 2) % 3) * np);   // the previous round's frontier
+        for (int64_t i = tid; i < np / 16; i += nth) clr[i] = make_int4(0, 0, 0, 0);
+        msb_round(t, g, p, vis, cur, nxt, r, a);
+        const int ch = block_sum(a.changed);
+        a.changed = 0;
+        if (threadIdx.x == 0 && ch) atomicAdd(&c->changed[r % 3], ch);
+        if (!sync_()) break;
+        if (__ldcg(&c->changed[r % 3]) == 0) {
+            done = true;
+            break;
+        }
+    }
+    const unsigned long long ev = block_sum(a.verts), ee = block_sum(a.edges), eu = block_sum(a.updates),
+                             es = block_sum(a.scanned);
+    if (threadIdx.x == 0) {
+        if (ev) atomicAdd(&c->st_vertices, ev);
+        if (ee) atomicAdd(&c->st_edges, ee);
+        if (eu) atomicAdd(&c->st_updates, eu);
+        if (es) atomicAdd(&c->st_scanned, es);
+    }
+    if (tid == 0) {
+        c->rounds = rounds;
+        c->barriers = n_barriers;
+        c->done = done;
+    }
+}
+
 // A query of either kind, as the kernels run it.
 template <int ALGO, int MODE>
 __device__ __forceinline__ void query_body(const Params &p, const Team &t, uint32_t &ring_used) {
     if constexpr (MODE == kMulti) {
         if constexpr (ALGO == kAnyAlgo) {
-            if (p.ms_bfs) multi_body<kBFS>(p, t);
+            if (p.ms_bfs) multi_bfs_body(p, t);
             else multi_body<kSSSP>(p, t);
-        } else if constexpr (ALGO != kCC) {
-            multi_body<ALGO>(p, t);
+        } else if constexpr (ALGO == kBFS) {
+            multi_bfs_body(p, t);
+        } else if constexpr (ALGO == kSSSP) {
+            multi_body<kSSSP>(p, t);
         }
     } else {
         fixpoint_body<ALGO, MODE>(p, t, ring_used);
