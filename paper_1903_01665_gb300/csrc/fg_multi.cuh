@@ -20,8 +20,9 @@
 // stamped, so every lowering is propagated; a round with no lowering ends the
 // sweep.  Values only decrease, so a stale (L1) copy of a row can only let
 // through a candidate that the MIN then leaves without effect -- at worst a
-// spurious stamp and one more expansion, never a wrong value.  BFS is the
-// same sweep with unit weights (levels are unit-weight distances).
+// spurious stamp and one more expansion, never a wrong value.  BFS has its
+// own k-source sweep over source masks (multi_bfs_body, below): levels need
+// no per-source distances, only which sources have reached a vertex.
 #pragma once
 
 #include "fg_device.cuh"
