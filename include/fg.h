@@ -240,7 +240,7 @@ typedef struct {
                                    mid-round or pointer-jumping barrier), at most
                                    round_trace_cap entries; NULL = no tracing */
     int32_t round_trace_cap;
-    int32_t delta;              /* FG_BUCKET: bucket width (0 = 5 x the mean edge weight x the
+    int32_t delta;              /* FG_BUCKET and fg_run_multi SSSP: bucket width (0 = 5 x the mean edge weight x the
                                    mean out-degree) */
 } fg_options;
 
@@ -288,7 +288,12 @@ fg_status fg_run(const fg_graph *g, fg_algo algo, int32_t src, int32_t *out, fg_
  * SSSP runs as one multi-source sweep, the k-source form of Alg. 1:
  * vertex-based over the degree buckets, every vertex's k values in one
  * 32-byte row (one L2 sector), updated in place by atomic MIN and driven by a
- * per-vertex round stamp until a round lowers nothing.  Each relaxed edge
+ * per-vertex round stamp until a round lowers nothing.  The k sources share
+ * one near-far order (the one FG_BUCKET runs for one source): values at
+ * or above a threshold T wait; when a round lowers nothing below T, T moves
+ * to the smallest waiting value plus the width delta, and the sweep ends when
+ * nothing waits.  Each source measures from itself, so the one schedule is a
+ * near-far delta-stepping for every source.  Each relaxed edge
  * reads its target id and weight once for all k sources and probes the
  * target's k values with one sector access, so k queries cost far less than
  * k separate sweeps.  BFS runs as a k-source level-synchronous sweep (Alg. 3
@@ -302,7 +307,9 @@ fg_status fg_run(const fg_graph *g, fg_algo algo, int32_t src, int32_t *out, fg_
  * a graph.  CC has no source: it runs once (in fg_select_mode's mode) and is
  * copied to every output.
  *
- * Options: stream, max_rounds (0 = n + 2), wait_timeout_ms, blocks_per_sm;
+ * Options: stream, max_rounds (0 = n + 2 for BFS and CC, 2 k n + 2 for
+ * SSSP, whose epochs add rounds), wait_timeout_ms, blocks_per_sm, delta (the
+ * SSSP width; 0 = FG_BUCKET's default, 5 x mean weight x mean out-degree);
  * the other fields are ignored.  status_out[k] (may be NULL) receives each
  * query's status: they differ only when some SSSP sources overflow
  * (FG_ERR_OVERFLOW for those, FG_OK and their outputs for the others).
@@ -310,8 +317,8 @@ fg_status fg_run(const fg_graph *g, fg_algo algo, int32_t src, int32_t *out, fg_
  * FG_OK if every query succeeded, else the first failing status; a failing
  * SSSP query's output is untouched, while BFS writes its levels as the
  * sweep runs, so after a BFS error (a timeout) the outputs are unspecified.
- * Blocks until the outputs are written.  Device state: SSSP 36 bytes per
- * vertex (rows and stamps), BFS 4 bytes per vertex (masks), plus 4 per
+ * Blocks until the outputs are written.  Device state: SSSP 40 bytes per
+ * vertex (rows, stamps, far marks), BFS 4 bytes per vertex (masks), plus 4 per
  * vertex for each host output.  Errors: FG_ERR_INVALID_ARG (k outside [1,
  * FG_MULTI_MAX], NULL, a source outside [0,n), wrong device),
  * FG_ERR_OVERFLOW, FG_ERR_OUT_OF_MEMORY, FG_ERR_TIMEOUT, FG_ERR_CUDA.

@@ -292,10 +292,10 @@ def fg_run(g, algo, src, out, mode, stream=None, max_rounds=0, wait_timeout_ms=0
 FG_MULTI_MAX = 8
 
 
-def fg_run_multi(g, algo, srcs, outs, stream=None, max_rounds=0, wait_timeout_ms=0, blocks_per_sm=0):
+def fg_run_multi(g, algo, srcs, outs, stream=None, max_rounds=0, wait_timeout_ms=0, blocks_per_sm=0, delta=0):
     """k = len(outs) queries of one algorithm on one graph (srcs: k sources,
-    ignored for CC).  Returns (status, [per-query status], fg_stats of the
-    fused sweep)."""
+    ignored for CC; delta: the SSSP sweep's near-far width, 0 = default).
+    Returns (status, [per-query status], fg_stats of the fused sweep)."""
     k = len(outs)
     for o in outs:
         _check_dtype(o, "int32")
@@ -306,7 +306,7 @@ def fg_run_multi(g, algo, srcs, outs, stream=None, max_rounds=0, wait_timeout_ms
     out_arr = (ctypes.c_void_p * max(k, 1))(*[_ptr(o) for o in outs])
     if stream is not None and hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
-    opt = fg_options(stream, int(max_rounds), int(wait_timeout_ms), int(blocks_per_sm), 0, None, 0, 0)
+    opt = fg_options(stream, int(max_rounds), int(wait_timeout_ms), int(blocks_per_sm), 0, None, 0, int(delta))
     sts = (ctypes.c_int * max(k, 1))()
     stats = fg_stats()
     st = load().fg_run_multi(g, int(algo), int(k), src_arr, out_arr, ctypes.byref(opt), sts, ctypes.byref(stats))

@@ -340,6 +340,7 @@ fg_status batch_launch(const fg_query *qs, int32_t nq, const fg_batch_options *o
         if (un.mode == kMulti) {
             p.ms_k = (int32_t)un.q.size();
             p.ms_bfs = un.algo == kBFS ? 1 : 0;
+            p.max_rounds = ms_default_rounds(view[u]->n, p.ms_k, un.algo == kSSSP);
             for (size_t j = 0; j < un.q.size(); j++) {
                 p.ms_src[j] = qs[un.q[j]].src;
                 p.ms_out[j] = job.dout[un.q[j]];

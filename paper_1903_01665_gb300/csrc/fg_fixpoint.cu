@@ -137,8 +137,8 @@ size_t query_workspace_bytes(const View &g, Algo algo, Mode mode) {
         if (algo == kBFS)   // control block, reached-by masks, three frontier mask arrays
             return Workspace::need(1, sizeof(Ctrl)) + Workspace::need(msb_pad(n), 1) +
                    Workspace::need(3 * msb_pad(n), 1);
-        // control block, rows of 8 values, stamps
-        return Workspace::need(1, sizeof(Ctrl)) + Workspace::need((int64_t)n * 8, 4) + Workspace::need(n, 4);
+        // control block, rows of 8 values, stamps, far-pending epochs
+        return Workspace::need(1, sizeof(Ctrl)) + Workspace::need((int64_t)n * 8, 4) + 2 * Workspace::need(n, 4);
     }
     const bool sync = (mode == kVertexSync || mode == kEdgeSync || mode == kPull);
     size_t need = Workspace::need(1, sizeof(Ctrl)) + Workspace::need(n, 4);
@@ -171,6 +171,7 @@ void carve_query_workspace(char *base, const View &g, Algo algo, Mode mode, Para
         } else {
             p.A = ws.take<int32_t>((int64_t)n * 8);
             p.S0 = ws.take<int32_t>(n);
+            p.far_mark = ws.take<int32_t>(n);
         }
         return;
     }
@@ -198,6 +199,16 @@ void carve_query_workspace(char *base, const View &g, Algo algo, Mode mode, Para
             p.far_cap = n;
         }
     }
+}
+
+// Default round cap of a multi-source sweep.  Without a width a round count
+// never exceeds n + 1 (every round extends the settled hop count of every
+// slot).  With the near-far order (SSSP) the rounds of one epoch that lower
+// something are at most the vertex-slot pairs the epoch settles, and each
+// epoch ends with one round that lowers nothing: 2 k n + 2 bounds the sum.
+int32_t ms_default_rounds(int32_t n, int k, bool near_far) {
+    const int64_t cap = near_far ? 2 * (int64_t)k * n + 2 : (int64_t)n + 2;
+    return cap > INT32_MAX ? INT32_MAX : (int32_t)cap;
 }
 
 // bucket mode: 5 x the mean edge weight x the mean out-degree unless the
@@ -409,13 +420,14 @@ fg_status run_multi(const fg_graph *G, Algo algo, int32_t k, const int32_t *srcs
     carve_query_workspace(base, g, algo, kMulti, p);
     p.ms_k = k;
     p.ms_bfs = algo == kBFS ? 1 : 0;
+    p.delta = (opt && opt->delta > 0) ? opt->delta : default_delta(G);   // the SSSP sweep's near-far width
     int32_t *dout[kMsMax] = {};
     for (int j = 0, h = 0; j < k; j++) {
         p.ms_src[j] = srcs[j];
         dout[j] = on_dev[j] ? outs[j] : reinterpret_cast<int32_t *>(base + qbytes + (size_t)(h++) * sbytes);
         p.ms_out[j] = dout[j];
     }
-    p.max_rounds = (opt && opt->max_rounds > 0) ? opt->max_rounds : (n > INT32_MAX - 2 ? INT32_MAX : n + 2);
+    p.max_rounds = (opt && opt->max_rounds > 0) ? opt->max_rounds : ms_default_rounds(n, k, algo == kSSSP);
     const int tmo = (opt && opt->wait_timeout_ms > 0) ? opt->wait_timeout_ms : 1000;
     p.timeout_ns = (unsigned long long)tmo * 1000000ull;
 

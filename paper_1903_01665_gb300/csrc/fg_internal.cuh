@@ -392,6 +392,7 @@ fg_status ensure_src(const fg_graph *g);
 
 // queries (fg_fixpoint.cu)
 int32_t default_delta(const fg_graph *G);
+int32_t ms_default_rounds(int32_t n, int k, bool near_far);
 fg_status run_multi(const fg_graph *g, Algo algo, int32_t k, const int32_t *srcs, int32_t *const *outs,
                     const fg_options *opt, fg_status *status_out, fg_stats *stats);
 fg_status run_query(const fg_graph *g, Algo algo, Mode mode, int32_t source, int32_t *out,

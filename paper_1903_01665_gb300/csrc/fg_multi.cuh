@@ -40,14 +40,27 @@ __device__ __forceinline__ void ms_load_row(const int32_t *row, int32_t (&x)[kMs
     x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
 }
 
+// The shared near-far order of the SSSP sweep.  Slots of a row at or above
+// the threshold ms_T are not propagated yet; a lowering to a value at or
+// above it marks the vertex far-pending (far_mark = the round) instead of
+// stamping it.  ms_T = INF (no width) leaves every finite slot near.  The
+// threshold sits in shared memory, one copy per CTA, written by thread 0 only
+// between team barriers: it costs the hot loop no register.
+struct MsNear {
+    int32_t *far_mark;
+};
+__shared__ int32_t ms_T;
+
 // Relaxes up to N edges per lane: all loads (targets, weights, then the
 // targets' rows) are issued before any result is used.  du[j] holds the
-// source values of edge j (a slot at INF has no candidate).  A lowered
-// target is stamped for the next round.
+// source values of edge j (a slot at INF, or at or above T, has no
+// candidate).  A target lowered below T is stamped for the next round, one
+// lowered at or above T is marked far-pending with the round.
 template <int ALGO, int N>
-__device__ __forceinline__ void ms_relax(const View &g, int32_t *D, int32_t *stamp, int32_t r,
+__device__ __forceinline__ void ms_relax(const View &g, int32_t *D, int32_t *stamp, int32_t r, const MsNear &nf,
                                          const uint32_t (&e)[N], const bool (&in)[N],
                                          const int32_t (&du)[N][kMsMax], Acc &a) {
+    const int32_t T = ms_T;   // read once: the atomics below would force a re-read
     int32_t v[N], wv[N];
 #pragma unroll
     for (int j = 0; j < N; j++) {
@@ -72,23 +85,27 @@ __device__ __forceinline__ void ms_relax(const View &g, int32_t *D, int32_t *sta
     for (int j = 0; j < N; j++) {
         if (!in[j]) continue;
         int32_t *row = D + (size_t)v[j] * kMsMax;
-        bool any = false;
+        bool near = false, far = false;
 #pragma unroll
         for (int s = 0; s < kMsMax; s++) {
-            if (du[j][s] == kInf) continue;
+            if (du[j][s] >= T) continue;   // INF, or a far slot: not propagated yet
             const uint32_t c = (uint32_t)du[j][s] + (uint32_t)wv[j];
             if (c >= (uint32_t)kInf) {
                 a.overflow = 1;
             } else if ((int32_t)c < pv[j][s]) {
                 red_min(row + s, (int32_t)c);
-                any = true;
+                if ((int32_t)c < T) near = true;
+                else far = true;
             }
         }
-        if (any) {
+        if (near) {
             stcg(stamp + v[j], r + 1);
             a.changed++;
-            a.updates++;
         }
+        if (far) {
+            stcg(nf.far_mark + v[j], r);
+        }
+        if (near || far) a.updates++;
     }
 }
 
@@ -96,8 +113,9 @@ __device__ __forceinline__ void ms_relax(const View &g, int32_t *D, int32_t *sta
 // of one vertex).
 template <int ALGO, int N>
 __device__ __forceinline__ void ms_relax_one_source(const View &g, int32_t *D, int32_t *stamp, int32_t r,
-                                                    const uint32_t (&e)[N], const bool (&in)[N],
+                                                    const MsNear &nf, const uint32_t (&e)[N], const bool (&in)[N],
                                                     const int32_t (&du)[kMsMax], Acc &a) {
+    const int32_t T = ms_T;   // read once: the atomics below would force a re-read
     int32_t v[N], wv[N];
 #pragma unroll
     for (int j = 0; j < N; j++) {
@@ -122,23 +140,27 @@ __device__ __forceinline__ void ms_relax_one_source(const View &g, int32_t *D, i
     for (int j = 0; j < N; j++) {
         if (!in[j]) continue;
         int32_t *row = D + (size_t)v[j] * kMsMax;
-        bool any = false;
+        bool near = false, far = false;
 #pragma unroll
         for (int s = 0; s < kMsMax; s++) {
-            if (du[s] == kInf) continue;
+            if (du[s] >= T) continue;   // INF, or a far slot: not propagated yet
             const uint32_t c = (uint32_t)du[s] + (uint32_t)wv[j];
             if (c >= (uint32_t)kInf) {
                 a.overflow = 1;
             } else if ((int32_t)c < pv[j][s]) {
                 red_min(row + s, (int32_t)c);
-                any = true;
+                if ((int32_t)c < T) near = true;
+                else far = true;
             }
         }
-        if (any) {
+        if (near) {
             stcg(stamp + v[j], r + 1);
             a.changed++;
-            a.updates++;
         }
+        if (far) {
+            stcg(nf.far_mark + v[j], r);
+        }
+        if (near || far) a.updates++;
     }
 }
 
@@ -152,7 +174,7 @@ constexpr int kMsU = FG_MULTI_EDGES_PER_LANE;   // edges per lane per step (each
 // dense scan of the stamps and their edges spread over the warp's lanes.
 template <int ALGO>
 __device__ __forceinline__ void ms_round(const Team &t, const View &g, int32_t *D, int32_t *stamp, int32_t r,
-                                         Acc &a) {
+                                         const MsNear &nf, Acc &a) {
     __shared__ int32_t s_list[kBlock];
     __shared__ int s_n;
     __shared__ uint32_t s_rb[kWarps][128];
@@ -187,7 +209,7 @@ __device__ __forceinline__ void ms_round(const Team &t, const View &g, int32_t *
                     e[j] = eb + j * kBlock + threadIdx.x;
                     in[j] = e[j] < e1;
                 }
-                ms_relax_one_source<ALGO>(g, D, stamp, r, e, in, du, a);
+                ms_relax_one_source<ALGO>(g, D, stamp, r, nf, e, in, du, a);
             }
         }
         __syncthreads();
@@ -221,7 +243,7 @@ __device__ __forceinline__ void ms_round(const Team &t, const View &g, int32_t *
                     e[j] = eb + 32 * j + lane;
                     in[j] = e[j] < en;
                 }
-                ms_relax_one_source<ALGO>(g, D, stamp, r, e, in, du, a);
+                ms_relax_one_source<ALGO>(g, D, stamp, r, nf, e, in, du, a);
             }
         }
     }
@@ -306,17 +328,35 @@ __device__ __forceinline__ void ms_round(const Team &t, const View &g, int32_t *
                         for (int s = 0; s < kMsMax; s++) du[j][s] = kInf;
                     }
                 }
-                ms_relax<ALGO>(g, D, stamp, r, e, in, du, a);
+                ms_relax<ALGO>(g, D, stamp, r, nf, e, in, du, a);
             }
         }
         __syncwarp();
     }
 }
 
+// Split of the shared near-far order, when a round lowered nothing below T.
+// The far-pending vertices of the epoch are those marked in one of its
+// rounds (far_mark >= the epoch's first round); each may hold finite slots at
+// or above T.  Pass 1 finds the smallest such slot m over all of them; none
+// means the sweep is done.  Otherwise T moves to m + delta, and pass 2 stamps
+// each far-pending vertex with a slot now below T for the next round, and
+// marks those that still hold a slot at or above T for the next epoch.
+// Every source measures distances from itself, so one threshold schedule
+// serves all of them: each source's sweep is a near-far delta-stepping of
+// its own.
+__device__ __forceinline__ int32_t ms_far_min(const int32_t (&x)[kMsMax], int32_t T) {
+    int32_t m = kInf;
+#pragma unroll
+    for (int s = 0; s < kMsMax; s++)
+        if (x[s] >= T && x[s] < m) m = x[s];
+    return m;
+}
+
 // The whole multi-source query run by one team: init, rounds until one
-// lowers nothing, then the rows are written out per source (unless a
-// candidate overflowed: the host then checks which sources overflowed and
-// writes the others).
+// lowers nothing and no vertex is far-pending, then the rows are written out
+// per source (unless a candidate overflowed: the host then checks which
+// sources overflowed and writes the others).
 template <int ALGO>
 __device__ __forceinline__ void multi_body(const Params &p, const Team &t) {
     Ctrl *c = p.ctrl;
@@ -349,6 +389,17 @@ __device__ __forceinline__ void multi_body(const Params &p, const Team &t) {
         row[0] = make_int4(x[0], x[1], x[2], x[3]);
         row[1] = make_int4(x[4], x[5], x[6], x[7]);
         stamp[v] = src ? 1 : 0;
+        p.far_mark[v] = 0;   // rounds start at 1
+    }
+    if (tid == 0)
+        for (int e = 0; e < 3; e++) c->far_min[e] = kInf;
+    // the epoch state lives in shared memory too, out of the round loop's registers
+    __shared__ int32_t s_epoch0, s_splits;   // first round of the current epoch; splits so far
+    MsNear nf{p.far_mark};
+    if (threadIdx.x == 0) {
+        ms_T = p.delta > 0 ? p.delta : kInf;
+        s_epoch0 = 1;
+        s_splits = 0;
     }
     bool ok = sync_();
     for (int r = 1; ok; r++) {
@@ -358,7 +409,7 @@ __device__ __forceinline__ void multi_body(const Params &p, const Team &t) {
         }
         if (tid == 0) c->changed[(r + 1) % 3] = 0;
         rounds = r;
-        ms_round<ALGO>(t, g, D, stamp, r, a);
+        ms_round<ALGO>(t, g, D, stamp, r, nf, a);
         const int ch = block_sum(a.changed);
         a.changed = 0;
         const int of = block_sum(a.overflow);
@@ -367,10 +418,54 @@ __device__ __forceinline__ void multi_body(const Params &p, const Team &t) {
             if (of) atomicOr(&c->status, kStOverflow);
         }
         if (!sync_()) break;
-        if (__ldcg(&c->changed[r % 3]) == 0) {
+        if (__ldcg(&c->changed[r % 3]) != 0) continue;
+        const int32_t T = ms_T;
+        if (T >= kInf) {   // no width: nothing is ever far
             done = true;
             break;
         }
+        // ---- split, pass 1: the smallest far slot of the epoch's far-pending vertices
+        const int32_t epoch0 = s_epoch0;
+        const int splits = s_splits;
+        int32_t fm = kInf;
+        for (int64_t v = tid; v < n; v += nth) {
+            if (ldcg(p.far_mark + v) < epoch0) continue;
+            int32_t x[kMsMax];
+            ms_load_row(D + (size_t)v * kMsMax, x, true);
+            fm = min(fm, ms_far_min(x, T));
+        }
+        fm = block_min(fm);
+        if (threadIdx.x == 0 && fm < kInf) atomicMin(&c->far_min[splits % 3], fm);
+        if (!sync_()) break;
+        const int32_t m = __ldcg(&c->far_min[splits % 3]);
+        if (m >= kInf) {
+            done = true;
+            break;
+        }
+        // ---- pass 2: far-pending vertices that turned near run next round, the rest wait for the next epoch
+        if (tid == 0) c->far_min[(splits + 1) % 3] = kInf;
+        const int32_t T_old = T;
+        const int32_t T_new = m >= kInf - p.delta ? kInf : m + p.delta;
+        for (int64_t v = tid; v < n; v += nth) {
+            if (ldcg(p.far_mark + v) < epoch0) continue;
+            int32_t x[kMsMax];
+            ms_load_row(D + (size_t)v * kMsMax, x, true);
+            bool now = false, still = false;
+#pragma unroll
+            for (int s = 0; s < kMsMax; s++) {
+                now |= x[s] >= T_old && x[s] < T_new;
+                still |= x[s] >= T_new && x[s] < kInf;
+            }
+            if (now) stcg(stamp + v, r + 1);
+            if (still) stcg(p.far_mark + v, r + 1);
+        }
+        __syncthreads();   // every thread of the CTA is done with this epoch's state
+        if (threadIdx.x == 0) {
+            s_epoch0 = r + 1;
+            s_splits = splits + 1;
+            ms_T = T_new;
+        }
+        if (!sync_()) break;
     }
     // ---- statistics
     const unsigned long long ev = block_sum(a.verts), ee = block_sum(a.edges), eu = block_sum(a.updates),
@@ -385,6 +480,7 @@ __device__ __forceinline__ void multi_body(const Params &p, const Team &t) {
         c->rounds = rounds;
         c->barriers = n_barriers;
         c->done = done;
+        c->splits = s_splits;
     }
     // ---- results: slot s of every row to source s's output (the barrier
     // above made the overflow bit visible to every CTA)

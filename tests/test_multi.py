@@ -5,8 +5,9 @@ hold the eight values of a vertex; every slot must equal the oracle's result
 for its source (Dijkstra, FIFO BFS), whatever the other slots hold: repeated
 sources, sources without out-edges, unreachable parts, zero weights,
 self-loops and duplicate edges, hubs that take the CTA path, fewer than
-eight slots.  CC has no source and is computed once for all outputs.  An
-overflow in one slot fails that slot only, and leaves its output untouched.
+eight slots, near-far widths from 1 to INT32_MAX.  CC has no source and is
+computed once for all outputs.  An overflow in one slot fails that slot
+only, and leaves its output untouched.
 """
 import numpy as np
 import pytest
@@ -83,6 +84,33 @@ def test_fewer_slots_and_mixed_outputs(k):
                 np.testing.assert_array_equal(as_numpy(o), _want(g, algo, s))
 
 
+@pytest.mark.parametrize("delta", [1, 3, 40, 1000, 2**30, 2**31 - 1])
+@pytest.mark.parametrize("name", ["grid", "rmat", "zero_weights", "heavy_path"])
+def test_near_far_widths_bit_exact(name, delta):
+    """The SSSP sweep's shared near-far order at widths from 1 (a split after
+    nearly every value) to INT32_MAX (nothing is ever far): every slot is the
+    oracle's.  Zero-weight edges keep a lowering at its source's value; the
+    heavy path puts each vertex in an epoch of its own."""
+    if name == "grid":
+        g = gg.grid(96, seed=61)
+    elif name == "rmat":
+        g = gg.rmat(13, seed=62)
+    elif name == "zero_weights":
+        g = gg.rmat(11, seed=63)
+        g = gg.Graph(g.n, g.src, g.dst, np.where(np.arange(g.m) % 3 == 0, 0, g.w).astype(np.int32), "zw")
+    else:
+        n = 300
+        g = gg.Graph(n, np.arange(n - 1, dtype=np.int32), np.arange(1, n, dtype=np.int32),
+                     np.full(n - 1, 7_000_000, np.int32), "heavy_path")
+    srcs = _sources(g, 8, seed=64)
+    with graph_handle(g) as h:
+        outs = [make_out(g.n, "device") for _ in srcs]
+        st, sts, stats = fg.fg_run_multi(h, fg.FG_ALGO_SSSP, srcs, outs, delta=delta)
+        assert st == fg.FG_OK, fg.fg_last_error()
+    for s, o in zip(srcs, outs):
+        np.testing.assert_array_equal(as_numpy(o), _want(g, fg.FG_ALGO_SSSP, s), err_msg=f"{name} delta {delta} src {s}")
+
+
 def test_cc_is_computed_once_for_every_output():
     g = gg.disjoint_cliques([40, 1, 70, 3, 1, 33, 2], seed=5)
     want = _want(g, fg.FG_ALGO_CC, 0)
@@ -126,6 +154,12 @@ def test_overflow_fails_only_its_own_slot():
             np.testing.assert_array_equal(as_numpy(o), _want(g, fg.FG_ALGO_SSSP, s))
         rc, _ = oracle.sssp(g.n, g.src, g.dst, g.w, 0)
         assert rc == oracle.OVERFLOW
+        # the same with a width of 1: vertex 1 waits far until the threshold reaches INF
+        outs = [make_out(g.n, "device", fill=-9) for _ in range(3)]
+        st, sts, _ = fg.fg_run_multi(h, fg.FG_ALGO_SSSP, [0, 1, 3], outs, delta=1)
+        assert sts == [fg.FG_ERR_OVERFLOW, fg.FG_OK, fg.FG_OK]
+        for s, o in zip([1, 3], outs[1:]):
+            np.testing.assert_array_equal(as_numpy(o), _want(g, fg.FG_ALGO_SSSP, s))
         # BFS on the same graph cannot overflow
         outs = [make_out(g.n, "device") for _ in range(3)]
         fg.check(fg.fg_run_multi(h, fg.FG_ALGO_BFS, [0, 1, 3], outs)[0])
