@@ -140,10 +140,26 @@ fg_status fg_graph_create_coo(int32_t n, int64_t m, const int32_t *src, const in
  *                 error can then come from a query; fg_graph_info reports
  *                 device_bytes as it grows and n_isolated as -1 until the
  *                 symmetrised view exists.  Results are identical.
+ * FG_GRAPH_RELABEL  renumber the vertices internally, by in-degree class
+ *                 (floor(log2(in-degree)), highest first; original order
+ *                 within a class), so that the most probed targets share
+ *                 cache lines and stay in L2.  Every call still takes and
+ *                 returns original ids: a query's source is translated on
+ *                 the device, its output permuted back, and CC labels stay
+ *                 the minimum original id of each component.  Costs 8
+ *                 bytes per vertex and, per query, one gather of the output
+ *                 (CC: two passes).
+ * FG_GRAPH_KEEP_IDS  never renumber.
+ * Neither flag: renumber when the in-degrees are skewed (their Gini
+ *                 coefficient above 0.5: R-MAT yes, grids no).
+ *                 fg_graph_info's relabelled field tells which.
  *
- * Unknown flag bits: FG_ERR_INVALID_ARG.
+ * Unknown flag bits, or both FG_GRAPH_RELABEL and FG_GRAPH_KEEP_IDS:
+ * FG_ERR_INVALID_ARG.
  */
 #define FG_GRAPH_LAZY 1u
+#define FG_GRAPH_RELABEL 2u
+#define FG_GRAPH_KEEP_IDS 4u
 fg_status fg_graph_create_csr_ex(int32_t n, int64_t m, const int64_t *row_off, const int32_t *col,
                                  const int32_t *w, uint32_t flags, fg_graph **out);
 fg_status fg_graph_create_coo_ex(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
@@ -165,6 +181,9 @@ typedef struct {
     int32_t n_isolated;         /* vertices with no edge in either direction (-1 until a
                                    FG_GRAPH_LAZY graph has built its symmetrised view) */
     int64_t device_bytes;       /* device memory held by the handle */
+    int32_t relabelled;         /* 1 if the vertices are renumbered internally
+                                   (FG_GRAPH_RELABEL, or skewed in-degrees) */
+    float in_degree_gini;       /* Gini coefficient of the in-degrees (binned) */
 } fg_graph_info_t;
 
 fg_status fg_graph_info(const fg_graph *g, fg_graph_info_t *out);

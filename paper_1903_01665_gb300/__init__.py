@@ -42,6 +42,8 @@ FG_ALGO_BFS = 1
 FG_ALGO_CC = 2
 FG_INF = 2**31 - 1
 FG_GRAPH_LAZY = 1
+FG_GRAPH_RELABEL = 2
+FG_GRAPH_KEEP_IDS = 4
 
 
 class fg_options(ctypes.Structure):
@@ -67,7 +69,8 @@ class fg_graph_info_t(ctypes.Structure):
                 ("max_out_degree", ctypes.c_int32), ("n_zero_out", ctypes.c_int32),
                 ("n_low", ctypes.c_int32), ("n_mid", ctypes.c_int32), ("n_high", ctypes.c_int32),
                 ("n_high_chunks", ctypes.c_int32), ("n_isolated", ctypes.c_int32),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("relabelled", ctypes.c_int32),
+                ("in_degree_gini", ctypes.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -211,7 +214,7 @@ def _len(x):
 
 
 def fg_graph_create_coo(n, src, dst, w=None, flags=0):
-    """Returns (status, handle).  flags: 0 or FG_GRAPH_LAZY."""
+    """Returns (status, handle).  flags: FG_GRAPH_LAZY | FG_GRAPH_RELABEL or FG_GRAPH_KEEP_IDS."""
     for a in (src, dst, w):
         _check_dtype(a, "int32")
     h = _VP()
@@ -224,7 +227,7 @@ def fg_graph_create_coo(n, src, dst, w=None, flags=0):
 
 
 def fg_graph_create_csr(n, row_off, col, w=None, flags=0):
-    """Returns (status, handle).  row_off is int64[n+1]; flags: 0 or FG_GRAPH_LAZY."""
+    """Returns (status, handle).  row_off is int64[n+1]; flags as for fg_graph_create_coo."""
     _check_dtype(row_off, "int64")
     _check_dtype(col, "int32")
     _check_dtype(w, "int32")

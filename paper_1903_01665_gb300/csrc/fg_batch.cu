@@ -294,7 +294,11 @@ fg_status batch_launch(const fg_query *qs, int32_t nq, const fg_batch_options *o
     }
     job.staged.assign(nq, false);
     size_t ws_bytes = 0;
-    for (int u = 0; u < nu; u++) ws_bytes += query_workspace_bytes(*view[u], units[u].algo, units[u].mode);
+    for (int u = 0; u < nu; u++) {
+        ws_bytes += query_workspace_bytes(*view[u], units[u].algo, units[u].mode);
+        if (units[u].algo == kCC && units[u].g->orig_of)   // the labels' smallest original ids
+            ws_bytes += Workspace::need(view[u]->n, 4);
+    }
     for (int i = 0; i < nq; i++) {
         job.staged[i] = !is_device_pointer(qs[i].out);
         if (job.staged[i]) ws_bytes += Workspace::need(view[job.qunit[i]]->n, 4);
@@ -324,6 +328,8 @@ fg_status batch_launch(const fg_query *qs, int32_t nq, const fg_batch_options *o
         qw.off += query_workspace_bytes(*view[u], un.algo, un.mode);
         Params p;
         carve_query_workspace(w, *view[u], un.algo, un.mode, p);
+        set_relabel(un.g, p);
+        if (un.algo == kCC && un.g->orig_of) p.cc_min = qw.take<int32_t>(view[u]->n);
         h_params[u] = p;
     }
     for (int i = 0; i < nq; i++)
@@ -503,8 +509,8 @@ fg_status batch_finish(BatchJob &job, fg_status *status_out, fg_stats *stats_out
             ck(cudaMemsetAsync(flag, 0, sizeof(int), st), "memset");
             if (un.mode == kMulti) {
                 ms_overflow_check_launch(v, p.A, p.ms_k, flag, st);
-            } else {
-                overflow_check_launch(v, p.out, flag, st);
+            } else {   // on the result in internal order (p.out holds it in original order)
+                overflow_check_launch(v, p.new_of ? ((hc.result_in_b && p.B) ? p.B : p.A) : p.out, flag, st);
             }
             ck(cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
             ck(cudaStreamSynchronize(st), "overflow check");
@@ -515,7 +521,7 @@ fg_status batch_finish(BatchJob &job, fg_status *status_out, fg_stats *stats_out
                     if ((hf >> j) & 1) qst[un.q[j]] = FG_ERR_OVERFLOW;
                     else ok.p[j] = job.dout[un.q[j]];
                 }
-                ms_output_launch(p.A, v.n, p.ms_k, ok, st);
+                ms_output_launch(p.A, v.n, p.ms_k, ok, p.new_of, st);
                 if (job.host_copies_done)   // the early copies carried no result: copy again
                     for (size_t j = 0; j < un.q.size(); j++) {
                         const int i = un.q[j];

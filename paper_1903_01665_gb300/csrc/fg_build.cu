@@ -93,14 +93,21 @@ __global__ void k_weight_sum(int64_t m, const int32_t *__restrict__ w, unsigned 
 // degrees in [2^(k-1), 2^k)) with each bin's degree sum: the Lorenz curve of
 // the degree distribution, from which the host forms a Gini coefficient.
 constexpr int kDegBins = 33;
-__global__ void k_degree_bins(int32_t n, const uint32_t *__restrict__ ro, unsigned long long *cnt,
+// renumber by default above this in-degree Gini (R-MAT about 0.6-0.7, grids
+// about 0.1)
+constexpr double kRelabelGini = 0.5;
+__device__ __forceinline__ int degree_bin(uint32_t d) { return d == 0 ? 0 : 32 - __clz(d); }
+
+// FROM_OFFSETS: a holds row offsets (degree = a[v+1] - a[v]), else degrees
+template <bool FROM_OFFSETS>
+__global__ void k_degree_bins(int32_t n, const uint32_t *__restrict__ a, unsigned long long *cnt,
                               unsigned long long *sum) {
     __shared__ unsigned long long s_cnt[kDegBins], s_sum[kDegBins];
     for (int i = threadIdx.x; i < kDegBins; i += blockDim.x) s_cnt[i] = s_sum[i] = 0;
     __syncthreads();
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t d = ro[v + 1] - ro[v];
-        const int b = d == 0 ? 0 : 32 - __clz(d);
+        const uint32_t d = FROM_OFFSETS ? a[v + 1] - a[v] : a[v];
+        const int b = degree_bin(d);
         atomicAdd(&s_cnt[b], 1ull);
         atomicAdd(&s_sum[b], (unsigned long long)d);
     }
@@ -129,6 +136,66 @@ double gini_of_bins(const unsigned long long *cnt, const unsigned long long *sum
         y0 = y1;
     }
     return 1.0 - 2.0 * area;
+}
+
+// ---------------------------------------------------------------- renumbering
+// Internal ids ordered by in-degree class (the bins above), highest class
+// first and original order within a class: the most probed targets then
+// share cache lines.  One block per chunk of kBlock vertices; the position
+// of vertex v is the exclusive prefix, over (class descending, chunk), of the
+// class counts, plus v's rank among the chunk's vertices of its class.
+// Counts are stored class-major: counts[(kDegBins - 1 - class) * nch + chunk].
+__global__ void k_class_counts(int32_t n, const uint32_t *__restrict__ indeg, int64_t nch, uint32_t *counts) {
+    __shared__ uint32_t s_cnt[kDegBins];
+    for (int i = threadIdx.x; i < kDegBins; i += blockDim.x) s_cnt[i] = 0;
+    __syncthreads();
+    const int64_t v = blockIdx.x * (int64_t)kBlock + threadIdx.x;
+    if (v < n) atomicAdd(&s_cnt[degree_bin(indeg[v])], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kDegBins; i += blockDim.x)
+        counts[(int64_t)(kDegBins - 1 - i) * nch + blockIdx.x] = s_cnt[i];
+}
+
+__global__ void k_class_scatter(int32_t n, const uint32_t *__restrict__ indeg, int64_t nch,
+                                const uint32_t *__restrict__ offs, int32_t *new_of, int32_t *orig_of) {
+    __shared__ uint32_t s_w[kWarps][kDegBins];   // per warp: vertices of each class
+    for (int i = threadIdx.x; i < kWarps * kDegBins; i += blockDim.x) (&s_w[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t v = blockIdx.x * (int64_t)kBlock + threadIdx.x;
+    const int wid = threadIdx.x >> 5;
+    const bool valid = v < n;
+    const unsigned act = __ballot_sync(0xffffffffu, valid);
+    int c = 0;
+    unsigned rank = 0;
+    if (valid) {
+        c = degree_bin(indeg[v]);
+        const unsigned peers = __match_any_sync(act, c);
+        rank = __popc(peers & ((1u << lane_id()) - 1u));
+        if (rank == 0) s_w[wid][c] = __popc(peers);
+    }
+    __syncthreads();
+    if (valid) {
+        uint32_t base = offs[(int64_t)(kDegBins - 1 - c) * nch + blockIdx.x] + rank;
+        for (int w = 0; w < wid; w++) base += s_w[w][c];
+        new_of[v] = (int32_t)base;
+        orig_of[base] = (int32_t)v;
+    }
+}
+
+// the edges in internal ids (their order is kept)
+__global__ void k_relabel_edges(int64_t m, const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                                const int32_t *__restrict__ new_of, int32_t *rsrc, int32_t *rdst) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        rsrc[e] = new_of[src[e]];
+        rdst[e] = new_of[dst[e]];
+    }
+}
+
+// out[new_of[v]] = in[v]
+__global__ void k_permute_u32(int32_t n, const uint32_t *__restrict__ in, const int32_t *__restrict__ new_of,
+                              uint32_t *out) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        out[new_of[v]] = in[v];
 }
 
 // Transposed CSR: every edge u->v stored at v's in-edge list as (u, w).
@@ -483,7 +550,7 @@ void build_src(Builder &b, View &v) {
 // The symmetrised view used by connected components: every edge u->v also
 // stored as v->u (the undirected nbrs iterator, Table "foreach iterators"),
 // as CSR plus edge sources.  Needs the directed view's edge sources.
-void build_sym(Builder &b, fg_graph *g) {
+void build_sym(Builder &b, fg_graph *g, const uint32_t *indeg = nullptr) {
     const View &v = g->g;
     const int32_t n = v.n;
     const int64_t m = v.m;
@@ -497,8 +564,13 @@ void build_sym(Builder &b, fg_graph *g) {
         uint32_t *deg = b.alloc_tmp<uint32_t>(n);
         uint32_t *cursor = b.alloc_tmp<uint32_t>((int64_t)n + 1);
         if (b.status == FG_OK) {
-            b.check(cudaMemsetAsync(deg, 0, (size_t)n * sizeof(uint32_t), b.st), "memset");
-            if (m > 0) { k_histogram<<<grid_for(m), kBlock, 0, b.st>>>(m, v.col, deg); count_launch(); }
+            if (indeg) {   // the in-degrees counted at creation
+                b.check(cudaMemcpyAsync(deg, indeg, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, b.st),
+                        "copy");
+            } else {
+                b.check(cudaMemsetAsync(deg, 0, (size_t)n * sizeof(uint32_t), b.st), "memset");
+                if (m > 0) { k_histogram<<<grid_for(m), kBlock, 0, b.st>>>(m, v.col, deg); count_launch(); }
+            }
             k_sym_degree<<<grid_for(n), kBlock, 0, b.st>>>(n, v.row_off, deg);
             count_launch();
             b.check(exclusive_scan(deg, sro, n, b.st), "scan");
@@ -560,6 +632,75 @@ fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const i
             else { b.status = FG_ERR_NEGATIVE_WEIGHT; b.msg = "a weight is negative"; }
         }
     }
+    // ---- in-degrees (their skew decides the renumbering; the symmetrised
+    // view reuses them) and the renumbering itself
+    uint32_t *indeg = nullptr;     // in-degrees by internal id
+    int32_t *t_rsrc = nullptr, *t_rdst = nullptr, *t_csrc = nullptr;
+    uint32_t *t_ro32 = nullptr;
+    if (b.status == FG_OK && !(create_flags & FG_GRAPH_KEEP_IDS)) {
+        indeg = b.alloc_tmp<uint32_t>(n);
+        unsigned long long *bins = b.alloc_tmp<unsigned long long>(2 * kDegBins);
+        unsigned long long hb[2 * kDegBins] = {};
+        if (b.status == FG_OK) {
+            b.check(cudaMemsetAsync(indeg, 0, (size_t)n * sizeof(uint32_t), b.st), "memset");
+            b.check(cudaMemsetAsync(bins, 0, sizeof(hb), b.st), "memset");
+            if (m > 0) { k_histogram<<<grid_for(m), kBlock, 0, b.st>>>(m, d_dst, indeg); count_launch(); }
+            k_degree_bins<false><<<grid_for(n), kBlock, 0, b.st>>>(n, indeg, bins, bins + kDegBins);
+            count_launch();
+            b.check(cudaMemcpyAsync(hb, bins, sizeof(hb), cudaMemcpyDeviceToHost, b.st), "copy");
+            b.check(cudaStreamSynchronize(b.st), "in-degrees");
+        }
+        if (bins) cudaFreeAsync(bins, b.st);
+        if (b.status == FG_OK) g->info.in_degree_gini = (float)gini_of_bins(hb, hb + kDegBins);
+    }
+    const bool relabel = b.status == FG_OK && indeg &&
+                         ((create_flags & FG_GRAPH_RELABEL) || g->info.in_degree_gini > kRelabelGini);
+    if (relabel) {
+        const int64_t nch = ((int64_t)n + kBlock - 1) / kBlock;
+        g->new_of = b.alloc_graph<int32_t>(n);
+        g->orig_of = b.alloc_graph<int32_t>(n);
+        uint32_t *counts = b.alloc_tmp<uint32_t>(kDegBins * nch);
+        uint32_t *offs = b.alloc_tmp<uint32_t>(kDegBins * nch + 1);
+        uint32_t *pdeg = b.alloc_tmp<uint32_t>(n);
+        if (from_csr) {   // the edges' sources, to renumber them as a COO
+            t_ro32 = b.alloc_tmp<uint32_t>((int64_t)n + 1);
+            t_csrc = b.alloc_tmp<int32_t>(m);
+        }
+        t_rsrc = b.alloc_tmp<int32_t>(m);
+        t_rdst = b.alloc_tmp<int32_t>(m);
+        if (b.status == FG_OK) {
+            k_class_counts<<<(unsigned)nch, kBlock, 0, b.st>>>(n, indeg, nch, counts);
+            count_launch();
+            b.check(exclusive_scan(counts, offs, kDegBins * nch, b.st), "scan");
+            k_class_scatter<<<(unsigned)nch, kBlock, 0, b.st>>>(n, indeg, nch, offs, g->new_of, g->orig_of);
+            count_launch();
+            k_permute_u32<<<grid_for(n), kBlock, 0, b.st>>>(n, indeg, g->new_of, pdeg);
+            count_launch();
+            if (from_csr) {
+                k_offsets_to_u32<<<grid_for((int64_t)n + 1), kBlock, 0, b.st>>>(n, d_ro, t_ro32);
+                count_launch();
+                if (m > 0) {
+                    k_src_from_rows<<<grid_for((int64_t)n * 32), kBlock, 0, b.st>>>(n, t_ro32, t_csrc);
+                    count_launch();
+                }
+                d_src = t_csrc;
+                from_csr = false;   // built as a COO from here on
+            }
+            if (m > 0) {
+                k_relabel_edges<<<grid_for(m), kBlock, 0, b.st>>>(m, d_src, d_dst, g->new_of, t_rsrc, t_rdst);
+                count_launch();
+            }
+            b.check(cudaGetLastError(), "renumbering");
+            d_src = t_rsrc;
+            d_dst = t_rdst;
+            std::swap(indeg, pdeg);
+        }
+        if (counts) cudaFreeAsync(counts, b.st);
+        if (offs) cudaFreeAsync(offs, b.st);
+        if (pdeg) cudaFreeAsync(pdeg, b.st);
+        g->info.relabelled = 1;
+    }
+
     View &v = g->g;
     v.n = n;
     v.m = m;
@@ -604,9 +745,14 @@ fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const i
     g->info.n_isolated = -1;
     if (!(create_flags & FG_GRAPH_LAZY)) {
         build_src(b, v);
-        build_sym(b, g);
+        build_sym(b, g, indeg);
     }
 
+    if (indeg) cudaFreeAsync(indeg, b.st);
+    if (t_rsrc) cudaFreeAsync(t_rsrc, b.st);
+    if (t_rdst) cudaFreeAsync(t_rdst, b.st);
+    if (t_csrc) cudaFreeAsync(t_csrc, b.st);
+    if (t_ro32) cudaFreeAsync(t_ro32, b.st);
     if (t_src) cudaFreeAsync(t_src, b.st);
     if (t_dst) cudaFreeAsync(t_dst, b.st);
     if (t_w) cudaFreeAsync(t_w, b.st);
@@ -630,7 +776,7 @@ fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const i
             count_launch();
         }
         if (e == cudaSuccess) {
-            k_degree_bins<<<grid_for(n), kBlock>>>(n, v.row_off, d_sum + 1, d_sum + 1 + kDegBins);
+            k_degree_bins<true><<<grid_for(n), kBlock>>>(n, v.row_off, d_sum + 1, d_sum + 1 + kDegBins);
             count_launch();
             e = cudaMemcpy(h, d_sum, sizeof(h), cudaMemcpyDeviceToHost);
         }

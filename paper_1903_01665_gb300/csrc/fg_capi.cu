@@ -141,7 +141,10 @@ fg_status fg_graph_create_csr(int32_t n, int64_t m, const int64_t *row_off, cons
 fg_status fg_graph_create_coo_ex(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
                                  const int32_t *w, uint32_t flags, fg_graph **out) {
     if (!out) return fail(FG_ERR_INVALID_ARG, "out is NULL");
-    if (flags & ~FG_GRAPH_LAZY) return fail(FG_ERR_INVALID_ARG, "unknown graph creation flags");
+    if (flags & ~(FG_GRAPH_LAZY | FG_GRAPH_RELABEL | FG_GRAPH_KEEP_IDS))
+        return fail(FG_ERR_INVALID_ARG, "unknown graph creation flags");
+    if ((flags & FG_GRAPH_RELABEL) && (flags & FG_GRAPH_KEEP_IDS))
+        return fail(FG_ERR_INVALID_ARG, "graph creation flags FG_GRAPH_RELABEL and FG_GRAPH_KEEP_IDS together");
     if (n <= 0) return fail(FG_ERR_INVALID_ARG, "n must be positive");
     if (m < 0) return fail(FG_ERR_INVALID_ARG, "m must be non-negative");
     if (m >= ((int64_t)1 << 31)) return fail(FG_ERR_INVALID_ARG, "m must be below 2^31 (the symmetrised copy uses 32-bit offsets)");
@@ -153,7 +156,10 @@ fg_status fg_graph_create_coo_ex(int32_t n, int64_t m, const int32_t *src, const
 fg_status fg_graph_create_csr_ex(int32_t n, int64_t m, const int64_t *row_off, const int32_t *col,
                                  const int32_t *w, uint32_t flags, fg_graph **out) {
     if (!out) return fail(FG_ERR_INVALID_ARG, "out is NULL");
-    if (flags & ~FG_GRAPH_LAZY) return fail(FG_ERR_INVALID_ARG, "unknown graph creation flags");
+    if (flags & ~(FG_GRAPH_LAZY | FG_GRAPH_RELABEL | FG_GRAPH_KEEP_IDS))
+        return fail(FG_ERR_INVALID_ARG, "unknown graph creation flags");
+    if ((flags & FG_GRAPH_RELABEL) && (flags & FG_GRAPH_KEEP_IDS))
+        return fail(FG_ERR_INVALID_ARG, "graph creation flags FG_GRAPH_RELABEL and FG_GRAPH_KEEP_IDS together");
     if (n <= 0) return fail(FG_ERR_INVALID_ARG, "n must be positive");
     if (m < 0) return fail(FG_ERR_INVALID_ARG, "m must be non-negative");
     if (m >= ((int64_t)1 << 31)) return fail(FG_ERR_INVALID_ARG, "m must be below 2^31 (the symmetrised copy uses 32-bit offsets)");
@@ -299,6 +305,8 @@ fg_status depth_estimate(const fg_graph *g, int32_t *out) {
     } else if (g->g.n_low > 0) {
         cudaMemcpy(&start, g->g.low, sizeof(int32_t), cudaMemcpyDeviceToHost);
     }
+    if (g->orig_of)   // run_query takes original ids
+        cudaMemcpy(&start, g->orig_of + start, sizeof(int32_t), cudaMemcpyDeviceToHost);
     fg_stats st{};
     fg_status s = run_query(g, kBFS, kVertexAsync, start, level, nullptr, &st);
     cudaFree(level);

@@ -1783,28 +1783,31 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
         return r;
     };
 
+    // the source in internal ids (a renumbered graph takes original ones)
+    const int32_t source = (ALGO != kCC && p.new_of) ? __ldg(p.new_of + p.source) : p.source;
     // ---- init: values, stamps, initial worklist (a2)
     for (int64_t v = tid; v < n; v += nth) {
-        int32_t x = (ALGO == kCC) ? (int32_t)v : (v == p.source ? 0 : kInf);
+        int32_t x = (ALGO == kCC) ? (int32_t)v : (v == source ? 0 : kInf);
         p.A[v] = x;
         if (SYNC && ALGO != kBFS) {
             p.B[v] = x;
-            p.S1[v] = (ALGO == kCC || v == p.source) ? 1 : 0;   // active in round 1
+            p.S1[v] = (ALGO == kCC || v == source) ? 1 : 0;   // active in round 1
             p.S0[v] = 0;
         }
         if (!SYNC && ALGO != kBFS) p.S0[v] = 0;
         if (MODE == kBucket && ALGO == kSSSP) p.far_mark[v] = 0;
+        if (ALGO == kCC && p.cc_min) p.cc_min[v] = kInf;
     }
     if (ALGO == kBFS)   // visited bitmap: the source alone
         for (int64_t k = tid; k < ((int64_t)n + 31) / 32; k += nth)
-            p.vis[k] = (k == (p.source >> 5)) ? 1u << (p.source & 31) : 0u;
+            p.vis[k] = (k == (source >> 5)) ? 1u << (source & 31) : 0u;
     if (MODE == kBucket && tid == 0)
         for (int k = 0; k < 3; k++) c->far_min[k] = kInf;
     if (MODE == kEdgeSync)
         for (int64_t k = tid; k < (g.m + kWTile - 1) / kWTile; k += nth) p.eflag[k] = 0;
 
     if (!SYNC && ALGO != kCC && tid == 0) {
-        int32_t s = p.source;
+        int32_t s = source;
         uint32_t b = g.row_off[s], d = g.row_off[s + 1] - b;
         if (d > 0) {
             if (MODE == kEdgeAsync) {
@@ -2166,13 +2169,21 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
     }
     // a query of a batch with a device output: the team writes the result
     // there (both sync buffers hold values >= the fixpoint and one holds it,
-    // so their minimum is the result)
+    // so their minimum is the result), in original order on a renumbered
+    // graph, where CC labels become each component's smallest original id
     if (done && p.out) {
         constexpr bool TWO = SYNC && ALGO != kBFS;
-        for (int64_t v = tid; v < n; v += nth) {
-            int32_t x = ldcg(p.A + v);
-            if (TWO) x = min(x, ldcg(p.B + v));
-            p.out[v] = x;
+        auto result = [&](int64_t u) {
+            int32_t x = ldcg(p.A + u);
+            if (TWO) x = min(x, ldcg(p.B + u));
+            return x;
+        };
+        if (ALGO == kCC && p.orig_of) {
+            for (int64_t u = tid; u < n; u += nth) atomicMin(p.cc_min + result(u), __ldg(p.orig_of + u));
+            if (sync_())
+                for (int64_t v = tid; v < n; v += nth) p.out[v] = ldcg(p.cc_min + result(__ldg(p.new_of + v)));
+        } else {
+            for (int64_t v = tid; v < n; v += nth) p.out[v] = result(p.new_of ? __ldg(p.new_of + v) : v);
         }
     }
 }

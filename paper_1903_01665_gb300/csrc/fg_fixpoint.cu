@@ -111,9 +111,73 @@ void ms_overflow_check_launch(const View &g, const int32_t *D, int k, int *flag,
     count_launch();
 }
 
-void ms_output_launch(const int32_t *D, int32_t n, int k, const MsOuts &outs, cudaStream_t st) {
-    ms_output_kernel<<<std::max(1, device_props(current_device()).sms) * 8, kBlock, 0, st>>>(D, n, k, outs);
+void ms_output_launch(const int32_t *D, int32_t n, int k, const MsOuts &outs, const int32_t *new_of,
+                      cudaStream_t st) {
+    ms_output_kernel<<<std::max(1, device_props(current_device()).sms) * 8, kBlock, 0, st>>>(D, n, k, outs,
+                                                                                             new_of);
     count_launch();
+}
+
+// ---------------------------------------------------------------- renumbered graphs
+namespace {
+// out[v] = res[idx[v]]: with idx = new_of, an internal-order result in
+// original order; with idx = orig_of, the reverse
+__global__ void k_gather_out(int32_t n, const int32_t *__restrict__ res, const int32_t *__restrict__ idx,
+                             int32_t *out) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        out[v] = res[idx[v]];
+}
+__global__ void k_fill_inf(int32_t n, int32_t *x) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        x[v] = kInf;
+}
+// mn[L] = the smallest original id among the vertices labelled L
+__global__ void k_cc_min_orig(int32_t n, const int32_t *__restrict__ lab, const int32_t *__restrict__ orig_of,
+                              int32_t *mn) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+        atomicMin(mn + lab[u], orig_of[u]);
+}
+// out[v] = mn[lab[new_of[v]]]: every vertex labelled with its component's smallest original id
+__global__ void k_cc_out(int32_t n, const int32_t *__restrict__ lab, const int32_t *__restrict__ new_of,
+                         const int32_t *__restrict__ mn, int32_t *out) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        out[v] = mn[lab[new_of[v]]];
+}
+}  // namespace
+
+void set_relabel(const fg_graph *G, Params &p) {
+    p.new_of = G->new_of;
+    p.orig_of = G->orig_of;
+}
+
+fg_status relabel_output(const fg_graph *G, Algo algo, const int32_t *res, int32_t *out, cudaStream_t st) {
+    const int32_t n = G->info.n;
+    const bool direct = is_device_pointer_on(out, G->device);
+    const int64_t tmp_n = (direct ? 0 : (int64_t)n) + (algo == kCC ? (int64_t)n : 0);
+    int32_t *tmp = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (tmp_n > 0) e = cudaMallocAsync((void **)&tmp, (size_t)tmp_n * sizeof(int32_t), st);
+    if (e != cudaSuccess) return cuda_fail(e, "output permutation workspace");
+    int32_t *dst = direct ? out : tmp;
+    const int grid = std::max(1, device_props(G->device).sms) * 8;
+    if (algo == kCC) {
+        int32_t *mn = tmp + (direct ? 0 : n);
+        k_fill_inf<<<grid, kBlock, 0, st>>>(n, mn);
+        k_cc_min_orig<<<grid, kBlock, 0, st>>>(n, res, G->orig_of, mn);
+        k_cc_out<<<grid, kBlock, 0, st>>>(n, res, G->new_of, mn, dst);
+        count_launch();
+        count_launch();
+        count_launch();
+    } else {
+        k_gather_out<<<grid, kBlock, 0, st>>>(n, res, G->new_of, dst);
+        count_launch();
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess && !direct) e = cudaMemcpyAsync(out, dst, (size_t)n * sizeof(int32_t), cudaMemcpyDefault, st);
+    if (tmp) cudaFreeAsync(tmp, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "output permutation");
+    return FG_OK;
 }
 
 namespace {
@@ -263,6 +327,7 @@ fg_status run_query(const fg_graph *G, Algo algo, Mode mode, int32_t source, int
         char *base;
     } ws{wsbase};
     p.source = source;
+    set_relabel(G, p);
     p.max_rounds = (opt && opt->max_rounds > 0) ? opt->max_rounds : (n > INT32_MAX - 2 ? INT32_MAX : n + 2);
     int tmo = (opt && opt->wait_timeout_ms > 0) ? opt->wait_timeout_ms : 1000;
     p.timeout_ns = (unsigned long long)tmo * 1000000ull;
@@ -333,7 +398,10 @@ fg_status run_query(const fg_graph *G, Algo algo, Mode mode, int32_t source, int
             }
         }
     }
-    if (status == FG_OK) {
+    if (status == FG_OK && G->new_of) {   // internal order to original order
+        status = relabel_output(G, algo, result, out, st);
+        if (status != FG_OK) msg = fg_last_error();
+    } else if (status == FG_OK) {
         e = cudaMemcpyAsync(out, result, (size_t)n * sizeof(int32_t), cudaMemcpyDefault, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) {
@@ -420,6 +488,7 @@ fg_status run_multi(const fg_graph *G, Algo algo, int32_t k, const int32_t *srcs
     carve_query_workspace(base, g, algo, kMulti, p);
     p.ms_k = k;
     p.ms_bfs = algo == kBFS ? 1 : 0;
+    set_relabel(G, p);
     p.delta = (opt && opt->delta > 0) ? opt->delta : default_delta(G);   // the SSSP sweep's near-far width
     int32_t *dout[kMsMax] = {};
     for (int j = 0, h = 0; j < k; j++) {
@@ -480,7 +549,7 @@ fg_status run_multi(const fg_graph *G, Algo algo, int32_t k, const int32_t *srcs
             else ok_outs.p[j] = dout[j];
         }
         if (e == cudaSuccess && hf != (1 << k) - 1) {
-            ms_output_launch(p.A, n, k, ok_outs, st);
+            ms_output_launch(p.A, n, k, ok_outs, p.new_of, st);
             e = cudaGetLastError();
         }
         if (e != cudaSuccess) {
@@ -535,6 +604,22 @@ fg_status run_sweep(const fg_graph *G, Mode mode, const int32_t *cur, int32_t *n
         if (ss != FG_OK) return ss;
     }
     DeviceProps dp = device_props(dev);
+    // a renumbered graph: the caller's arrays to internal order around the round
+    const int32_t n = g.n;
+    int32_t *icur = nullptr, *inext = nullptr;
+    int32_t *const user_next = next;
+    const int pgrid = std::max(1, dp.sms) * 8;
+    if (G->new_of) {
+        cudaError_t e0 = cudaMallocAsync((void **)&icur, 2 * (size_t)n * sizeof(int32_t), st);
+        if (e0 != cudaSuccess) return cuda_fail(e0, "sweep permutation workspace");
+        inext = icur + n;
+        k_gather_out<<<pgrid, kBlock, 0, st>>>(n, cur, G->orig_of, icur);
+        k_gather_out<<<pgrid, kBlock, 0, st>>>(n, next, G->orig_of, inext);
+        count_launch();
+        count_launch();
+        cur = icur;
+        next = inext;
+    }
     auto fn = (mode == kVertexSync) ? sweep_kernel<kVertexSync> : sweep_kernel<kEdgeSync>;
     int per_sm = 0;
 #ifdef FG_L1_CARVEOUT
@@ -544,7 +629,10 @@ fg_status run_sweep(const fg_graph *G, Mode mode, const int32_t *cur, int32_t *n
     int grid = std::max(1, per_sm * dp.sms);
     Ctrl *c = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&c, sizeof(Ctrl), st);
-    if (e != cudaSuccess) return cuda_fail(e, "sweep workspace");
+    if (e != cudaSuccess) {
+        if (icur) cudaFreeAsync(icur, st);
+        return cuda_fail(e, "sweep workspace");
+    }
     cudaEvent_t ev0, ev1;
     cudaEventCreate(&ev0);
     cudaEventCreate(&ev1);
@@ -557,6 +645,11 @@ fg_status run_sweep(const fg_graph *G, Mode mode, const int32_t *cur, int32_t *n
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaEventRecord(ev1, st);
+    if (e == cudaSuccess && icur) {   // next back to original order
+        k_gather_out<<<pgrid, kBlock, 0, st>>>(n, inext, G->new_of, user_next);
+        count_launch();
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, c, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     float ms = 0.f;
@@ -564,6 +657,7 @@ fg_status run_sweep(const fg_graph *G, Mode mode, const int32_t *cur, int32_t *n
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
     cudaFreeAsync(c, st);
+    if (icur) cudaFreeAsync(icur, st);
     if (e != cudaSuccess) return cuda_fail(e, "sweep");
     if (updates) *updates = (int64_t)hc.st_updates;
     if (kernel_ms) *kernel_ms = ms;

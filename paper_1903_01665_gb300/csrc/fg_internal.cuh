@@ -64,6 +64,10 @@ struct fg_graph {
     mutable int32_t diam_est = -1;
     double w_mean = 1.0;        // mean edge weight (bucket mode's default width)
     double degree_gini = 0.0;   // Gini coefficient of the out-degrees (the selection model's skew)
+    // renumbered vertices (by in-degree class), else null: every view holds
+    // internal ids, the API original ones
+    int32_t *new_of = nullptr;  // original id -> internal id
+    int32_t *orig_of = nullptr; // internal id -> original id
     mutable int32_t tuned_mode[3] = {-1, -1, -1};
     mutable int32_t tuned_bps[3] = {0, 0, 0};   // CTAs per SM measured with the tuned mode
 };
@@ -132,6 +136,11 @@ struct Params {
     unsigned long long *trace = nullptr;   // optional per-barrier timestamps (CTA 0)
     int32_t trace_cap = 0;
     Ctrl *ctrl = nullptr;
+    // renumbered graph (else null): sources come as original ids, device
+    // outputs are written in original order, CC labels as minimum original ids
+    const int32_t *new_of = nullptr;       // original id -> internal id
+    const int32_t *orig_of = nullptr;      // internal id -> original id
+    int32_t *cc_min = nullptr;             // batch CC: smallest original id of each internal label
 };
 
 // multi-source: one output pointer per slot, passed by value to a kernel
@@ -392,6 +401,12 @@ fg_status ensure_src(const fg_graph *g);
 
 // queries (fg_fixpoint.cu)
 int32_t default_delta(const fg_graph *G);
+// renumbered graphs: an internal-order result to an output in original order
+// (device or host; CC: labels to minimum original ids).  The caller has
+// checked the result; res is left unchanged.
+fg_status relabel_output(const fg_graph *G, Algo algo, const int32_t *res, int32_t *out, cudaStream_t st);
+// fills the relabelling fields of a query's Params from its graph
+void set_relabel(const fg_graph *G, Params &p);
 int32_t ms_default_rounds(int32_t n, int k, bool near_far);
 fg_status run_multi(const fg_graph *g, Algo algo, int32_t k, const int32_t *srcs, int32_t *const *outs,
                     const fg_options *opt, fg_status *status_out, fg_stats *stats);
@@ -403,7 +418,8 @@ void overflow_check_launch(const View &g, const int32_t *D, int *flag, cudaStrea
 // multi-source sweeps: bit s of *flag for each source s that overflowed; the
 // rows' slots to the outputs that are set
 void ms_overflow_check_launch(const View &g, const int32_t *D, int k, int *flag, cudaStream_t st);
-void ms_output_launch(const int32_t *D, int32_t n, int k, const MsOuts &outs, cudaStream_t st);
+void ms_output_launch(const int32_t *D, int32_t n, int k, const MsOuts &outs, const int32_t *new_of,
+                      cudaStream_t st);
 
 // batches (fg_batch.cu)
 // One fixpoint of a batch: a plain query (its outputs all receive the one

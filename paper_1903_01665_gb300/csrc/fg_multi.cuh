@@ -335,6 +335,14 @@ __device__ __forceinline__ void ms_round(const Team &t, const View &g, int32_t *
     }
 }
 
+// The sweep's sources in internal ids (a renumbered graph takes original
+// ones); slots beyond k get -1, which matches no vertex.
+__device__ __forceinline__ void ms_internal_sources(const Params &p, int k, int32_t (&out)[kMsMax]) {
+#pragma unroll
+    for (int s = 0; s < kMsMax; s++)
+        out[s] = s < k ? (p.new_of ? __ldg(p.new_of + p.ms_src[s]) : p.ms_src[s]) : -1;
+}
+
 // Split of the shared near-far order, when a round lowered nothing below T.
 // The far-pending vertices of the epoch are those marked in one of its
 // rounds (far_mark >= the epoch's first round); each may hold finite slots at
@@ -376,12 +384,14 @@ __device__ __forceinline__ void multi_body(const Params &p, const Team &t) {
         return ok;
     };
     // ---- init: every row INF but the sources' own slots; the sources are stamped for round 1
+    int32_t msrc[kMsMax];
+    ms_internal_sources(p, k, msrc);
     for (int64_t v = tid; v < n; v += nth) {
         int32_t x[kMsMax];
         bool src = false;
 #pragma unroll
         for (int s = 0; s < kMsMax; s++) {
-            const bool mine = s < k && p.ms_src[s] == (int32_t)v;
+            const bool mine = msrc[s] == (int32_t)v;
             x[s] = mine ? 0 : kInf;
             src |= mine;
         }
@@ -482,12 +492,12 @@ __device__ __forceinline__ void multi_body(const Params &p, const Team &t) {
         c->done = done;
         c->splits = s_splits;
     }
-    // ---- results: slot s of every row to source s's output (the barrier
-    // above made the overflow bit visible to every CTA)
+    // ---- results: slot s of every row to source s's output, in original
+    // order (the barrier above made the overflow bit visible to every CTA)
     if (done && !(__ldcg(&c->status) & kStOverflow)) {
         for (int64_t v = tid; v < n; v += nth) {
             int32_t x[kMsMax];
-            ms_load_row(D + (size_t)v * kMsMax, x, true);
+            ms_load_row(D + (size_t)(p.new_of ? __ldg(p.new_of + v) : v) * kMsMax, x, true);
 #pragma unroll
             for (int s = 0; s < kMsMax; s++)
                 if (s < k && p.ms_out[s]) p.ms_out[s][v] = x[s];
@@ -519,11 +529,12 @@ __global__ void ms_overflow_check_kernel(View g, const int32_t *D, int k, int *f
 }
 
 // Writes slot s of every row to outs[s] for the sources whose output is set
-// (after an overflow: the sources that did not overflow).
-__global__ void ms_output_kernel(const int32_t *D, int32_t n, int k, MsOuts outs) {
+// (after an overflow: the sources that did not overflow), in original order
+// (new_of: a renumbered graph's internal ids, else null).
+__global__ void ms_output_kernel(const int32_t *D, int32_t n, int k, MsOuts outs, const int32_t *new_of) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         int32_t x[kMsMax];
-        ms_load_row(D + (size_t)v * kMsMax, x, true);
+        ms_load_row(D + (size_t)(new_of ? __ldg(new_of + v) : v) * kMsMax, x, true);
 #pragma unroll
         for (int s = 0; s < kMsMax; s++)
             if (s < k && outs.p[s]) outs.p[s][v] = x[s];
@@ -567,9 +578,10 @@ __device__ __forceinline__ void msb_relax(const View &g, const Params &p, uint8_
         const uint32_t newly = bits & ~(old >> sh) & 0xffu;
         if (!newly) continue;
         red_or(reinterpret_cast<uint32_t *>(nxt + (v[j] & ~3)), newly << sh);
+        const int32_t ov = p.orig_of ? __ldg(p.orig_of + v[j]) : v[j];   // outputs are in original order
 #pragma unroll
         for (int s = 0; s < kMsMax; s++)
-            if ((newly >> s) & 1u) stcg(p.ms_out[s] + v[j], r);
+            if ((newly >> s) & 1u) stcg(p.ms_out[s] + ov, r);
         a.changed++;
         a.updates++;
     }
@@ -745,12 +757,16 @@ __device__ __forceinline__ void multi_bfs_body(const Params &p, const Team &t) {
         n_barriers++;
         return ok;
     };
-    // ---- init: the sources' bits (reached, and the frontier of round 1), level 0 at the sources, INF elsewhere
+    // ---- init: the sources' bits (reached, and the frontier of round 1),
+    // level 0 at the sources, INF elsewhere (the outputs are in original
+    // order, the masks in internal ids)
+    int32_t msrc[kMsMax];
+    ms_internal_sources(p, k, msrc);
     for (int64_t v = tid; v < np; v += nth) {
         uint32_t bits = 0;
 #pragma unroll
         for (int s = 0; s < kMsMax; s++)
-            if (s < k && p.ms_src[s] == (int32_t)v) bits |= 1u << s;
+            if (msrc[s] == (int32_t)v) bits |= 1u << s;
         vis[v] = (uint8_t)bits;
         F[np + v] = (uint8_t)bits;   // F[1]
         F[v] = 0;                    // F[0]
@@ -758,7 +774,7 @@ __device__ __forceinline__ void multi_bfs_body(const Params &p, const Team &t) {
         if (v < n)
 #pragma unroll
             for (int s = 0; s < kMsMax; s++)
-                if (s < k) p.ms_out[s][v] = ((bits >> s) & 1u) ? 0 : kInf;
+                if (s < k) p.ms_out[s][v] = p.ms_src[s] == (int32_t)v ? 0 : kInf;
     }
     bool ok = sync_();
     for (int r = 1; ok; r++) {

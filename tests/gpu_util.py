@@ -22,8 +22,9 @@ def to_csr(g):
 
 
 @contextlib.contextmanager
-def graph_handle(g, kind="coo", where="host", weights=True):
-    """Create a device graph from a graphgen.Graph; destroyed on exit."""
+def graph_handle(g, kind="coo", where="host", weights=True, flags=0):
+    """Create a device graph from a graphgen.Graph (creation flags: e.g.
+    FG_GRAPH_RELABEL, FG_GRAPH_KEEP_IDS); destroyed on exit."""
     import torch
     w = g.w if weights else None
     if kind == "coo":
@@ -35,9 +36,9 @@ def graph_handle(g, kind="coo", where="host", weights=True):
     if where == "device":
         arrs = [None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
     if kind == "coo":
-        st, h = fg.fg_graph_create_coo(g.n, *arrs)
+        st, h = fg.fg_graph_create_coo(g.n, *arrs, flags=flags)
     else:
-        st, h = fg.fg_graph_create_csr(g.n, *arrs)
+        st, h = fg.fg_graph_create_csr(g.n, *arrs, flags=flags)
     fg.check(st)
     try:
         yield h

@@ -57,7 +57,7 @@ int main(void) {
   P(fg_graph_info_t, max_out_degree); P(fg_graph_info_t, n_zero_out); P(fg_graph_info_t, n_low);
   P(fg_graph_info_t, n_mid); P(fg_graph_info_t, n_high); P(fg_graph_info_t, n_high_chunks);
   P(fg_graph_info_t, n_isolated);
-  P(fg_graph_info_t, device_bytes);
+  P(fg_graph_info_t, device_bytes); P(fg_graph_info_t, relabelled); P(fg_graph_info_t, in_degree_gini);
   printf("fg_query %zu\nfg_batch_options %zu\nfg_batch_stats %zu\n", sizeof(fg_query), sizeof(fg_batch_options), sizeof(fg_batch_stats));
   P(fg_query, g); P(fg_query, algo); P(fg_query, src); P(fg_query, out); P(fg_query, mode);
   P(fg_batch_options, stream); P(fg_batch_options, use_cuda_graph); P(fg_batch_options, wait_timeout_ms);
@@ -104,7 +104,7 @@ def test_host_side_argument_checks():
     st = fg.load().fg_graph_create_coo(3, 1 << 31, src.ctypes.data, dst.ctypes.data, None,
                                        ctypes.byref(ctypes.c_void_p()))
     assert st == fg.FG_ERR_INVALID_ARG
-    for bad_flags in (2, 0x80000000):
+    for bad_flags in (8, 0x80000000, 2 | 4):   # unknown bits; renumber and keep ids together
         st, g = fg.fg_graph_create_coo(3, src, dst, flags=bad_flags)
         assert st == fg.FG_ERR_INVALID_ARG and g is None and "flags" in fg.fg_last_error()
         st, g = fg.fg_graph_create_csr(3, np.array([0, 1, 2, 2], np.int64), dst, flags=bad_flags)
