@@ -98,18 +98,28 @@ constexpr int kDegBins = 33;
 constexpr double kRelabelGini = 0.5;
 __device__ __forceinline__ int degree_bin(uint32_t d) { return d == 0 ? 0 : 32 - __clz(d); }
 
-// FROM_OFFSETS: a holds row offsets (degree = a[v+1] - a[v]), else degrees
+// FROM_OFFSETS: a holds row offsets (degree = a[v+1] - a[v]), else degrees.
+// The lanes of a warp that fall in one bin add to it once (most vertices
+// fall in a few bins).
 template <bool FROM_OFFSETS>
 __global__ void k_degree_bins(int32_t n, const uint32_t *__restrict__ a, unsigned long long *cnt,
                               unsigned long long *sum) {
     __shared__ unsigned long long s_cnt[kDegBins], s_sum[kDegBins];
     for (int i = threadIdx.x; i < kDegBins; i += blockDim.x) s_cnt[i] = s_sum[i] = 0;
     __syncthreads();
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = base + threadIdx.x;
+        const bool valid = v < n;
+        const unsigned act = __ballot_sync(0xffffffffu, valid);
+        if (!valid) continue;
         const uint32_t d = FROM_OFFSETS ? a[v + 1] - a[v] : a[v];
         const int b = degree_bin(d);
-        atomicAdd(&s_cnt[b], 1ull);
-        atomicAdd(&s_sum[b], (unsigned long long)d);
+        const unsigned peers = __match_any_sync(act, b);
+        const unsigned long long ds = __reduce_add_sync(peers, d);   // at most m < 2^31
+        if ((int)lane_id() == __ffs(peers) - 1) {
+            atomicAdd(&s_cnt[b], (unsigned long long)__popc(peers));
+            atomicAdd(&s_sum[b], ds);
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kDegBins; i += blockDim.x) {
@@ -182,12 +192,22 @@ __global__ void k_class_scatter(int32_t n, const uint32_t *__restrict__ indeg, i
     }
 }
 
-// the edges in internal ids (their order is kept)
-__global__ void k_relabel_edges(int64_t m, const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
-                                const int32_t *__restrict__ new_of, int32_t *rsrc, int32_t *rdst) {
+// A renumbered graph's CSR, scattered from the original edge list: the
+// cursors are indexed by original id (cursor[x] = row_off[new_of[x]]), so the
+// atomics land where they would without renumbering -- spread over the ids --
+// and not on the adjacent counters of the hubs, which renumbering puts first.
+__global__ void k_cursor_of_orig(int32_t n, const uint32_t *__restrict__ ro, const int32_t *__restrict__ new_of,
+                                 uint32_t *cursor) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+        cursor[x] = ro[new_of[x]];
+}
+__global__ void k_scatter_coo_renum(int64_t m, const int32_t *__restrict__ s, const int32_t *__restrict__ d,
+                                    const int32_t *__restrict__ w, const int32_t *__restrict__ new_of,
+                                    uint32_t *cursor, int32_t *col, int32_t *wout) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
-        rsrc[e] = new_of[src[e]];
-        rdst[e] = new_of[dst[e]];
+        const uint32_t pos = atomicAdd(&cursor[s[e]], 1u);
+        col[pos] = new_of[d[e]];
+        wout[pos] = w ? w[e] : 1;
     }
 }
 
@@ -246,6 +266,29 @@ __global__ void k_sym_cursor(int32_t n, const uint32_t *__restrict__ sro, const 
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x)
         cursor[v] = sro[v] + (ro[v + 1] - ro[v]);
+}
+
+// Renumbered graphs: as k_scatter_sym, but the in-edge cursors are indexed by
+// original id (cursor[x] for x = orig_of[v]), so that the atomics of the
+// hubs' in-edges, which renumbering makes adjacent, spread over the ids; the
+// edges are still taken in CSR order, so each in-edge list stays ordered by
+// source roughly as without renumbering.
+__global__ void k_sym_cursor_orig(int32_t n, const uint32_t *__restrict__ sro, const uint32_t *__restrict__ ro,
+                                  const int32_t *__restrict__ new_of, uint32_t *cursor) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = new_of[x];
+        cursor[x] = sro[u] + (ro[u + 1] - ro[u]);
+    }
+}
+__global__ void k_scatter_sym_renum(int64_t m, const int32_t *__restrict__ src, const int32_t *__restrict__ col,
+                                    const uint32_t *__restrict__ ro, const uint32_t *__restrict__ sro,
+                                    const int32_t *__restrict__ orig_of, uint32_t *cursor, int32_t *scol) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = src[e], v = col[e];
+        scol[sro[u] + ((uint32_t)e - ro[u])] = v;
+        const uint32_t q = atomicAdd(&cursor[orig_of[v]], 1u);
+        scol[q] = u;
+    }
 }
 
 __global__ void k_scatter_sym(int64_t m, const int32_t *__restrict__ src, const int32_t *__restrict__ col,
@@ -550,6 +593,7 @@ void build_src(Builder &b, View &v) {
 // The symmetrised view used by connected components: every edge u->v also
 // stored as v->u (the undirected nbrs iterator, Table "foreach iterators"),
 // as CSR plus edge sources.  Needs the directed view's edge sources.
+// indeg: the in-degrees counted at creation (else counted here)
 void build_sym(Builder &b, fg_graph *g, const uint32_t *indeg = nullptr) {
     const View &v = g->g;
     const int32_t n = v.n;
@@ -574,11 +618,22 @@ void build_sym(Builder &b, fg_graph *g, const uint32_t *indeg = nullptr) {
             k_sym_degree<<<grid_for(n), kBlock, 0, b.st>>>(n, v.row_off, deg);
             count_launch();
             b.check(exclusive_scan(deg, sro, n, b.st), "scan");
-            k_sym_cursor<<<grid_for(n), kBlock, 0, b.st>>>(n, sro, v.row_off, cursor);
-            count_launch();
-            if (m > 0) {
-                k_scatter_sym<<<grid_for(m), kBlock, 0, b.st>>>(m, v.src, v.col, v.row_off, sro, cursor, scol);
+            if (g->new_of) {
+                k_sym_cursor_orig<<<grid_for(n), kBlock, 0, b.st>>>(n, sro, v.row_off, g->new_of, cursor);
                 count_launch();
+            } else {
+                k_sym_cursor<<<grid_for(n), kBlock, 0, b.st>>>(n, sro, v.row_off, cursor);
+                count_launch();
+            }
+            if (m > 0) {
+                if (g->new_of) {
+                    k_scatter_sym_renum<<<grid_for(m), kBlock, 0, b.st>>>(m, v.src, v.col, v.row_off, sro,
+                                                                          g->orig_of, cursor, scol);
+                    count_launch();
+                } else {
+                    k_scatter_sym<<<grid_for(m), kBlock, 0, b.st>>>(m, v.src, v.col, v.row_off, sro, cursor, scol);
+                    count_launch();
+                }
                 k_src_from_rows<<<grid_for((int64_t)n * 32), kBlock, 0, b.st>>>(n, sro, ssrc);
                 count_launch();
             }
@@ -635,7 +690,7 @@ fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const i
     // ---- in-degrees (their skew decides the renumbering; the symmetrised
     // view reuses them) and the renumbering itself
     uint32_t *indeg = nullptr;     // in-degrees by internal id
-    int32_t *t_rsrc = nullptr, *t_rdst = nullptr, *t_csrc = nullptr;
+    int32_t *t_csrc = nullptr;
     uint32_t *t_ro32 = nullptr;
     if (b.status == FG_OK && !(create_flags & FG_GRAPH_KEEP_IDS)) {
         indeg = b.alloc_tmp<uint32_t>(n);
@@ -666,8 +721,6 @@ fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const i
             t_ro32 = b.alloc_tmp<uint32_t>((int64_t)n + 1);
             t_csrc = b.alloc_tmp<int32_t>(m);
         }
-        t_rsrc = b.alloc_tmp<int32_t>(m);
-        t_rdst = b.alloc_tmp<int32_t>(m);
         if (b.status == FG_OK) {
             k_class_counts<<<(unsigned)nch, kBlock, 0, b.st>>>(n, indeg, nch, counts);
             count_launch();
@@ -686,14 +739,8 @@ fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const i
                 d_src = t_csrc;
                 from_csr = false;   // built as a COO from here on
             }
-            if (m > 0) {
-                k_relabel_edges<<<grid_for(m), kBlock, 0, b.st>>>(m, d_src, d_dst, g->new_of, t_rsrc, t_rdst);
-                count_launch();
-            }
             b.check(cudaGetLastError(), "renumbering");
-            d_src = t_rsrc;
-            d_dst = t_rdst;
-            std::swap(indeg, pdeg);
+            std::swap(indeg, pdeg);   // the edges stay in original ids: the scatters renumber them
         }
         if (counts) cudaFreeAsync(counts, b.st);
         if (offs) cudaFreeAsync(offs, b.st);
@@ -719,7 +766,22 @@ fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const i
         } else {
             uint32_t *cnt = b.alloc_tmp<uint32_t>(n);
             uint32_t *cursor = b.alloc_tmp<uint32_t>((int64_t)n + 1);
-            if (b.status == FG_OK) {
+            uint32_t *cnt_o = g->new_of ? b.alloc_tmp<uint32_t>(n) : nullptr;
+            if (b.status == FG_OK && g->new_of) {   // counted and scattered by original source id
+                b.check(cudaMemsetAsync(cnt_o, 0, (size_t)n * sizeof(uint32_t), b.st), "memset");
+                if (m > 0) { k_histogram<<<grid_for(m), kBlock, 0, b.st>>>(m, d_src, cnt_o); count_launch(); }
+                k_permute_u32<<<grid_for(n), kBlock, 0, b.st>>>(n, cnt_o, g->new_of, cnt);
+                count_launch();
+                b.check(exclusive_scan(cnt, ro, n, b.st), "scan");
+                k_cursor_of_orig<<<grid_for(n), kBlock, 0, b.st>>>(n, ro, g->new_of, cursor);
+                count_launch();
+                if (m > 0) {
+                    k_scatter_coo_renum<<<grid_for(m), kBlock, 0, b.st>>>(m, d_src, d_dst, d_w, g->new_of, cursor,
+                                                                          col, wt);
+                    count_launch();
+                }
+                b.check(cudaGetLastError(), "scatter");
+            } else if (b.status == FG_OK) {
                 b.check(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(uint32_t), b.st), "memset");
                 if (m > 0) { k_histogram<<<grid_for(m), kBlock, 0, b.st>>>(m, d_src, cnt); count_launch(); }
                 b.check(exclusive_scan(cnt, ro, n, b.st), "scan");
@@ -731,6 +793,7 @@ fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const i
                 b.check(cudaGetLastError(), "scatter");
             }
             if (cnt) cudaFreeAsync(cnt, b.st);
+            if (cnt_o) cudaFreeAsync(cnt_o, b.st);
             if (cursor) cudaFreeAsync(cursor, b.st);
         }
         b.check(cudaGetLastError(), "csr");
@@ -749,8 +812,6 @@ fg_status build_graph_from_coo(int32_t n, int64_t m, const int32_t *src, const i
     }
 
     if (indeg) cudaFreeAsync(indeg, b.st);
-    if (t_rsrc) cudaFreeAsync(t_rsrc, b.st);
-    if (t_rdst) cudaFreeAsync(t_rdst, b.st);
     if (t_csrc) cudaFreeAsync(t_csrc, b.st);
     if (t_ro32) cudaFreeAsync(t_ro32, b.st);
     if (t_src) cudaFreeAsync(t_src, b.st);

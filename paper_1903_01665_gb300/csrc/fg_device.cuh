@@ -2179,7 +2179,7 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
             return x;
         };
         if (ALGO == kCC && p.orig_of) {
-            for (int64_t u = tid; u < n; u += nth) atomicMin(p.cc_min + result(u), __ldg(p.orig_of + u));
+            cc_min_orig_warp(tid >> 5, nth >> 5, n, result, p.orig_of, p.cc_min);
             if (sync_())
                 for (int64_t v = tid; v < n; v += nth) p.out[v] = ldcg(p.cc_min + result(__ldg(p.new_of + v)));
         } else {

@@ -134,8 +134,9 @@ __global__ void k_fill_inf(int32_t n, int32_t *x) {
 // mn[L] = the smallest original id among the vertices labelled L
 __global__ void k_cc_min_orig(int32_t n, const int32_t *__restrict__ lab, const int32_t *__restrict__ orig_of,
                               int32_t *mn) {
-    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
-        atomicMin(mn + lab[u], orig_of[u]);
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    cc_min_orig_warp(warp, nwarps, n, [&](int64_t u) { return lab[u]; }, orig_of, mn);
 }
 // out[v] = mn[lab[new_of[v]]]: every vertex labelled with its component's smallest original id
 __global__ void k_cc_out(int32_t n, const int32_t *__restrict__ lab, const int32_t *__restrict__ new_of,

@@ -312,6 +312,44 @@ __device__ __forceinline__ bool grid_sync(Ctrl *c, unsigned long long timeout_ns
 
 // ---------------------------------------------------------------- warp helpers
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// Renumbered graphs, CC: the smallest original id of each internal label,
+// mn[L] = min orig_of[u] over the vertices u labelled L (mn preset to INF).
+// A warp takes 32 x kRun consecutive vertices; each lane keeps the run of
+// equal labels it sees (the giant component of a skewed graph is one long
+// run, since its vertices come first, broken only by vertices that are their
+// own label, e.g. isolated ones, which MIN their own word) and flushes a run
+// with one atomic MIN; the warp's last runs are combined across lanes first.
+// Without the runs, every vertex of a giant component would MIN the same word.
+template <typename LabelFn>
+__device__ __forceinline__ void cc_min_orig_warp(int64_t warp, int64_t nwarps, int32_t n, LabelFn lab,
+                                                 const int32_t *orig_of, int32_t *mn) {
+    constexpr int kRun = 64;
+    const unsigned lane = lane_id();
+    for (int64_t base = warp * 32 * kRun; base < n; base += nwarps * 32 * kRun) {
+        int32_t cl = -1, cm = kInf;
+        for (int k = 0; k < kRun; k++) {
+            const int64_t u = base + (int64_t)k * 32 + lane;
+            if (u >= n) break;
+            const int32_t L = lab(u), o = __ldg(orig_of + u);
+            if (L == cl) {
+                if (o < cm) cm = o;
+            } else if (L == (int32_t)u) {   // a label's own vertex (e.g. an isolated one): no run to break
+                atomicMin(mn + L, o);
+            } else {
+                if (cl >= 0) atomicMin(mn + cl, cm);
+                cl = L;
+                cm = o;
+            }
+        }
+        const unsigned act = __ballot_sync(0xffffffffu, cl >= 0);
+        if (cl >= 0) {
+            const unsigned peers = __match_any_sync(act, cl);
+            const int32_t m = __reduce_min_sync(peers, cm);
+            if ((int)lane == __ffs(peers) - 1) atomicMin(mn + cl, m);
+        }
+    }
+}
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
