@@ -57,20 +57,20 @@ ALGO_NAMES = ["sssp", "bfs", "cc"]
 # is unchanged (sha256 over fg_internal.cuh, fg_device.cuh and fg_fixpoint.cu
 # at capture time).
 NCU_TRAFFIC: dict = {
-    # profiles/sssp_rmat22_traffic.md: one launch each, first seeded source, R-MAT 22
-    "fixpoint_kernel<sssp,vertex_sync>": {"bytes_per_launch": 4248252672 + 547456000, "src_sha": "f6a823493813f9a6"},
-    "fixpoint_kernel<sssp,vertex_async>": {"bytes_per_launch": 2705021952 + 202434816, "src_sha": "f6a823493813f9a6"},
-    "fixpoint_kernel<sssp,edge_sync>": {"bytes_per_launch": 5180406528 + 161949696, "src_sha": "f6a823493813f9a6"},
-    "fixpoint_kernel<sssp,edge_async>": {"bytes_per_launch": 4268786176 + 244483584, "src_sha": "f6a823493813f9a6"},
+    # profiles/sssp_rmat22_traffic.md: one launch each, first seeded source, R-MAT 22 (renumbered)
+    "fixpoint_kernel<sssp,vertex_sync>": {"bytes_per_launch": 3400207616 + 343535104, "src_sha": "f5263d1212ab3d76"},
+    "fixpoint_kernel<sssp,vertex_async>": {"bytes_per_launch": 2316889344 + 134529536, "src_sha": "f5263d1212ab3d76"},
+    "fixpoint_kernel<sssp,edge_sync>": {"bytes_per_launch": 4794400000 + 75219968, "src_sha": "f5263d1212ab3d76"},
+    "fixpoint_kernel<sssp,edge_async>": {"bytes_per_launch": 3582338048 + 167827712, "src_sha": "f5263d1212ab3d76"},
 }
 
 
 # DRAM bytes of one all-active sweep launch (R-MAT 22, the sweep roofline
 # state), same validity rule
 NCU_SWEEP_DRAM: dict = {
-    # profiles/sweep_rmat22.md: the sweep roofline state on R-MAT 22, one launch each
-    "vertex_sync": {"bytes": 670645504 + 12172544, "src_sha": "f6a823493813f9a6"},
-    "edge_sync": {"bytes": 837081088 + 5563904, "src_sha": "f6a823493813f9a6"},
+    # profiles/sweep_rmat22.md: the sweep roofline state on R-MAT 22 (renumbered), one launch each
+    "vertex_sync": {"bytes": 585667072 + 4412416, "src_sha": "f5263d1212ab3d76"},
+    "edge_sync": {"bytes": 829439232 + 3662592, "src_sha": "f5263d1212ab3d76"},
 }
 
 KERNEL_SOURCES = ("fg_internal.cuh", "fg_device.cuh", "fg_fixpoint.cu")
