@@ -356,7 +356,11 @@ fg_status fg_run_multi(const fg_graph *g, fg_algo algo, int32_t k, const int32_t
  * FG_ERR_OVERFLOW after applying every other edge.  *updates (may be NULL)
  * receives the number of successful lowering writes, which depends on the
  * schedule: at least the number of lowered vertices, at most the number of
- * edges.  *kernel_ms (may be NULL) receives the kernel's device time.  Runs
+ * edges.  *kernel_ms (may be NULL) receives the kernel's device time.  On a
+ * renumbered graph (FG_GRAPH_RELABEL) cur and next stay in original order:
+ * they are gathered into internal order before the kernel and next is
+ * gathered back after it (2 n int32 of device scratch; kernel_ms covers the
+ * round's kernel only).  Runs
  * on `stream` (NULL: legacy default stream) and blocks until done.  Used to
  * measure the sweep against the HBM roofline.  Errors: FG_ERR_INVALID_ARG
  * (NULL, host pointers, mode not FG_VERTEX_SYNC/FG_EDGE_SYNC, another
