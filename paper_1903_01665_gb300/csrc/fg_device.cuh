@@ -109,7 +109,7 @@ struct SyncOp {
     __device__ __forceinline__ int32_t refresh(int32_t, int32_t val) const { return val; }
     __device__ __forceinline__ bool cand(int32_t val, uint32_t e, int32_t &c, Acc &a) const {
         if (ALGO == kSSSP) {
-            uint32_t x = (uint32_t)val + (uint32_t)__ldg(w + e);
+            uint32_t x = (uint32_t)val + (uint32_t)ld_edge(w + e);
             if (x >= (uint32_t)kInf) { a.overflow = 1; return false; }
             c = (int32_t)x;
         } else {
@@ -249,7 +249,7 @@ struct AsyncOp {
     __device__ __forceinline__ int32_t refresh(int32_t u, int32_t val) const { return min(val, ldcg(D + u)); }
     __device__ __forceinline__ bool cand(int32_t val, uint32_t e, int32_t &c, Acc &a) const {
         if (ALGO == kSSSP) {
-            uint32_t x = (uint32_t)val + (uint32_t)__ldg(w + e);
+            uint32_t x = (uint32_t)val + (uint32_t)ld_edge(w + e);
             if (x >= (uint32_t)kInf) { a.overflow = 1; return false; }
             c = (int32_t)x;
         } else {
@@ -369,7 +369,7 @@ struct SweepOp {
     __device__ __forceinline__ void own(int32_t, int32_t) const {}
     __device__ __forceinline__ int32_t refresh(int32_t, int32_t val) const { return val; }
     __device__ __forceinline__ bool cand(int32_t val, uint32_t e, int32_t &c, Acc &a) const {
-        uint32_t x = (uint32_t)val + (uint32_t)__ldg(w + e);
+        uint32_t x = (uint32_t)val + (uint32_t)ld_edge(w + e);
         if (x >= (uint32_t)kInf) { a.overflow = 1; return false; }
         c = (int32_t)x;
         return true;
@@ -585,7 +585,7 @@ __device__ __forceinline__ void relax_batch(const int32_t *__restrict__ col, con
         c[j] = 0;
         ok[j] = in[j];
         if (ok[j]) {
-            v[j] = __ldg(col + e[j]);
+            v[j] = ld_edge(col + e[j]);
             ok[j] = op.cand(val[j], e[j], c[j], a);
         }
     }
@@ -987,7 +987,7 @@ struct PullMinOp {
     static constexpr bool kWeights = (ALGO == kSSSP);
 
     __device__ __forceinline__ bool skip(int32_t) const { return false; }
-    __device__ __forceinline__ int32_t weight(uint32_t e) const { return kWeights ? __ldg(w + e) : 0; }
+    __device__ __forceinline__ int32_t weight(uint32_t e) const { return kWeights ? ld_edge(w + e) : 0; }
     __device__ __forceinline__ int32_t cand(int32_t u, int32_t wv, Acc &a) const {
         const int32_t x = ldca(cur + u);
         if (ALGO != kSSSP || x == kInf) return x;
@@ -1074,7 +1074,7 @@ __device__ __forceinline__ void pull_vertices(const Team &t, const View &tv, con
 #pragma unroll
             for (int j = 0; j < kU; j++) {
                 const bool in = eb + j * kBlock < e1;
-                u[j] = in ? __ldg(tv.col + eb + j * kBlock) : -1;
+                u[j] = in ? ld_edge(tv.col + eb + j * kBlock) : -1;
                 wv[j] = in ? op.weight(eb + j * kBlock) : 0;
             }
 #pragma unroll
@@ -1098,7 +1098,7 @@ __device__ __forceinline__ void pull_vertices(const Team &t, const View &tv, con
 #pragma unroll
             for (int j = 0; j < kU; j++) {
                 const bool in = eb + 32 * j < re;
-                u[j] = in ? __ldg(tv.col + eb + 32 * j) : -1;
+                u[j] = in ? ld_edge(tv.col + eb + 32 * j) : -1;
                 wv[j] = in ? op.weight(eb + 32 * j) : 0;
             }
 #pragma unroll
@@ -1147,7 +1147,7 @@ __device__ __forceinline__ void pull_vertices(const Team &t, const View &tv, con
                 const uint32_t oe = __shfl_sync(0xffffffffu, excl, owner);
                 own[j] = owner;
                 e[j] = ob + (k - oe);
-                u[j] = k < total ? __ldg(tv.col + e[j]) : -1;
+                u[j] = k < total ? ld_edge(tv.col + e[j]) : -1;
                 wv[j] = k < total ? op.weight(e[j]) : 0;
             }
 #pragma unroll

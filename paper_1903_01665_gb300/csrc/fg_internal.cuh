@@ -313,6 +313,11 @@ __device__ __forceinline__ bool grid_sync(Ctrl *c, unsigned long long timeout_ns
 // ---------------------------------------------------------------- warp helpers
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
+// An edge-array element (target id, weight) read once per pass over the
+// edges: cached evict-first, so that the streamed edge arrays do not push
+// the randomly probed values out of L1 and L2.
+__device__ __forceinline__ int32_t ld_edge(const int32_t *p) { return __ldcs(p); }
+
 // Renumbered graphs, CC: the smallest original id of each internal label,
 // mn[L] = min orig_of[u] over the vertices u labelled L (mn preset to INF).
 // A warp takes 32 x kRun consecutive vertices; each lane keeps the run of

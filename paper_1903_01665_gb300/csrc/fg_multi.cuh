@@ -67,8 +67,8 @@ __device__ __forceinline__ void ms_relax(const View &g, int32_t *D, int32_t *sta
         v[j] = 0;
         wv[j] = 1;
         if (in[j]) {
-            v[j] = __ldg(g.col + e[j]);
-            if (ALGO == kSSSP) wv[j] = __ldg(g.w + e[j]);
+            v[j] = ld_edge(g.col + e[j]);
+            if (ALGO == kSSSP) wv[j] = ld_edge(g.w + e[j]);
         }
     }
     int32_t pv[N][kMsMax];
@@ -122,8 +122,8 @@ __device__ __forceinline__ void ms_relax_one_source(const View &g, int32_t *D, i
         v[j] = 0;
         wv[j] = 1;
         if (in[j]) {
-            v[j] = __ldg(g.col + e[j]);
-            if (ALGO == kSSSP) wv[j] = __ldg(g.w + e[j]);
+            v[j] = ld_edge(g.col + e[j]);
+            if (ALGO == kSSSP) wv[j] = ld_edge(g.w + e[j]);
         }
     }
     int32_t pv[N][kMsMax];
@@ -565,7 +565,7 @@ __device__ __forceinline__ void msb_relax(const View &g, const Params &p, uint8_
     int32_t v[N];
     uint32_t seen[N];
 #pragma unroll
-    for (int j = 0; j < N; j++) v[j] = in[j] ? __ldg(g.col + e[j]) : 0;
+    for (int j = 0; j < N; j++) v[j] = in[j] ? ld_edge(g.col + e[j]) : 0;
 #pragma unroll
     for (int j = 0; j < N; j++) seen[j] = in[j] ? (uint32_t)__ldca(vis + v[j]) : 0xffu;
 #pragma unroll
