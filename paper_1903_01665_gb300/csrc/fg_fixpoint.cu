@@ -19,10 +19,15 @@ __global__ void __launch_bounds__(kBlock, min_blocks<MODE>()) fixpoint_kernel(Pa
 }
 
 // One all-active sweep: vertex variant over the buckets, edge variant over
-// the COO (staged edge stream).  Ordinary launch (no grid barrier).
+// the COO (staged edge stream).  Ordinary launch (no grid barrier).  The
+// vertex variant is held to 32 registers, 8 CTAs per SM: all 64 warps of an
+// SM in flight for its latency-bound gathers (at 40 registers, 6 CTAs, its
+// all-active round ran 3 % slower under ncu); the edge variant keeps 6 CTAs
+// at 40 registers.
 constexpr unsigned long long kSweepTimeoutNs = 2000000000ull;
 template <int MODE>
-__global__ void __launch_bounds__(kBlock) sweep_kernel(View g, const int32_t *cur, int32_t *next, Ctrl *c) {
+__global__ void __launch_bounds__(kBlock, MODE == kVertexSync ? 8 : 6)
+    sweep_kernel(View g, const int32_t *cur, int32_t *next, Ctrl *c) {
     const Team t{(int)blockIdx.x, (int)gridDim.x, nullptr};
     Acc a;
     SweepOp op{g.w, cur, next};
