@@ -887,7 +887,37 @@ def cpu_baseline_sample(g, srcs, deg, workload):
            "sample": f"1 SSSP + 1 BFS from source {s}" + (" + 1 CC" if workload != "er16k" else "")
                      + f" on {workload}, sequential C, {dt:.1f} s"}
     out.update(host_info())
+    out["omp"] = omp_baseline_sample(g, srcs, deg, workload)
     return out
+
+
+def omp_baseline_sample(g, srcs, deg, workload):
+    """The multi-core CPU baseline (OpenMP frontier SSSP/BFS, union-find CC,
+    all host cores), context only: one adjacency build, then SSSP and BFS
+    from each seeded source and one CC, like the GPU step's build and
+    queries.  Its results are checked against the oracle by the CPU tests."""
+    from oracle import omp
+    if omp.build() is None:
+        return {"unavailable": "no OpenMP in the host compiler"}
+    t0 = time.perf_counter()
+    units = 0
+    with omp.Graph(g.n, g.src, g.dst, g.w) as h:
+        if h.status != omp.OK:
+            return {"unavailable": f"build status {h.status}"}
+        for s in srcs:
+            rc1, _ = h.sssp(int(s))
+            rc2, lv = h.bfs(int(s))
+            if rc1 != omp.OK or rc2 != omp.OK:
+                return {"unavailable": f"query status {rc1}/{rc2}"}
+            units += 2 * int(deg[lv != np.iinfo(np.int32).max].sum())
+    n_cc = 0
+    if workload != "er16k":
+        omp.cc(g.n, g.src, g.dst)
+        units += g.m
+        n_cc = 1
+    dt = time.perf_counter() - t0
+    return {"value": round(units / dt / 1e9, 5), "cores": omp.threads(),
+            "sample": f"1 build + {len(srcs)} SSSP + {len(srcs)} BFS + {n_cc} CC, {dt:.1f} s"}
 
 
 def run_reference(args):

@@ -8,6 +8,10 @@ state (the all-active sweep).  Only ``tests/``, ``__graft_entry__.smoke()`` and 
 benchmark's CPU-baseline leg may import this package; the CUDA library never
 does, and the two share no code.
 
+``oracle/omp.py`` (the multi-core OpenMP baseline that the benchmark reports
+beside the oracle's timing) is not part of the oracle: nothing here uses it,
+and its tests compare it with the functions below.
+
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (Floyd-Warshall, brute-force path enumeration, scipy.sparse.csgraph, closed
 forms and invariants).  Nothing is left unpinned.
