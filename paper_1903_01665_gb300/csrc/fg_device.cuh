@@ -1171,11 +1171,17 @@ __device__ __forceinline__ void pull_vertices(const Team &t, const View &tv, con
 // by every CTA.
 
 // Flag pass: a warp tests 128 consecutive vertices per step (128-bit loads of
-// the activity word); each active vertex stamps the warp tiles of its edge
-// range [row_off[v], row_off[v+1]) with `round`, a long range (more than 8
-// tiles) by the whole warp.
-__device__ __forceinline__ void flag_edge_tiles(const Team &t, const uint32_t *__restrict__ row_off, const int32_t *actw,
-                                                int32_t act_val, int32_t n, int32_t *eflag, int32_t round, Acc &a) {
+// the activity word); each active vertex of the low and mid classes stamps
+// the warp tiles of its edge range [row_off[v], row_off[v+1]) with `round`.
+// The high class (>= kMidMax out-edges) is flagged from its 2048-edge chunk
+// list instead, one warp per chunk over every warp of the team: graphs
+// renumbered by in-degree class hold their hubs in the first few 128-vertex
+// steps (on R-MAT 22 the first step alone spans 23 K of the 524 K tiles),
+// which the warps owning those steps would otherwise flag alone while the
+// rest of the grid waits at the barrier.
+__device__ __forceinline__ void flag_edge_tiles(const Team &t, const View &g, const int32_t *actw, int32_t act_val,
+                                                int32_t n, int32_t *eflag, int32_t round, Acc &a) {
+    const uint32_t *__restrict__ row_off = g.row_off;
     const unsigned lane = lane_id();
     const int64_t gw = (t.rank * (int64_t)kBlock + threadIdx.x) >> 5;
     const int64_t nw = (int64_t)t.size * kWarps;
@@ -1196,7 +1202,7 @@ __device__ __forceinline__ void flag_edge_tiles(const Team &t, const uint32_t *_
         for (int j = 0; j < 4; j++) {
             if (!act[j]) continue;
             const uint32_t rb = __ldg(row_off + vb + j), re = __ldg(row_off + vb + j + 1);
-            if (re <= rb) continue;
+            if (re <= rb || re - rb >= (uint32_t)kMidMax) continue;   // none, or high (chunk list)
             const uint32_t t0 = rb / kWTile, t1 = (re - 1) / kWTile;
             if (t1 - t0 < 8) {
                 for (uint32_t k = t0; k <= t1; k++) stcg(eflag + k, round);
@@ -1213,6 +1219,17 @@ __device__ __forceinline__ void flag_edge_tiles(const Team &t, const uint32_t *_
             const uint32_t t0 = __shfl_sync(0xffffffffu, big_t0, src), t1 = __shfl_sync(0xffffffffu, big_t1, src);
             for (uint32_t k = t0 + lane; k <= t1; k += 32) stcg(eflag + k, round);
         }
+    }
+    // high class: a chunk of at most kChunk edges spans at most
+    // kChunk / kWTile + 1 = 17 tiles, one per lane
+    static_assert(kChunk / kWTile + 1 <= 32, "a high chunk's tiles must fit one warp");
+    for (int64_t i = gw; i < g.n_high_chunks; i += nw) {
+        const int32_t u = __ldg(&g.high[i].x);
+        if (ldcg(actw + u) != act_val) continue;
+        const uint32_t e0 = (uint32_t)__ldg(&g.high[i].y);
+        const uint32_t e1 = e0 + min((uint32_t)kChunk, __ldg(row_off + u + 1) - e0);   // e0 < row_off[u+1]
+        const uint32_t k = e0 / kWTile + lane;
+        if (k <= (e1 - 1) / kWTile) stcg(eflag + k, round);
     }
 }
 
@@ -1871,7 +1888,7 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
                                     NoPush{}, a);
                     expand_low_dense(t, g.row_off, g.col, p.A, r - 1, n, op, a);
                 } else if (sparse_round(r)) {
-                    flag_edge_tiles(t, g.row_off, p.A, r - 1, n, p.eflag, r, a);
+                    flag_edge_tiles(t, g, p.A, r - 1, n, p.eflag, r, a);
                     if (!sync_()) break;
                     if (!stream_flagged_edges<kW>(t, ring_used, g, p.eflag, r, op, a, c, p.timeout_ns)) break;
                 } else {
@@ -1902,7 +1919,7 @@ __device__ __forceinline__ void fixpoint_body(const Params &p, const Team &t, ui
                                     NoPush{}, a);
                     expand_low_dense(t, g.row_off, g.col, scur, r, n, op, a);
                 } else if (sparse_round(r)) {
-                    flag_edge_tiles(t, g.row_off, scur, r, n, p.eflag, r, a);
+                    flag_edge_tiles(t, g, scur, r, n, p.eflag, r, a);
                     if (!sync_()) break;
                     if (!stream_flagged_edges<kW>(t, ring_used, g, p.eflag, r, op, a, c, p.timeout_ns)) break;
                 } else {
