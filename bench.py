@@ -58,8 +58,8 @@ ALGO_NAMES = ["sssp", "bfs", "cc"]
 # at capture time).
 NCU_TRAFFIC: dict = {
     # profiles/sssp_rmat22_traffic.md: one launch each, first seeded source, R-MAT 22 (renumbered)
-    "fixpoint_kernel<sssp,vertex_sync>": {"bytes_per_launch": 3257021184 + 123283200, "src_sha": "e479afec47bc4315"},
-    "fixpoint_kernel<sssp,edge_sync>": {"bytes_per_launch": 4793155328 + 73600768, "src_sha": "e479afec47bc4315"},
+    "fixpoint_kernel<sssp,vertex_sync>": {"bytes_per_launch": 3255336960 + 123581184, "src_sha": "0c29859e2a74ef96"},
+    "fixpoint_kernel<sssp,edge_sync>": {"bytes_per_launch": 4797810944 + 75623168, "src_sha": "0c29859e2a74ef96"},
     "fixpoint_kernel<sssp,vertex_async>": {"bytes_per_launch": 2316889344 + 134529536, "src_sha": "f5263d1212ab3d76"},
     "fixpoint_kernel<sssp,edge_async>": {"bytes_per_launch": 3582338048 + 167827712, "src_sha": "f5263d1212ab3d76"},
 }
@@ -69,8 +69,8 @@ NCU_TRAFFIC: dict = {
 # state), same validity rule
 NCU_SWEEP_DRAM: dict = {
     # profiles/sweep_rmat22.md: the sweep roofline state on R-MAT 22 (renumbered), one launch each
-    "vertex_sync": {"bytes": 584974592 + 3340288, "src_sha": "e479afec47bc4315"},
-    "edge_sync": {"bytes": 829853440 + 3479808, "src_sha": "e479afec47bc4315"},
+    "vertex_sync": {"bytes": 584944128 + 3304960, "src_sha": "0c29859e2a74ef96"},
+    "edge_sync": {"bytes": 829428224 + 3476736, "src_sha": "0c29859e2a74ef96"},
 }
 
 KERNEL_SOURCES = ("fg_internal.cuh", "fg_device.cuh", "fg_fixpoint.cu")
