@@ -148,7 +148,7 @@ def algorithmic_bytes(algo: int, mode: int, st: dict, info: dict) -> float:
     return float(b)
 
 
-def survey_bytes(algo: int, mode: int, st: dict, info: dict) -> float:
+def plan_bytes(algo: int, mode: int, st: dict, info: dict) -> float:
     """Algorithmic bytes of one query by the measurement plan's per-round
     formulas (4-byte offsets o, ids and values), summed over the rounds run:
 
@@ -729,7 +729,7 @@ def run_ours(args):
         k = (algo, mode)
         d = per_kernel.setdefault(k, {"ms": 0.0, "bytes": 0.0, "model_bytes": 0.0, "launches": 0})
         d["ms"] += st["kernel_ms"]
-        d["bytes"] += survey_bytes(algo, mode, st, r.info)
+        d["bytes"] += plan_bytes(algo, mode, st, r.info)
         d["model_bytes"] += algorithmic_bytes(algo, mode, st, r.info)
         d["launches"] += 1
     total_kernel_ms = sum(d["ms"] for d in per_kernel.values())

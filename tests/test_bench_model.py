@@ -68,15 +68,15 @@ def test_measurement_plan_formula_term_by_term():
     and per update; 4 bytes less per edge without weights; CC + 8 n per jump."""
     st = rstats(R=5, Va=40, Ea=300, U=7, P=9)
     n = INFO["n"]
-    assert bench.survey_bytes(0, 0, st, INFO) == 16 * n * 5 + 12 * 300 + 4 * 7
-    assert bench.survey_bytes(0, 5, st, INFO) == 16 * n * 5 + 12 * 300 + 4 * 7
-    assert bench.survey_bytes(0, 2, st, INFO) == 8 * n * 5 + 20 * 300 + 4 * 7
-    assert bench.survey_bytes(1, 2, st, INFO) == 8 * n * 5 + 16 * 300 + 4 * 7
+    assert bench.plan_bytes(0, 0, st, INFO) == 16 * n * 5 + 12 * 300 + 4 * 7
+    assert bench.plan_bytes(0, 5, st, INFO) == 16 * n * 5 + 12 * 300 + 4 * 7
+    assert bench.plan_bytes(0, 2, st, INFO) == 8 * n * 5 + 20 * 300 + 4 * 7
+    assert bench.plan_bytes(1, 2, st, INFO) == 8 * n * 5 + 16 * 300 + 4 * 7
     for mode in (1, 3, 6):
-        assert bench.survey_bytes(0, mode, st, INFO) == 16 * 40 + 12 * 300 + 4 * 9 + 4 * 7
-        assert bench.survey_bytes(1, mode, st, INFO) == 16 * 40 + 8 * 300 + 4 * 9 + 4 * 7
+        assert bench.plan_bytes(0, mode, st, INFO) == 16 * 40 + 12 * 300 + 4 * 9 + 4 * 7
+        assert bench.plan_bytes(1, mode, st, INFO) == 16 * 40 + 8 * 300 + 4 * 9 + 4 * 7
     st_cc = rstats(R=5, Va=40, Ea=300, U=7, jumps=3)
-    assert bench.survey_bytes(2, 0, st_cc, INFO) == 16 * n * 5 + 8 * 300 + 4 * 7 + 8 * n * 3
+    assert bench.plan_bytes(2, 0, st_cc, INFO) == 16 * n * 5 + 8 * 300 + 4 * 7 + 8 * n * 3
 
 
 def test_measurement_plan_formula_matches_the_full_sweep_figures():
@@ -85,8 +85,8 @@ def test_measurement_plan_formula_matches_the_full_sweep_figures():
     headline figures of the measurement plan."""
     n, m = 1 << 22, 16 << 22
     st = rstats(R=1, Ea=m)
-    assert abs(bench.survey_bytes(0, 0, st, {"n": n}) / 1e6 - 872.4) < 0.1
-    assert abs(bench.survey_bytes(0, 2, st, {"n": n}) / 1e6 - 1375.7) < 0.1
+    assert abs(bench.plan_bytes(0, 0, st, {"n": n}) / 1e6 - 872.4) < 0.1
+    assert abs(bench.plan_bytes(0, 2, st, {"n": n}) / 1e6 - 1375.7) < 0.1
 
 
 def test_host_info_states_cores_and_model():
