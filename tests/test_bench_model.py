@@ -102,3 +102,22 @@ def test_compact_serving_keeps_both_arms_per_rate():
                                "requests_per_rate": 2000, "rates": [row]})
     r = c["rates"]["1000"]
     assert r["qps"] == [870.0, 750.0] and r["p50"] == [1.0, 2.0] and r["p99"] == [10.0, 20.0] and r["ok"]
+
+
+def test_cpu_baseline_legs_on_a_small_graph():
+    """The CPU-baseline leg (host only): the oracle's single-thread figure with
+    the host it ran on, and the multi-core OpenMP figure beside it, both in
+    GTEPS of the same edge-counting convention; the OpenMP leg reports its
+    thread count and sample, or why it is unavailable."""
+    import numpy as np
+    import graphgen as gg
+    g = gg.rmat(12)
+    srcs = gg.sources(g, 8)
+    deg = np.bincount(g.src, minlength=g.n).astype(np.int64)
+    out = bench.cpu_baseline_sample(g, srcs, deg, "rmat22")
+    assert out["kind"] == "oracle" and out["cores"] == 1 and out["unit"] == "GTEPS"
+    assert out["value"] > 0 and out["host_cores"] >= 1 and out["cpu_model"]
+    omp = out["omp"]
+    if "unavailable" not in omp:
+        assert omp["value"] > 0 and omp["cores"] >= 1
+        assert omp["sample"].startswith("1 build + 8 SSSP + 8 BFS + 1 CC")
